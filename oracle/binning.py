@@ -1,0 +1,142 @@
+"""Step B of the oracle: tile lists, their depth order and tile ranges (test infrastructure).
+
+The paper's rasterizer (Sec. 3.1, and the 3DGS frustum culling recalled in
+Sec. 5.2 that "preserves Gaussians associated with touched tiles") splits the
+image into 16x16 tiles and gives every tile the depth-ordered list of the
+Gaussians that touch it.  The reading adopted here:
+
+  * Gaussian i touches pixel x iff o_i G_i(x) >= alpha_min, i.e.
+    q(x) = d^T conic d <= tau_i = 2 ln(o_i / alpha_min), d = x - mean2d;
+  * tile T (pixel centres [16 tx + 0.5, 16 tx + 15.5] x [16 ty + 0.5,
+    16 ty + 15.5], whether or not they fall inside the image) is kept iff the
+    minimum of q over that rectangle is <= tau_i;
+  * the candidate tiles are limited to the image's tile grid;
+  * keys are (view_tile_base + ty * tiles_x + tx, float32 bits of z); the sort
+    is stable with input order (view, Gaussian index, tiles row-major), so
+    ties in z fall back to ascending Gaussian index.
+
+These functions take the FP32 projected state as numbers (for the parity check
+they are handed the CUDA path's own stage-P outputs) and decide in float64.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def rect_min_q(A, B, C, mx, my, x0, x1, y0, y1):
+    """Exact minimum of q(x, y) = A dx^2 + 2B dx dy + C dy^2, d = (x - mx, y - my),
+    over the rectangle [x0, x1] x [y0, y1], for a positive-definite [[A,B],[B,C]].
+
+    0 if the centre is inside; otherwise the minimum lies on an edge, and on
+    each edge q is a 1-D convex quadratic minimised by clamping its vertex."""
+    A, B, C, mx, my, x0, x1, y0, y1 = np.broadcast_arrays(
+        *(np.asarray(a, np.float64) for a in (A, B, C, mx, my, x0, x1, y0, y1)))
+    inside = (mx >= x0) & (mx <= x1) & (my >= y0) & (my <= y1)
+    best = np.full(A.shape, np.inf)
+    for X in (x0, x1):                   # vertical edges: dx fixed
+        dx = X - mx
+        dy = np.clip(-B * dx / C, y0 - my, y1 - my)
+        best = np.minimum(best, A * dx * dx + 2 * B * dx * dy + C * dy * dy)
+    for Y in (y0, y1):                   # horizontal edges: dy fixed
+        dy = Y - my
+        dx = np.clip(-B * dy / A, x0 - mx, x1 - mx)
+        best = np.minimum(best, A * dx * dx + 2 * B * dx * dy + C * dy * dy)
+    return np.where(inside, 0.0, best)
+
+
+def tile_lists(mean2d, conic, opacity, valid, width, height, alpha_min=1.0 / 255.0,
+               tile=16, eps=1e-4):
+    """Per-Gaussian touched tiles for one view.
+
+    mean2d [N,2], conic [N,3], opacity [N] (numbers; converted to float64),
+    valid [N] bool.  Returns (gauss [E], tiles [E], near [E]) in the order
+    (Gaussian index, tiles row-major), where `near` marks entries whose
+    decision is within eps (relative to tau) of the boundary, and a second
+    array of near-boundary *rejected* candidates (gauss, tiles) for the
+    same tolerance."""
+    mean2d = np.asarray(mean2d, np.float64)
+    conic = np.asarray(conic, np.float64)
+    opacity = np.asarray(opacity, np.float64)
+    valid = np.asarray(valid, bool)
+    tx_n = (width + tile - 1) // tile
+    ty_n = (height + tile - 1) // tile
+    with np.errstate(divide="ignore", invalid="ignore"):
+        tau = 2.0 * np.log(opacity / alpha_min)
+    ok = valid & (tau > 0)
+    A, B, C = conic[:, 0], conic[:, 1], conic[:, 2]
+    det = A * C - B * B
+    ok &= det > 0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        sxx = np.where(ok, C / det, 0.0)       # inverse conic = 2-D covariance
+        syy = np.where(ok, A / det, 0.0)
+    rx = np.sqrt(np.maximum(tau, 0) * sxx)
+    ry = np.sqrt(np.maximum(tau, 0) * syy)
+    # generous candidate range (one extra tile each side), clipped to the grid
+    tx0 = np.clip(np.floor((mean2d[:, 0] - rx - 15.5) / tile) - 1, 0, tx_n - 1)
+    tx1 = np.clip(np.floor((mean2d[:, 0] + rx - 0.5) / tile) + 1, 0, tx_n - 1)
+    ty0 = np.clip(np.floor((mean2d[:, 1] - ry - 15.5) / tile) - 1, 0, ty_n - 1)
+    ty1 = np.clip(np.floor((mean2d[:, 1] + ry - 0.5) / tile) + 1, 0, ty_n - 1)
+    g_all, t_all, near_all, rej_g, rej_t = [], [], [], [], []
+    idx = np.nonzero(ok)[0]
+    nx = (tx1 - tx0 + 1).astype(np.int64)
+    ny = (ty1 - ty0 + 1).astype(np.int64)
+    cnt = (nx * ny)[idx]
+    if len(idx):
+        g = np.repeat(idx, cnt)
+        start = np.repeat(np.cumsum(cnt) - cnt, cnt)
+        k = np.arange(len(g)) - start
+        tyy = ty0[g].astype(np.int64) + k // nx[g]
+        txx = tx0[g].astype(np.int64) + k % nx[g]
+        m = rect_min_q(A[g], B[g], C[g], mean2d[g, 0], mean2d[g, 1],
+                       txx * tile + 0.5, txx * tile + tile - 0.5,
+                       tyy * tile + 0.5, tyy * tile + tile - 0.5)
+        keep = m <= tau[g]
+        near = np.abs(m - tau[g]) <= eps * np.maximum(tau[g], 1.0)
+        g_all, t_all, near_all = g[keep], tyy[keep] * tx_n + txx[keep], near[keep]
+        rej_g, rej_t = g[~keep & near], (tyy * tx_n + txx)[~keep & near]
+    return (np.asarray(g_all, np.int64), np.asarray(t_all, np.int64),
+            np.asarray(near_all, bool), np.asarray(rej_g, np.int64),
+            np.asarray(rej_t, np.int64))
+
+
+def sort_entries(tile_id, z32, gauss):
+    """Stable order of (tile, z) keys: ascending global tile id, then
+    ascending float32 bit pattern of z (equal to ascending z for z > 0), then
+    input order.  Inputs are listed in (view, Gaussian, tile row-major) order.
+    Returns the permutation."""
+    zb = np.asarray(z32, np.float32).view(np.uint32).astype(np.uint64)
+    key = (np.asarray(tile_id, np.uint64) << np.uint64(32)) | zb
+    return np.argsort(key, kind="stable")
+
+
+def tile_ranges(sorted_tile_ids, total_tiles):
+    """[start, end) of every global tile in the sorted entry list."""
+    t = np.asarray(sorted_tile_ids, np.int64)
+    ids = np.arange(total_tiles)
+    return np.stack([np.searchsorted(t, ids, "left"), np.searchsorted(t, ids, "right")], 1)
+
+
+def tile_grid(width, height, tile=16):
+    return (width + tile - 1) // tile, (height + tile - 1) // tile
+
+
+def view_tile_bases(sizes, tile=16):
+    """Global tile-id base of every view when views are concatenated."""
+    bases, acc = [], 0
+    for (w, h) in sizes:
+        bases.append(acc)
+        tx, ty = tile_grid(w, h, tile)
+        acc += tx * ty
+    return bases, acc
+
+
+def exclusive_scan(counts):
+    """Offsets of a concatenation: out[k] = sum_{j<k} counts[j]."""
+    c = np.asarray(counts, np.int64)
+    return np.concatenate([[0], np.cumsum(c)[:-1]]) if len(c) else c
+
+
+def ceil_log2(n: int) -> int:
+    return max(0, math.ceil(math.log2(max(n, 1))))

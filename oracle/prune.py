@@ -1,0 +1,21 @@
+"""Selection by accumulated blending weight (test infrastructure).
+
+MSv2-D (Sec. 6.1) replaces simplification by importance-based pruning: the
+importance of Gaussian i is its accumulated blending weight I_i (Sec. 3.2),
+and the least important Gaussians are removed.  The reading adopted here for
+"keep the top fraction f": keep the ceil(f N) Gaussians with the largest I_i,
+ties broken towards the lower index, and list the kept indices ascending.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def keep_top(weight_sum, frac: float) -> np.ndarray:
+    w = np.asarray(weight_sum, np.float64)
+    n = len(w)
+    k = min(n, math.ceil(frac * n))
+    order = np.lexsort((np.arange(n), -w))      # descending weight, then index
+    return np.sort(order[:k])
