@@ -1,0 +1,403 @@
+"""Throughput benchmark of the rasterizer's training step.
+
+Workload (default): 1,000,000 Gaussians (SH degree 3, clustered synthetic
+scene), 8 views of uneven sizes (2x 800x800, 3x 1280x720, 2x 1600x1063,
+1x 1920x1080) rendered and backpropagated in one batch: gs_preprocess ->
+gs_bin_sort -> gs_render_fwd -> L1 loss -> gs_render_bwd, all in libgs.so.
+
+One JSON line on rank 0.  `value` is device-resident fwd+bwd Mpixel/s over
+all ranks; `e2e` is the same step with the scene and targets copied from
+pinned host memory and the loss and gradients copied back inside the timed
+region.  `--impl reference` times the CPU oracle on a bounded sample of the
+same workload instead.  Multi-GPU runs (torchrun) render independent
+replicas: there is no data-path collective.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "fwd+bwd Mpix/s and steps/s at 1M Gaussians; serving p50/p99 ms vs one-at-a-time"
+WORKLOAD = ("batched fwd+bwd, 1M Gaussians SH3 (64-cluster + shell scene), 8 views "
+            "2x800x800 + 3x1280x720 + 2x1600x1063 + 1x1920x1080, L1 loss")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed
+def dist_setup(gpus: int):
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def reduce_max(x: float, world: int) -> float:
+    """Max over ranks (timing only)."""
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(local_units: float, local_seconds: float, world: int) -> tuple[float, float]:
+    """(total units over ranks, max seconds over ranks): whole-job throughput
+    is total / max; each rank processes the same replica workload."""
+    return local_units * world, reduce_max(local_seconds, world)
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self, device_index=0) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.close()
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            p = [x.strip() for x in line.split(",")]
+            if len(p) < 9 or p[0] != str(device_index):
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = float(p[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+# ---------------------------------------------------------------- our arm
+class Step:
+    """Resident state of the batched training step (workspaces reused)."""
+
+    def __init__(self, n: int, seed: int):
+        import torch
+        from paper_2411_12788_gb300 import raster, scenes
+        self.torch, self.raster = torch, raster
+        self.scene = scenes.cluster_scene(n, 64, seed=seed, sh_degree=3)
+        self.cams = scenes.multiview_cameras()
+        tg = scenes.target_images(self.cams, seed=1)
+        self.g = raster.GaussianTensors.from_scene(self.scene, "cuda")
+        self.target = torch.as_tensor(np.concatenate([t.reshape(-1) for t in tg])).cuda()
+        self.plan = raster.make_plan(n, self.cams)
+        self.cfg = raster.make_config(flags=raster._lib.GS_FLAG_ZERO_ACCUM)
+        self.pre_ws = torch.empty(raster.preprocess_workspace_size(self.plan), dtype=torch.uint8, device="cuda")
+        self.sort_ws = torch.empty(0, dtype=torch.uint8, device="cuda")
+        self.outs = raster.alloc_outputs(self.plan, "cuda", want=("image", "final_T", "n_contrib", "depth",
+                                                                  "imax", "weight_sum"))
+        self.loss = torch.zeros(1, device="cuda")
+        self.dL = torch.empty_like(self.outs["image"])
+        self.grads = raster.alloc_grads(self.g)
+        self.pixels = int(self.plan.total_pixels)
+
+    def run(self):
+        r = self.raster
+        r.preprocess(self.plan, self.g.struct(), self.cfg, self.pre_ws)
+        need = r.bin_sort_workspace_size(self.plan)
+        if self.sort_ws.numel() < need:
+            self.sort_ws = self.torch.empty(int(need * 1.1), dtype=self.torch.uint8, device="cuda")
+        r.bin_sort(self.plan, self.pre_ws, self.sort_ws)
+        r.render_fwd(self.plan, self.cfg, self.pre_ws, self.sort_ws, self.outs)
+        r.loss_l1(self.outs["image"], self.target, self.loss, self.dL)
+        r.render_bwd(self.plan, self.g.struct(), self.cfg, self.pre_ws, self.sort_ws, self.dL,
+                     self.outs["final_T"], self.outs["n_contrib"], self.grads)
+
+
+def kernel_times(collect=True) -> dict:
+    from paper_2411_12788_gb300 import _lib
+    import ctypes as C
+    arr = (_lib.KernelTime * 64)()
+    k = _lib.lib().gs_timing_collect(arr, 64)
+    out = {}
+    for i in range(min(k, 64)):
+        out[arr[i].name.decode()] = {"ms": arr[i].ms, "launches": int(arr[i].launches)}
+    return out
+
+
+def roofline(kt: dict, st: "Step", steps: int, peaks: dict, clocks: dict) -> dict:
+    """Roofline of the dominant kernel (largest share of the timed region)."""
+    name = max(kt, key=lambda k: kt[k]["ms"])
+    ms = kt[name]["ms"] / max(1, kt[name]["launches"])
+    E = int(st.plan.n_entries)
+    torch = st.torch
+    if name == "render_bwd":
+        # units: (pixel, entry) evaluations = sum of n_contrib; ALU-bound
+        evals = float(st.outs["n_contrib"].to(torch.int64).sum().item())
+        flops = evals * BWD_FLOPS_PER_EVAL
+        sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        ach = flops / (ms * 1e-3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "units": {"evaluations_per_launch": evals, "flops_per_evaluation": BWD_FLOPS_PER_EVAL},
+                "peak_note": f"FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled)"}
+    if name == "render_fwd":
+        evals = float(st.outs["n_contrib"].to(torch.int64).sum().item())
+        flops = evals * FWD_FLOPS_PER_EVAL
+        sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+        peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        ach = flops / (ms * 1e-3) / 1e12
+        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                "frac": ach / peak, "traffic": None,
+                "units": {"evaluations_per_launch": evals, "flops_per_evaluation": FWD_FLOPS_PER_EVAL},
+                "peak_note": f"FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled)"}
+    # HBM-bound kernels: algorithmic bytes per launch
+    I = int(st.plan.n_items)
+    per = {"tile_sort_onesweep": 16 * E, "depth_sort_onesweep": 16 * I, "duplicate": 8 * E + 20 * I,
+           "preprocess": 236 * st.g.n + 120 * I, "preprocess_backward": 236 * 2 * st.g.n + 48 * I,
+           "tile_sort_histogram": 4 * E, "ranges": 4 * E}
+    bytes_ = per.get(name, 0)
+    ach = bytes_ / (ms * 1e-3) / 1e9
+    peak = peaks.get("hbm_gbs", 6800.0)
+    return {"kernel": name, "bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "traffic": None}
+
+
+FP32_LANES = 152 * 128
+# FP32 operations per (pixel, entry) evaluation, counted from the inner loops
+# (an FMA counts 2): forward ~ q (5 FMA) + exp (2) + alpha (2) + T (2) +
+# blend of colour, depth, weight (10) + compares;  backward adds the reverse
+# transmittance, the colour recursion and the nine gradient terms.
+FWD_FLOPS_PER_EVAL = 30
+BWD_FLOPS_PER_EVAL = 80
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2411_12788_gb300 import _lib
+    L = _lib.lib()
+    st = Step(args.n, seed=0)
+    for _ in range(args.warmup):
+        st.run()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    clocks = ClockSampler()
+    clocks.start()
+    L.gs_timing_enable(1)
+    kernel_times()
+    barrier(world)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        st.run()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    kt = kernel_times()
+    L.gs_timing_enable(0)
+    ck = clocks.stop(torch.cuda.current_device())
+    sec = e0.elapsed_time(e1) / 1e3
+    units, sec_max = aggregate(st.pixels * args.steps, sec, world)
+    value = units / sec_max / 1e6
+    total_kms = sum(v["ms"] for v in kt.values())
+    for v in kt.values():
+        v["share"] = v["ms"] / total_kms if total_kms else 0.0
+        v["ms_per_launch"] = v["ms"] / max(1, v["launches"])
+    launches = sum(v["launches"] for v in kt.values())
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        peaks = {"hbm_gbs": 6800.0, "note": "fallback"}
+    rl = roofline(kt, st, args.steps, peaks, ck)
+
+    e2e = None
+    if not args.no_e2e:
+        e2e = run_e2e(st, args, world)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(st.scene, st.cams)
+    line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": sec_max * 1e3 / args.steps,
+            "steps_per_s": args.steps / sec_max * world, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "gaussians": args.n, "views": len(st.cams),
+                       "pixels_per_step": st.pixels, "entries_per_step": int(st.plan.n_entries),
+                       "l2": "inputs larger than L2 (236 MB scene, 1.5 GB workspace)",
+                       "parallelism": f"replicas x{world}"},
+            "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
+            "clocks": ck, "kernels": kt}
+    return line
+
+
+def run_e2e(st: Step, args, world) -> dict:
+    """Same step with host buffers: H2D of the scene and targets from pinned
+    memory, the step, D2H of the loss and the gradients, every step."""
+    import torch
+    names = ("means", "scales", "rotations", "opacities", "sh")
+    host_in = {k: getattr(st.g, k).cpu().pin_memory() for k in names}
+    host_tg = st.target.cpu().pin_memory()
+    host_out = {k: v.cpu().pin_memory() for k, v in st.grads.items()}
+    host_loss = torch.zeros(1).pin_memory()
+    h2d = sum(t.numel() * 4 for t in host_in.values()) + host_tg.numel() * 4
+    d2h = sum(t.numel() * 4 for t in host_out.values()) + 4
+
+    def step():
+        for k in names:
+            getattr(st.g, k).copy_(host_in[k], non_blocking=True)
+        st.target.copy_(host_tg, non_blocking=True)
+        st.run()
+        for k, v in st.grads.items():
+            host_out[k].copy_(v, non_blocking=True)
+        host_loss.copy_(st.loss, non_blocking=True)
+
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    barrier(world)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    sec = e0.elapsed_time(e1) / 1e3
+    units, sec_max = aggregate(st.pixels * args.steps, sec, world)
+    return {"value": units / sec_max / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": sec_max * 1e3 / args.steps}
+
+
+# ---------------------------------------------------------------- oracle arm
+def oracle_sample_step(scene, cam, pix):
+    """fwd+bwd of the float64 oracle for the listed pixels of one view."""
+    import torch
+    from oracle import project as OP, render as OR
+    params = [torch.tensor(np.asarray(a, np.float64), requires_grad=True)
+              for a in (scene.means, scene.scales, scene.rotations, scene.opacities, scene.sh)]
+    pr = OP.project(*params, scene.sh_degree, cam)
+    out = OR.render_view(pr, cam, pix=pix, want_depth=True)
+    out["colour"].sum().backward()
+    return len(pix)
+
+
+def cpu_baseline(scene, cams, pixels_per_view=4, views=(0,)) -> dict:
+    import torch
+    rng = np.random.default_rng(11)
+    t0 = time.perf_counter()
+    done = 0
+    for v in views:
+        cam = cams[v]
+        pix = np.stack([rng.integers(0, cam.width, pixels_per_view),
+                        rng.integers(0, cam.height, pixels_per_view)], 1)
+        done += oracle_sample_step(scene, cam, pix)
+    sec = time.perf_counter() - t0
+    return {"value": done / sec / 1e6, "unit": "Mpix/s", "cores": torch.get_num_threads(), "kind": "oracle",
+            "sample": f"float64 oracle fwd+bwd of {done} random pixels of view {list(views)} over all "
+                      f"{scene.n} Gaussians (projection of every Gaussian included), {sec:.1f} s"}
+
+
+def run_reference(args, rank, world):
+    from paper_2411_12788_gb300 import scenes
+    if rank != 0:
+        return None
+    import torch
+    scene = scenes.cluster_scene(args.n, 64, seed=0, sh_degree=3)
+    cams = scenes.multiview_cameras()
+    rng = np.random.default_rng(11)
+    per_step = 2
+
+    def one(k):
+        cam = cams[k % len(cams)]
+        pix = np.stack([rng.integers(0, cam.width, per_step), rng.integers(0, cam.height, per_step)], 1)
+        return oracle_sample_step(scene, cam, pix)
+    for k in range(args.warmup):
+        one(k)
+    t0 = time.perf_counter()
+    done = 0
+    for k in range(args.steps):
+        done += one(k)
+    sec = time.perf_counter() - t0
+    value = done / sec / 1e6
+    cpu = {"value": value, "unit": "Mpix/s", "cores": torch.get_num_threads(), "kind": "oracle",
+           "sample": f"each step: float64 oracle fwd+bwd of {per_step} random pixels of one view (round robin "
+                     f"over the 8 views) over all {args.n} Gaussians"}
+    return {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "gaussians": args.n},
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world = dist_setup(args.gpus)
+    if args.impl == "reference":
+        line = run_reference(args, rank, world)
+    else:
+        line = run_ours(args, rank, world)
+    if rank == 0 and line is not None:
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,271 @@
+/*
+ * gs.h - C ABI of the tile-based differentiable Gaussian-splatting rasterizer.
+ *
+ * The rasterizer is the hot path of the 3D Gaussian Splatting method that
+ * Mini-Splatting2 (arXiv 2411.12788) optimizes: Gaussians are projected to
+ * 2-D by the local affine (EWA) approximation and coloured by spherical
+ * harmonics (Sec. 3.1), depth-ordered per 16x16 tile, and alpha-blended front
+ * to back (Eq. 1).  The forward pass also emits what the paper's
+ * reorganisation and simplification read: the rendered index
+ * i_max = argmax_i w_i and the midpoint depth d^mid_{i_max} (Eq. 2, Sec. 4.1),
+ * the blended depth (Sec. 4.1), the per-Gaussian accumulated blending weight
+ * I_i (Sec. 3.2; used for pruning, sampling and visibility, Sec. 4.2, 5.2)
+ * and the maximum-contribution area S_i (Sec. 4.1, blur split).
+ *
+ * Conventions
+ *  - All arrays named "device" live in GPU memory of the current device and
+ *    are owned by the caller; the library never allocates or frees them.
+ *    Workspaces are caller-allocated byte buffers whose sizes come from the
+ *    *_workspace_size() queries; they must be 256-byte aligned.
+ *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream) except gs_preprocess, which reads back one 8-byte
+ *    count (the number of tile entries) and therefore synchronises `stream`.
+ *  - Every call returns a gs_status; arguments are validated on the host
+ *    before any launch (GS_ERR_INVALID_ARG).  Device-side checks (entry
+ *    overflow, a radix-sort look-back that exceeded its spin budget) set a
+ *    status word in the preprocess workspace that gs_device_status() reads.
+ *  - Floating point is FP32 throughout.  Gaussian attributes are the
+ *    activated values: linear scales, a (w,x,y,z) quaternion that need not be
+ *    unit (it is normalised inside), opacity in (0,1), raw SH coefficients.
+ *  - Camera space: p_c = R p + t, x right, y down, z forward; pixel (u, v)
+ *    is sampled at its centre (u + 0.5, v + 0.5).
+ */
+#ifndef GS_H
+#define GS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GS_TILE 16          /* tile edge in pixels */
+#define GS_MAX_VIEWS 64     /* views (or serving requests) per plan */
+#define GS_MAX_SH_DEGREE 3
+
+typedef enum gs_status {
+  GS_OK = 0,
+  GS_ERR_INVALID_ARG = 1,   /* bad pointer, size, camera or degree */
+  GS_ERR_CAPACITY = 2,      /* a workspace is smaller than required */
+  GS_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+  GS_ERR_TIMEOUT = 4,       /* a device-side wait exceeded its budget */
+  GS_ERR_DEVICE_CHECK = 5   /* a device-side consistency check failed */
+} gs_status;
+
+/* Pinhole camera.  R is the row-major world->camera rotation. */
+typedef struct gs_camera {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  int32_t width, height;
+} gs_camera;
+
+/* Numeric conventions (defaults in brackets; gs_config_default fills them).
+ *  znear     [0.2]   cull Gaussians with camera z <= znear
+ *  lowpass   [0.3]   px^2 added to the diagonal of the 2-D covariance
+ *  clamp     [1.3]   Jacobian evaluated at x/z, y/z clamped to +-clamp*tan(fov/2)
+ *  alpha_max [0.99]  alpha = min(alpha_max, o * G)
+ *  alpha_min [1/255] an entry with alpha < alpha_min is skipped
+ *  t_min     [1e-4]  stop before the entry that would take T below t_min
+ *  bg        [0,0,0] background, added as T_final * bg
+ *  flags             GS_FLAG_* bits */
+typedef struct gs_config {
+  float znear, lowpass, clamp, alpha_max, alpha_min, t_min;
+  float bg[3];
+  uint32_t flags;
+} gs_config;
+
+/* gs_render_fwd / gs_render_bwd zero their accumulated outputs first */
+#define GS_FLAG_ZERO_ACCUM 1u
+
+/* Gaussian attributes, device, FP32, structure of arrays:
+ *   means [n][3], scales [n][3], rotations [n][4] (w,x,y,z), opacities [n],
+ *   sh [n][sh_coeffs][3] (band-major, m = -l..l, RGB innermost).
+ * Only the first (sh_degree+1)^2 coefficients of each row are read. */
+typedef struct gs_scene {
+  const float* means;
+  const float* scales;
+  const float* rotations;
+  const float* opacities;
+  const float* sh;
+  int64_t n;
+  int32_t sh_degree;        /* 0..3 */
+  int32_t sh_coeffs;        /* row length of sh, >= (sh_degree+1)^2 */
+} gs_scene;
+
+/* Host-side plan: the batch of views and the workspace layout.  Filled by
+ * gs_plan_init (host only, no GPU work) and completed by gs_preprocess, which
+ * stores the tile-entry count.  Items are (view, Gaussian) pairs numbered
+ * item = view * n + gaussian; per-pixel outputs of view v start at
+ * pixel_base[v] (row-major), the planar image of view v at 3 * pixel_base[v]. */
+typedef struct gs_plan {
+  int64_t n;
+  int64_t n_items;
+  int64_t total_pixels;
+  int64_t n_entries;        /* set by gs_preprocess */
+  int32_t n_views;
+  int32_t total_tiles;
+  int32_t sort_bits;        /* bits of the global tile id */
+  int32_t reserved;
+  gs_camera cams[GS_MAX_VIEWS];
+  int32_t tile_base[GS_MAX_VIEWS + 1];
+  int64_t pixel_base[GS_MAX_VIEWS + 1];
+} gs_plan;
+
+/* Forward outputs, device.  image and final_T / n_contrib are required (the
+ * backward pass reads the last two); the rest may be NULL.  The per-view
+ * per-Gaussian arrays are indexed by item and ACCUMULATED (+=). */
+typedef struct gs_fwd_outputs {
+  float* image;             /* [3 * total_pixels] planar per view: c(x) + T bg (Eq. 1) */
+  float* final_T;           /* [total_pixels] transmittance after the last blend */
+  uint32_t* n_contrib;      /* [total_pixels] list position of the last blended entry + 1 */
+  int32_t* imax;            /* [total_pixels] i_max (Gaussian index) or -1 (Eq. 2) */
+  float* wmax;              /* [total_pixels] w_{i_max}, 0 if none */
+  float* depth;             /* [total_pixels] d^mid of i_max (Eq. 2), 0 if none */
+  float* depth_blend;       /* [total_pixels] sum_i w_i z_i (Sec. 4.1) */
+  float* weight_sum;        /* [n_items] += sum over the view's pixels of w_i (Sec. 3.2) */
+  uint32_t* max_area;       /* [n_items] += #pixels with i_max = i (S_i, Sec. 4.1) */
+} gs_fwd_outputs;
+
+/* Gradients, device, ACCUMULATED (+=) over views, same layouts as gs_scene;
+ * d_sh has sh_coeffs columns (unused ones are left untouched).
+ * d_mean2d_abs (nullable, [n]) += |dL/d mean2d| per view (3DGS densification
+ * statistic). */
+typedef struct gs_grads {
+  float* d_means;
+  float* d_scales;
+  float* d_rotations;
+  float* d_opacities;
+  float* d_sh;
+  float* d_mean2d_abs;
+} gs_grads;
+
+/* ---- plan and sizes (host only) ------------------------------------- */
+void gs_config_default(gs_config* cfg);
+
+/* Fills `plan` for n Gaussians seen by n_views cameras (host array).
+ * Errors: GS_ERR_INVALID_ARG for n < 0, n_views outside 1..GS_MAX_VIEWS,
+ * non-positive sizes or focal lengths, or more than 2^31 tiles or items. */
+gs_status gs_plan_init(gs_plan* plan, int64_t n, const gs_camera* cams, int32_t n_views);
+
+/* Bytes of the preprocess workspace (per-item projected state, depth sort,
+ * scan, and the backward pass's per-item 2-D gradients). */
+size_t gs_preprocess_workspace_size(const gs_plan* plan);
+
+/* Bytes of the sort workspace for plan->n_entries entries (call after
+ * gs_preprocess): keys and values double-buffered, tile ranges, radix
+ * histograms and look-back state. */
+size_t gs_bin_sort_workspace_size(const gs_plan* plan);
+
+/* ---- the four hot-path calls ----------------------------------------- */
+
+/* Per (view, Gaussian): cull (z <= znear, mask == 0, opacity < alpha_min),
+ * covariance R(q) diag(s^2) R(q)^T, EWA projection J W Sigma W^T J^T +
+ * lowpass I, conic, projected centre, SH colour max(0, sum sh Y + 0.5) in
+ * the direction from the camera centre (Sec. 3.1), the midpoint-depth frame
+ * (Sec. 4.1), and the exact number of touched tiles: tile T is touched iff
+ * min over its pixel-centre rectangle of d^T conic d <= 2 ln(o / alpha_min).
+ * Then sorts the items by the float32 depth of their centres (stable, ties
+ * by item) and scans the tile counts in that order; stores the total in
+ * plan->n_entries (one device->host read, synchronises `stream`).
+ * mask: device [n_items] bytes or NULL (view-dependent culling, Sec. 5.2).
+ * cfg is read on the host. */
+gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* cfg,
+                        const uint8_t* mask, void* pre_ws, size_t pre_ws_bytes,
+                        void* stream);
+
+/* Emits one (global tile id, item) entry per touched tile in depth order,
+ * radix-sorts the entries by tile id (stable, so each tile's list stays in
+ * (depth, item) order) and computes each tile's [start, end) range.
+ * Errors: GS_ERR_CAPACITY if sort_ws_bytes < gs_bin_sort_workspace_size. */
+gs_status gs_bin_sort(const gs_plan* plan, void* pre_ws, void* sort_ws,
+                      size_t sort_ws_bytes, void* stream);
+
+/* Front-to-back alpha blending of every tile (Eq. 1) with alpha =
+ * min(alpha_max, o G), skip alpha < alpha_min, stop before T (1 - alpha) <
+ * t_min; writes the outputs listed in gs_fwd_outputs. */
+gs_status gs_render_fwd(const gs_plan* plan, const gs_config* cfg, void* pre_ws,
+                        const void* sort_ws, const gs_fwd_outputs* out, void* stream);
+
+/* Gradients of a loss L with respect to the Gaussian attributes, given
+ * dL/d image (device, [3 * total_pixels], planar like the image) and the
+ * forward's final_T and n_contrib: reverse replay of Eq. 1 per pixel, then
+ * the chain rule through the projection and SH colour.  The clamps pass no
+ * gradient (alpha at alpha_max, colour at 0, the clamped Jacobian
+ * coordinate); the thresholds are constants.  The scene must be the one
+ * passed to gs_preprocess.  pre_ws is also written (its 2-D gradient
+ * scratch). */
+gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_config* cfg,
+                        void* pre_ws, const void* sort_ws, const float* dL_dimage,
+                        const float* final_T, const uint32_t* n_contrib,
+                        const gs_grads* grads, void* stream);
+
+/* ---- training-step helpers ------------------------------------------- */
+
+/* Mean absolute error over `count` elements and its gradient (the L1 term
+ * of the 3DGS photometric objective the paper trains with, Sec. 6.2):
+ * *loss (device scalar) = mean |image - target|, dL_dimage = sign(image -
+ * target) / count.  *loss is overwritten. */
+gs_status gs_loss_l1(const float* image, const float* target, int64_t count,
+                     float* loss, float* dL_dimage, void* stream);
+
+/* ---- inspection --------------------------------------------------------- */
+
+/* Device pointers into a preprocess workspace after gs_preprocess, for tests
+ * and tools (read-only use).  Entries of culled items (tiles == 0) are not
+ * written and hold stale values. */
+typedef struct gs_preprocess_view {
+  const float* xy_tau_z;        /* [n_items][4] centre x, y, tau = 2 ln(o/alpha_min), z */
+  const float* conic_o;         /* [n_items][4] A, B, C, opacity */
+  const float* rgb;             /* [n_items][4] r, g, b, 0 */
+  const uint32_t* tiles;        /* [n_items] touched-tile count, 0 if culled */
+  const uint32_t* rect;         /* [n_items][2] (tx0 | ty0 << 16, tx1 | ty1 << 16) */
+  const uint32_t* sorted_items; /* [n_items] items in (float32 z, item) order, culled last */
+  const uint32_t* offsets;      /* [n_items] exclusive scan of tiles in that order */
+} gs_preprocess_view;
+gs_status gs_inspect_preprocess(const gs_plan* plan, const void* pre_ws, gs_preprocess_view* out);
+
+/* Device pointers into a sort workspace after gs_bin_sort. */
+typedef struct gs_sort_view {
+  const uint32_t* tile_ids;     /* [n_entries] global tile id, ascending */
+  const uint32_t* items;        /* [n_entries] item of each entry */
+  const uint32_t* ranges;       /* [total_tiles][2] [start, end) of each tile */
+} gs_sort_view;
+gs_status gs_inspect_sort(const gs_plan* plan, const void* sort_ws, gs_sort_view* out);
+
+/* ---- timing --------------------------------------------------------------- */
+
+/* Opt-in per-kernel timing: while enabled, every kernel launch of the library
+ * is bracketed by CUDA events recorded on its launch stream (events come from
+ * a pool created by the first enable; single-threaded use).  gs_timing_collect
+ * waits for the recorded events, writes up to max_out per-kernel totals since
+ * the previous collect (name, summed milliseconds, launches) and returns the
+ * number of distinct kernels.  Names are static strings. */
+typedef struct gs_kernel_time {
+  const char* name;
+  double ms;
+  int64_t launches;
+} gs_kernel_time;
+gs_status gs_timing_enable(int on);
+int gs_timing_collect(gs_kernel_time* out, int max_out);
+
+/* ---- status ------------------------------------------------------------ */
+
+/* Reads (and clears) the device status word of a preprocess workspace;
+ * synchronises `stream`.  Returns GS_OK, GS_ERR_TIMEOUT or GS_ERR_DEVICE_CHECK. */
+gs_status gs_device_status(const gs_plan* plan, void* pre_ws, void* stream);
+
+const char* gs_status_string(gs_status s);
+
+/* sizeof of the ABI structs, so bindings can check their layouts */
+size_t gs_sizeof_plan(void);
+size_t gs_sizeof_camera(void);
+size_t gs_sizeof_config(void);
+size_t gs_sizeof_scene(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GS_H */

@@ -204,3 +204,22 @@ def render(scene, cams, cfg: OracleConfig | None = None, masks=None, pix=None,
 def planar(colour: torch.Tensor, cam) -> torch.Tensor:
     """[H*W, 3] row-major pixel colours -> planar [3, H, W]."""
     return colour.reshape(cam.height, cam.width, 3).permute(2, 0, 1)
+
+
+def contributors(proj: dict, pix, alpha_min: float, slack: float = 1e-3) -> np.ndarray:
+    """Indices of the Gaussians whose o*G reaches (1 - slack) * alpha_min at
+    any of the given (u, v) pixels (no depth order, no termination): a
+    superset of the Gaussians that can influence those pixels."""
+    pix = np.asarray(pix).reshape(-1, 2)
+    if len(pix) == 0:
+        return np.zeros(0, np.int64)
+    valid = proj["valid"].numpy()
+    m = proj["mean2d"].detach().numpy()
+    c = proj["conic"].detach().numpy()
+    o = proj["opacity"].detach().numpy()
+    hit = np.zeros(len(m), bool)
+    for u, v in pix:
+        dx, dy = u + 0.5 - m[:, 0], v + 0.5 - m[:, 1]
+        q = c[:, 0] * dx * dx + 2 * c[:, 1] * dx * dy + c[:, 2] * dy * dy
+        hit |= valid & (o * np.exp(-0.5 * q) >= (1.0 - slack) * alpha_min)
+    return np.nonzero(hit)[0]

@@ -1,0 +1,365 @@
+// C ABI of the rasterizer: plans, workspace layouts, argument validation and
+// the launch sequences of gs_preprocess / gs_bin_sort / gs_render_fwd /
+// gs_render_bwd.  No allocation happens here: every buffer is the caller's.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace gs {
+namespace {
+
+PreLayout pre_layout(const gs_plan& p) {
+  PreLayout L;
+  const size_t m = (size_t)std::max<int64_t>(p.n_items, 1);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  L.views = take(sizeof(ViewDev) * GS_MAX_VIEWS);
+  L.status = take(16);          // status word (u32) then n_entries (u64) at +8
+  L.n_entries = L.status + 8;
+  L.xy_tau_z = take(16 * m);
+  L.conic_o = take(16 * m);
+  L.rgb = take(16 * m);
+  L.depth_frame = take(48 * m);
+  L.rect = take(8 * m);
+  L.tiles = take(4 * m);
+  L.depth_key = take(4 * m);
+  L.sort_keys_alt = take(4 * m);
+  L.sort_vals = take(4 * m);
+  L.sort_vals_alt = take(4 * m);
+  L.sorted_items = L.sort_vals;
+  L.offsets = take(4 * m);
+  L.scan_blocks = take(scan_block_bytes((int64_t)m));
+  L.radix_scratch = take(radix_scratch_bytes((int64_t)m, 32));
+  L.grad2d = take(48 * m);
+  L.total = o;
+  return L;
+}
+
+SortLayout sort_layout(const gs_plan& p) {
+  SortLayout L;
+  const size_t e = (size_t)std::max<int64_t>(p.n_entries, 1);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t at = o;
+    o = align_up(o + bytes);
+    return at;
+  };
+  L.keys = take(4 * e);
+  L.keys_alt = take(4 * e);
+  L.vals = take(4 * e);
+  L.vals_alt = take(4 * e);
+  L.ranges = take(8 * (size_t)std::max(p.total_tiles, 1));
+  L.radix_scratch = take(radix_scratch_bytes((int64_t)e, std::max(p.sort_bits, 1)));
+  L.total = o;
+  return L;
+}
+
+template <class T>
+T* at(void* base, size_t off) {
+  return reinterpret_cast<T*>(static_cast<char*>(base) + off);
+}
+template <class T>
+const T* at(const void* base, size_t off) {
+  return reinterpret_cast<const T*>(static_cast<const char*>(base) + off);
+}
+
+ItemState item_state(void* ws, const PreLayout& L) {
+  ItemState s;
+  s.xy_tau_z = at<float4>(ws, L.xy_tau_z);
+  s.conic_o = at<float4>(ws, L.conic_o);
+  s.rgb = at<float4>(ws, L.rgb);
+  s.depth_frame = at<float4>(ws, L.depth_frame);
+  s.rect = at<uint2>(ws, L.rect);
+  s.tiles = at<uint32_t>(ws, L.tiles);
+  s.depth_key = at<uint32_t>(ws, L.depth_key);
+  return s;
+}
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+gs_status cuda_status(cudaError_t e) { return e == cudaSuccess ? GS_OK : GS_ERR_CUDA; }
+
+bool valid_config(const gs_config* c) {
+  return c && c->znear > 0.f && c->lowpass >= 0.f && c->clamp > 0.f && c->alpha_max > 0.f &&
+         c->alpha_max < 1.f && c->alpha_min > 0.f && c->alpha_min < c->alpha_max && c->t_min > 0.f &&
+         c->t_min < 1.f;
+}
+
+bool valid_scene(const gs_plan* p, const gs_scene* s) {
+  if (!s || !s->means || !s->scales || !s->rotations || !s->opacities || !s->sh) return s && p->n == 0 && s->n == 0;
+  if (s->n != p->n) return false;
+  if (s->sh_degree < 0 || s->sh_degree > GS_MAX_SH_DEGREE) return false;
+  if (s->sh_coeffs < (s->sh_degree + 1) * (s->sh_degree + 1)) return false;
+  if (!aligned(s->rotations, 16) || !aligned(s->means, 4) || !aligned(s->scales, 4) || !aligned(s->sh, 4))
+    return false;
+  return true;
+}
+
+bool valid_plan(const gs_plan* p) {
+  return p && p->n >= 0 && p->n_views >= 1 && p->n_views <= GS_MAX_VIEWS && p->n_items == p->n * p->n_views;
+}
+
+}  // namespace
+}  // namespace gs
+
+using namespace gs;
+
+extern "C" {
+
+void gs_config_default(gs_config* c) {
+  if (!c) return;
+  c->znear = 0.2f;
+  c->lowpass = 0.3f;
+  c->clamp = 1.3f;
+  c->alpha_max = 0.99f;
+  c->alpha_min = 1.0f / 255.0f;
+  c->t_min = 1e-4f;
+  c->bg[0] = c->bg[1] = c->bg[2] = 0.f;
+  c->flags = 0u;
+}
+
+gs_status gs_plan_init(gs_plan* plan, int64_t n, const gs_camera* cams, int32_t n_views) {
+  if (!plan || !cams || n < 0 || n_views < 1 || n_views > GS_MAX_VIEWS) return GS_ERR_INVALID_ARG;
+  memset(plan, 0, sizeof(*plan));
+  plan->n = n;
+  plan->n_views = n_views;
+  plan->n_items = n * n_views;
+  if (plan->n_items >= (int64_t)1 << 30) return GS_ERR_INVALID_ARG;   // radix sort counts are 30-bit
+  int64_t tiles = 0, pixels = 0;
+  for (int v = 0; v < n_views; ++v) {
+    const gs_camera& c = cams[v];
+    if (c.width <= 0 || c.height <= 0 || c.width > 65535 * kTile || c.height > 65535 * kTile) return GS_ERR_INVALID_ARG;
+    if (!(c.fx > 0.f) || !(c.fy > 0.f)) return GS_ERR_INVALID_ARG;
+    plan->cams[v] = c;
+    plan->tile_base[v] = (int32_t)tiles;
+    plan->pixel_base[v] = pixels;
+    tiles += (int64_t)ceil_div(c.width, kTile) * ceil_div(c.height, kTile);
+    pixels += (int64_t)c.width * c.height;
+    if (tiles >= ((int64_t)1 << 31)) return GS_ERR_INVALID_ARG;
+  }
+  plan->tile_base[n_views] = (int32_t)tiles;
+  plan->pixel_base[n_views] = pixels;
+  plan->total_tiles = (int32_t)tiles;
+  plan->total_pixels = pixels;
+  int bits = 1;
+  while (((int64_t)1 << bits) < tiles) ++bits;
+  plan->sort_bits = bits;
+  plan->n_entries = -1;
+  return GS_OK;
+}
+
+size_t gs_preprocess_workspace_size(const gs_plan* plan) {
+  if (!valid_plan(plan)) return 0;
+  return pre_layout(*plan).total;
+}
+
+size_t gs_bin_sort_workspace_size(const gs_plan* plan) {
+  if (!valid_plan(plan) || plan->n_entries < 0) return 0;
+  return sort_layout(*plan).total;
+}
+
+gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* cfg, const uint8_t* mask,
+                        void* pre_ws, size_t pre_ws_bytes, void* stream_) {
+  if (!valid_plan(plan) || !valid_config(cfg) || !valid_scene(plan, scene)) return GS_ERR_INVALID_ARG;
+  if (!pre_ws || !aligned(pre_ws, 256)) return GS_ERR_INVALID_ARG;
+  const PreLayout L = pre_layout(*plan);
+  if (pre_ws_bytes < L.total) return GS_ERR_CAPACITY;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+
+  ViewDev views[GS_MAX_VIEWS];
+  memset(views, 0, sizeof(views));
+  for (int v = 0; v < plan->n_views; ++v) {
+    const gs_camera& c = plan->cams[v];
+    ViewDev& V = views[v];
+    memcpy(V.R, c.R, sizeof(V.R));
+    memcpy(V.t, c.t, sizeof(V.t));
+    V.fx = c.fx;
+    V.fy = c.fy;
+    V.cx = c.cx;
+    V.cy = c.cy;
+    V.limx = cfg->clamp * (0.5f * (float)c.width / c.fx);
+    V.limy = cfg->clamp * (0.5f * (float)c.height / c.fy);
+    for (int k = 0; k < 3; ++k) V.campos[k] = -(c.R[k] * c.t[0] + c.R[3 + k] * c.t[1] + c.R[6 + k] * c.t[2]);
+    V.width = c.width;
+    V.height = c.height;
+    V.tiles_x = ceil_div(c.width, kTile);
+    V.tiles_y = ceil_div(c.height, kTile);
+    V.tile_base = plan->tile_base[v];
+    V.pixel_base = plan->pixel_base[v];
+  }
+  cudaError_t e = cudaMemcpyAsync(at<ViewDev>(pre_ws, L.views), views, sizeof(ViewDev) * plan->n_views,
+                                  cudaMemcpyHostToDevice, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(at<char>(pre_ws, L.status), 0, 16, stream);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if (plan->n_items == 0) {
+    plan->n_entries = 0;
+    return cuda_status(cudaStreamSynchronize(stream));
+  }
+  const ItemState st = item_state(pre_ws, L);
+  uint32_t* status = at<uint32_t>(pre_ws, L.status);
+  e = launch_preprocess(*scene, at<ViewDev>(pre_ws, L.views), plan->n_views, mask, *cfg, st, stream);
+  if (e == cudaSuccess) e = launch_iota(at<uint32_t>(pre_ws, L.sort_vals), plan->n_items, stream);
+  if (e == cudaSuccess)
+    e = radix_sort_pairs(st.depth_key, at<uint32_t>(pre_ws, L.sort_keys_alt), at<uint32_t>(pre_ws, L.sort_vals),
+                         at<uint32_t>(pre_ws, L.sort_vals_alt), plan->n_items, 32,
+                         at<void>(pre_ws, L.radix_scratch), status, stream, "depth");
+  if (e == cudaSuccess)
+    e = gather_exclusive_scan(st.tiles, at<uint32_t>(pre_ws, L.sorted_items), at<uint32_t>(pre_ws, L.offsets),
+                              plan->n_items, at<uint64_t>(pre_ws, L.scan_blocks),
+                              at<unsigned long long>(pre_ws, L.n_entries), stream);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  uint64_t head[2];
+  e = cudaMemcpyAsync(head, at<char>(pre_ws, L.status), 16, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  const uint32_t st_word = (uint32_t)(head[0] & 0xffffffffu);
+  if (st_word & kStatusTimeout) return GS_ERR_TIMEOUT;
+  if (head[1] >= ((uint64_t)1 << 30)) return GS_ERR_CAPACITY;    // entries beyond the sort's range
+  plan->n_entries = (int64_t)head[1];
+  return GS_OK;
+}
+
+gs_status gs_bin_sort(const gs_plan* plan, void* pre_ws, void* sort_ws, size_t sort_ws_bytes, void* stream_) {
+  if (!valid_plan(plan) || plan->n_entries < 0 || !pre_ws || !sort_ws || !aligned(sort_ws, 256))
+    return GS_ERR_INVALID_ARG;
+  const PreLayout L = pre_layout(*plan);
+  const SortLayout S = sort_layout(*plan);
+  if (sort_ws_bytes < S.total) return GS_ERR_CAPACITY;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const ItemState st = item_state(pre_ws, L);
+  uint32_t* status = at<uint32_t>(pre_ws, L.status);
+  uint32_t* keys = at<uint32_t>(sort_ws, S.keys);
+  uint32_t* vals = at<uint32_t>(sort_ws, S.vals);
+  cudaError_t e = cudaSuccess;
+  if (plan->n_entries > 0) {
+    e = launch_duplicate(at<ViewDev>(pre_ws, L.views), plan->n_views, plan->n_items, plan->n,
+                         at<uint32_t>(pre_ws, L.sorted_items), at<uint32_t>(pre_ws, L.offsets), st, keys, vals,
+                         status, stream);
+    if (e == cudaSuccess)
+      e = radix_sort_pairs(keys, at<uint32_t>(sort_ws, S.keys_alt), vals, at<uint32_t>(sort_ws, S.vals_alt),
+                           plan->n_entries, plan->sort_bits, at<void>(sort_ws, S.radix_scratch), status, stream,
+                           "tile");
+  }
+  if (e == cudaSuccess) e = launch_ranges(keys, plan->n_entries, at<uint2>(sort_ws, S.ranges), plan->total_tiles, stream);
+  return cuda_status(e);
+}
+
+gs_status gs_render_fwd(const gs_plan* plan, const gs_config* cfg, void* pre_ws, const void* sort_ws,
+                        const gs_fwd_outputs* out, void* stream_) {
+  if (!valid_plan(plan) || !valid_config(cfg) || plan->n_entries < 0 || !pre_ws || !sort_ws || !out)
+    return GS_ERR_INVALID_ARG;
+  if (!out->image || !out->final_T || !out->n_contrib) return GS_ERR_INVALID_ARG;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const PreLayout L = pre_layout(*plan);
+  const SortLayout S = sort_layout(*plan);
+  cudaError_t e = cudaSuccess;
+  if (cfg->flags & GS_FLAG_ZERO_ACCUM) {
+    if (out->weight_sum) e = cudaMemsetAsync(out->weight_sum, 0, 4 * (size_t)plan->n_items, stream);
+    if (e == cudaSuccess && out->max_area) e = cudaMemsetAsync(out->max_area, 0, 4 * (size_t)plan->n_items, stream);
+    if (e != cudaSuccess) return GS_ERR_CUDA;
+  }
+  e = launch_render_fwd(at<ViewDev>(pre_ws, L.views), plan->n_views, plan->n, plan->total_tiles,
+                        at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals), item_state(pre_ws, L), *cfg,
+                        *out, stream);
+  return cuda_status(e);
+}
+
+gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_config* cfg, void* pre_ws,
+                        const void* sort_ws, const float* dL_dimage, const float* final_T,
+                        const uint32_t* n_contrib, const gs_grads* g, void* stream_) {
+  if (!valid_plan(plan) || !valid_config(cfg) || !valid_scene(plan, scene) || plan->n_entries < 0 || !pre_ws ||
+      !sort_ws || !dL_dimage || !final_T || !n_contrib || !g)
+    return GS_ERR_INVALID_ARG;
+  if (!g->d_means || !g->d_scales || !g->d_rotations || !g->d_opacities || !g->d_sh) return GS_ERR_INVALID_ARG;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const PreLayout L = pre_layout(*plan);
+  const SortLayout S = sort_layout(*plan);
+  const int64_t n = plan->n;
+  cudaError_t e = cudaMemsetAsync(at<char>(pre_ws, L.grad2d), 0, 48 * (size_t)plan->n_items, stream);
+  if (e == cudaSuccess && (cfg->flags & GS_FLAG_ZERO_ACCUM)) {
+    e = cudaMemsetAsync(g->d_means, 0, 12 * (size_t)n, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_scales, 0, 12 * (size_t)n, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_rotations, 0, 16 * (size_t)n, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_opacities, 0, 4 * (size_t)n, stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_sh, 0, 12 * (size_t)n * scene->sh_coeffs, stream);
+    if (e == cudaSuccess && g->d_mean2d_abs) e = cudaMemsetAsync(g->d_mean2d_abs, 0, 4 * (size_t)n, stream);
+  }
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  const ItemState st = item_state(pre_ws, L);
+  float4* grad2d = at<float4>(pre_ws, L.grad2d);
+  e = launch_render_bwd(at<ViewDev>(pre_ws, L.views), plan->n_views, n, plan->total_tiles,
+                        at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals), st, *cfg, dL_dimage, final_T,
+                        n_contrib, grad2d, stream);
+  if (e == cudaSuccess)
+    e = launch_preprocess_backward(*scene, at<ViewDev>(pre_ws, L.views), plan->n_views, *cfg, st.tiles, grad2d, *g,
+                                   stream);
+  return cuda_status(e);
+}
+
+gs_status gs_loss_l1(const float* image, const float* target, int64_t count, float* loss, float* dL_dimage,
+                     void* stream) {
+  if (!image || !target || !loss || !dL_dimage || count < 0) return GS_ERR_INVALID_ARG;
+  return cuda_status(launch_loss_l1(image, target, count, loss, dL_dimage, static_cast<cudaStream_t>(stream)));
+}
+
+gs_status gs_device_status(const gs_plan* plan, void* pre_ws, void* stream_) {
+  if (!valid_plan(plan) || !pre_ws) return GS_ERR_INVALID_ARG;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const PreLayout L = pre_layout(*plan);
+  uint32_t word = 0;
+  cudaError_t e = cudaMemcpyAsync(&word, at<char>(pre_ws, L.status), 4, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(at<char>(pre_ws, L.status), 0, 4, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  if (word & kStatusTimeout) return GS_ERR_TIMEOUT;
+  if (word & kStatusEntryMismatch) return GS_ERR_DEVICE_CHECK;
+  return GS_OK;
+}
+
+gs_status gs_inspect_preprocess(const gs_plan* plan, const void* pre_ws, gs_preprocess_view* out) {
+  if (!valid_plan(plan) || !pre_ws || !out) return GS_ERR_INVALID_ARG;
+  const PreLayout L = pre_layout(*plan);
+  out->xy_tau_z = at<float>(pre_ws, L.xy_tau_z);
+  out->conic_o = at<float>(pre_ws, L.conic_o);
+  out->rgb = at<float>(pre_ws, L.rgb);
+  out->tiles = at<uint32_t>(pre_ws, L.tiles);
+  out->rect = at<uint32_t>(pre_ws, L.rect);
+  out->sorted_items = at<uint32_t>(pre_ws, L.sorted_items);
+  out->offsets = at<uint32_t>(pre_ws, L.offsets);
+  return GS_OK;
+}
+
+gs_status gs_inspect_sort(const gs_plan* plan, const void* sort_ws, gs_sort_view* out) {
+  if (!valid_plan(plan) || plan->n_entries < 0 || !sort_ws || !out) return GS_ERR_INVALID_ARG;
+  const SortLayout S = sort_layout(*plan);
+  out->tile_ids = at<uint32_t>(sort_ws, S.keys);
+  out->items = at<uint32_t>(sort_ws, S.vals);
+  out->ranges = at<uint32_t>(sort_ws, S.ranges);
+  return GS_OK;
+}
+
+const char* gs_status_string(gs_status s) {
+  switch (s) {
+    case GS_OK: return "ok";
+    case GS_ERR_INVALID_ARG: return "invalid argument";
+    case GS_ERR_CAPACITY: return "workspace too small";
+    case GS_ERR_CUDA: return "CUDA runtime error";
+    case GS_ERR_TIMEOUT: return "device wait exceeded its budget";
+    case GS_ERR_DEVICE_CHECK: return "device consistency check failed";
+  }
+  return "unknown status";
+}
+
+size_t gs_sizeof_plan(void) { return sizeof(gs_plan); }
+size_t gs_sizeof_camera(void) { return sizeof(gs_camera); }
+size_t gs_sizeof_config(void) { return sizeof(gs_config); }
+size_t gs_sizeof_scene(void) { return sizeof(gs_scene); }
+
+}  // extern "C"

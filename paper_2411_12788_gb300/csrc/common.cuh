@@ -1,0 +1,127 @@
+// Internal definitions shared by the rasterizer's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <utility>
+
+#include "../../include/gs.h"
+
+namespace gs {
+
+constexpr int kTile = GS_TILE;
+constexpr int kTilePixels = kTile * kTile;     // 256 threads per tile block
+constexpr uint32_t kCulledKey = 0xFFFFFFFFu;   // depth key of a culled item
+
+// Device status word bits (preprocess workspace).
+constexpr uint32_t kStatusTimeout = 1u;        // a look-back spin ran out
+constexpr uint32_t kStatusEntryMismatch = 2u;  // duplicate != counted tiles
+
+// Per-view constants, uploaded into the preprocess workspace.
+struct ViewDev {
+  float R[9];
+  float t[3];
+  float fx, fy, cx, cy;
+  float limx, limy;          // clamp * tan(half fov)
+  float campos[3];           // camera centre -R^T t
+  int32_t width, height, tiles_x, tiles_y;
+  int32_t tile_base;
+  int32_t pad0;
+  int64_t pixel_base;
+};
+
+// Per-item projected state, written by the preprocess kernel.
+struct ItemState {
+  float4* xy_tau_z;          // (mean2d.x, mean2d.y, tau, z)
+  float4* conic_o;           // (A, B, C, opacity); q = A dx^2 + 2B dx dy + C dy^2
+  float4* rgb;               // (r, g, b, 0)
+  float4* depth_frame;       // 3 x float4 per item: rows of W = diag(1/s) (R Rq)^T, then e = W p_c
+  uint2* rect;               // (tx0 | ty0 << 16, tx1 | ty1 << 16), inclusive
+  uint32_t* tiles;           // exact touched-tile count (0 = culled)
+  uint32_t* depth_key;       // float bits of z, kCulledKey if culled
+};
+
+// Offsets of the preprocess workspace regions (bytes), host-computed.
+struct PreLayout {
+  size_t views, status, n_entries;
+  size_t xy_tau_z, conic_o, rgb, depth_frame, rect, tiles, depth_key;
+  size_t sort_keys_alt, sort_vals, sort_vals_alt;   // depth sort buffers
+  size_t sorted_items, offsets;                      // after the depth sort
+  size_t scan_blocks;
+  size_t radix_scratch;                              // histograms + look-back
+  size_t grad2d;                                     // 3 x float4 per item
+  size_t total;
+};
+
+struct SortLayout {
+  size_t keys, keys_alt, vals, vals_alt, ranges, radix_scratch, total;
+};
+
+inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
+
+__host__ __device__ inline int ceil_div(int64_t a, int64_t b) { return (int)((a + b - 1) / b); }
+
+// ---- onesweep radix sort sizing (sort.cu) ----------------------------------
+constexpr int kRadixBits = 8;
+constexpr int kRadix = 1 << kRadixBits;
+constexpr int kSortThreads = 256;
+constexpr int kSortItemsPerThread = 15;
+constexpr int kSortTile = kSortThreads * kSortItemsPerThread;   // keys per CTA tile
+
+size_t radix_scratch_bytes(int64_t n, int bits);
+// Stable LSD sort of (key, value) pairs over bits [0, bits); the result ends
+// up in (keys, vals) (the alt buffers are scratch).  `status` receives
+// kStatusTimeout if a look-back spin ran out.
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                             int64_t n, int bits, void* scratch, uint32_t* status,
+                             cudaStream_t stream, const char* tag);
+
+// ---- exclusive scan of gathered counts (sort.cu) ---------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+size_t scan_block_bytes(int64_t n);
+// out[k] = sum_{j<k} counts[idx[k]]; *total = sum of all (device, 64-bit).
+cudaError_t gather_exclusive_scan(const uint32_t* counts, const uint32_t* idx, uint32_t* out,
+                                  int64_t n, uint64_t* block_scratch, unsigned long long* total,
+                                  cudaStream_t stream);
+
+// ---- opt-in per-kernel timing (timing.cu) ----------------------------------
+void timing_begin(const char* name, cudaStream_t stream);
+void timing_end(cudaStream_t stream);
+struct TimedLaunch {
+  cudaStream_t s;
+  TimedLaunch(const char* name, cudaStream_t st) : s(st) { timing_begin(name, st); }
+  ~TimedLaunch() { timing_end(s); }
+};
+#define GS_TIMED(name, stream, launch) \
+  do {                                 \
+    ::gs::TimedLaunch _t(name, stream); \
+    launch;                            \
+  } while (0)
+
+// ---- kernel launchers -------------------------------------------------------
+cudaError_t launch_preprocess(const gs_scene& sc, const ViewDev* views, int n_views, const uint8_t* mask,
+                              const gs_config& cfg, const ItemState& st, cudaStream_t stream);
+cudaError_t launch_preprocess_backward(const gs_scene& sc, const ViewDev* views, int n_views, const gs_config& cfg,
+                                       const uint32_t* tiles, const float4* grad2d, const gs_grads& gr,
+                                       cudaStream_t stream);
+cudaError_t launch_duplicate(const ViewDev* views, int n_views, int64_t n_items, int64_t n, const uint32_t* sorted_items,
+                             const uint32_t* offsets, const ItemState& st, uint32_t* keys, uint32_t* vals,
+                             uint32_t* status, cudaStream_t stream);
+cudaError_t launch_ranges(const uint32_t* keys, int64_t n_entries, uint2* ranges, int total_tiles,
+                          cudaStream_t stream);
+cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
+                              const uint32_t* vals, const ItemState& st, const gs_config& cfg,
+                              const gs_fwd_outputs& out, cudaStream_t stream);
+cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
+                              const uint32_t* vals, const ItemState& st, const gs_config& cfg,
+                              const float* dL_dimage, const float* final_T, const uint32_t* n_contrib,
+                              float4* grad2d, cudaStream_t stream);
+cudaError_t launch_iota(uint32_t* out, int64_t n, cudaStream_t stream);
+cudaError_t launch_loss_l1(const float* image, const float* target, int64_t count, float* loss, float* dL,
+                           cudaStream_t stream);
+
+}  // namespace gs

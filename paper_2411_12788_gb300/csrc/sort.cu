@@ -1,0 +1,372 @@
+// Onesweep LSD radix sort of (uint32 key, uint32 value) pairs and a gathered
+// exclusive scan.  Both order the rasterizer's work: the depth sort of
+// (view, Gaussian) items and the stable sort of tile entries by tile id give
+// every tile its list in the depth order of Sec. 3.1.
+//
+// Radix sort, per 8-bit digit pass:
+//   * one histogram kernel counts every pass's digits in a single read;
+//   * each CTA of the pass kernel takes the next tile of 3840 keys (dynamic
+//     tile id, so every predecessor tile is already running), ranks its keys
+//     stably by digit with warp-level match_any, publishes its per-digit
+//     counts, and looks back over its predecessors' published counts
+//     (decoupled look-back) to find its global offset per digit; keys are
+//     then staged in shared memory in output order and written out so that
+//     runs of equal digits are coalesced.
+// The look-back spin is bounded: after kSpinLimit polls the CTA records
+// kStatusTimeout in the status word and carries on (the result is then
+// wrong, and the host reports GS_ERR_TIMEOUT), so a bug cannot hang the GPU.
+#include "common.cuh"
+
+namespace gs {
+
+namespace {
+
+constexpr uint32_t kFlagAggregate = 1u << 30;
+constexpr uint32_t kFlagPrefix = 2u << 30;
+constexpr uint32_t kValueMask = (1u << 30) - 1;
+constexpr int kMaxPasses = 4;
+constexpr int kWarps = kSortThreads / 32;
+constexpr int kWarpKeys = kSortItemsPerThread * 32;
+constexpr long kSpinLimit = 1L << 20;
+
+struct RadixScratch {
+  uint32_t* hist;      // [kMaxPasses][kRadix] counts, then exclusive offsets
+  uint32_t* counters;  // [kMaxPasses] dynamic tile counters
+  uint32_t* lookback;  // [kMaxPasses][tiles][kRadix]
+};
+
+__host__ __device__ inline int64_t sort_tiles(int64_t n) { return (n + kSortTile - 1) / kSortTile; }
+
+RadixScratch carve(void* base, int64_t n) {
+  RadixScratch s;
+  char* p = static_cast<char*>(base);
+  s.hist = reinterpret_cast<uint32_t*>(p);
+  s.counters = s.hist + kMaxPasses * kRadix;
+  s.lookback = reinterpret_cast<uint32_t*>(p + align_up((kMaxPasses * kRadix + kMaxPasses) * 4));
+  return s;
+}
+
+__device__ __forceinline__ uint32_t lanemask_lt() {
+  uint32_t m;
+  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
+  return m;
+}
+
+// Counts the digits of every pass in one read of the keys.
+__global__ void __launch_bounds__(256) radix_histogram_kernel(const uint32_t* __restrict__ keys, int64_t n,
+                                                              int passes, uint32_t* __restrict__ hist) {
+  __shared__ uint32_t sh[kMaxPasses * kRadix];
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
+    int64_t i = base + threadIdx.x;
+    bool valid = i < n;
+    uint32_t k = valid ? keys[i] : 0u;
+    uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+    if (valid) {
+      for (int p = 0; p < passes; ++p) {
+        uint32_t d = (k >> (p * kRadixBits)) & (kRadix - 1);
+        uint32_t peers = __match_any_sync(vmask, d);
+        int leader = __ffs(peers) - 1;
+        if (lane == leader) atomicAdd(&sh[p * kRadix + d], __popc(peers));
+      }
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// Exclusive scan of each pass's 256 digit counts (one block per pass).
+__global__ void __launch_bounds__(kRadix) radix_scan_hist_kernel(uint32_t* hist) {
+  __shared__ uint32_t s[kRadix];
+  uint32_t* h = hist + blockIdx.x * kRadix;
+  uint32_t v = h[threadIdx.x];
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int off = 1; off < kRadix; off <<= 1) {
+    uint32_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0u;
+    __syncthreads();
+    s[threadIdx.x] += t;
+    __syncthreads();
+  }
+  h[threadIdx.x] = s[threadIdx.x] - v;
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_onesweep_kernel(
+    const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift,
+    const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ counter,
+    uint32_t* __restrict__ lookback, uint32_t* __restrict__ status) {
+  __shared__ uint32_t s_keys[kSortTile];
+  __shared__ uint32_t s_vals[kSortTile];
+  __shared__ uint32_t s_warp_hist[kWarps][kRadix];
+  __shared__ uint32_t s_cta_start[kRadix];
+  __shared__ int64_t s_out_base[kRadix];
+  __shared__ uint32_t s_tile;
+
+  const int tid = threadIdx.x;
+  const int lane = tid & 31;
+  const int warp = tid >> 5;
+  if (tid == 0) s_tile = atomicAdd(counter, 1u);
+  for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&s_warp_hist[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t tile = s_tile;
+  const int64_t tile_start = tile * kSortTile;
+
+  // 1. load keys (warp-striped: each warp owns a contiguous segment) and rank
+  //    them stably by digit inside the warp.
+  uint32_t key[kSortItemsPerThread];
+  uint32_t rank[kSortItemsPerThread];
+  const uint32_t lt = lanemask_lt();
+#pragma unroll
+  for (int k = 0; k < kSortItemsPerThread; ++k) {
+    int64_t i = tile_start + warp * kWarpKeys + k * 32 + lane;
+    bool valid = i < n;
+    key[k] = valid ? keys_in[i] : 0u;
+    uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+    rank[k] = 0;
+    if (valid) {
+      uint32_t d = (key[k] >> shift) & (kRadix - 1);
+      uint32_t peers = __match_any_sync(vmask, d);
+      int leader = __ffs(peers) - 1;
+      uint32_t before = 0;
+      if (lane == leader) {
+        before = s_warp_hist[warp][d];
+        s_warp_hist[warp][d] = before + __popc(peers);
+      }
+      before = __shfl_sync(peers, before, leader);
+      rank[k] = before + __popc(peers & lt);
+    }
+    __syncwarp();
+  }
+  __syncthreads();
+
+  // 2. per digit: offsets of each warp inside the CTA and the CTA's count.
+  uint32_t cta_count = 0;
+  {
+    const int d = tid;   // kSortThreads == kRadix
+    for (int w = 0; w < kWarps; ++w) {
+      uint32_t c = s_warp_hist[w][d];
+      s_warp_hist[w][d] = cta_count;
+      cta_count += c;
+    }
+    // publish this tile's count (or its inclusive prefix for tile 0)
+    uint32_t* mine = lookback + tile * kRadix + d;
+    if (tile == 0) {
+      __threadfence();
+      *(volatile uint32_t*)mine = kFlagPrefix | cta_count;
+    } else {
+      *(volatile uint32_t*)mine = kFlagAggregate | cta_count;
+    }
+  }
+
+  // 3. decoupled look-back for this digit
+  uint32_t exclusive = 0;
+  if (tile > 0) {
+    const int d = tid;
+    int64_t j = tile - 1;
+    long spins = 0;
+    while (j >= 0) {
+      uint32_t s = *(volatile uint32_t*)(lookback + j * kRadix + d);
+      uint32_t flag = s & ~kValueMask;
+      if (flag == 0) {
+        if (++spins > kSpinLimit) {
+          atomicOr(status, kStatusTimeout);
+          break;
+        }
+        continue;
+      }
+      exclusive += s & kValueMask;
+      if (flag == kFlagPrefix) break;
+      --j;
+    }
+    *(volatile uint32_t*)(lookback + tile * kRadix + d) = kFlagPrefix | (exclusive + cta_count);
+  }
+
+  // 4. CTA-local exclusive scan over digits (for the shared-memory staging)
+  {
+    const int d = tid;
+    // warp-level inclusive scan then across warps
+    uint32_t v = cta_count;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      uint32_t t = __shfl_up_sync(0xffffffffu, v, off);
+      if (lane >= off) v += t;
+    }
+    __shared__ uint32_t s_warp_tot[kWarps];
+    if (lane == 31) s_warp_tot[warp] = v;
+    __syncthreads();
+    uint32_t add = 0;
+    for (int w = 0; w < warp; ++w) add += s_warp_tot[w];
+    uint32_t start = v - cta_count + add;
+    s_cta_start[d] = start;
+    s_out_base[d] = (int64_t)digit_base[d] + exclusive - start;
+  }
+  __syncthreads();
+
+  // 5. stage keys and values in output order
+#pragma unroll
+  for (int k = 0; k < kSortItemsPerThread; ++k) {
+    int64_t i = tile_start + warp * kWarpKeys + k * 32 + lane;
+    if (i < n) {
+      uint32_t d = (key[k] >> shift) & (kRadix - 1);
+      uint32_t pos = s_cta_start[d] + s_warp_hist[warp][d] + rank[k];
+      s_keys[pos] = key[k];
+      s_vals[pos] = vals_in[i];
+    }
+  }
+  __syncthreads();
+
+  // 6. write out
+  const int count = (int)((n - tile_start < kSortTile) ? (n - tile_start) : (int64_t)kSortTile);
+  for (int i = tid; i < count; i += kSortThreads) {
+    uint32_t k = s_keys[i];
+    uint32_t d = (k >> shift) & (kRadix - 1);
+    int64_t out = s_out_base[d] + i;
+    keys_out[out] = k;
+    vals_out[out] = s_vals[i];
+  }
+}
+
+// ---- gathered exclusive scan ------------------------------------------------
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s_warp, uint32_t* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    uint32_t t = __shfl_up_sync(0xffffffffu, x, off);
+    if (lane >= off) x += t;
+  }
+  if (lane == 31) s_warp[warp] = x;
+  __syncthreads();
+  uint32_t add = 0, tot = 0;
+  for (int w = 0; w < kScanThreads / 32; ++w) {
+    if (w < warp) add += s_warp[w];
+    tot += s_warp[w];
+  }
+  *total = tot;
+  return x - v + add;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_block_sums_kernel(const uint32_t* __restrict__ counts,
+                                                                       const uint32_t* __restrict__ idx,
+                                                                       int64_t n, uint64_t* __restrict__ sums) {
+  __shared__ uint32_t s_warp[kScanThreads / 32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint32_t acc = 0;
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + k * kScanThreads + threadIdx.x;
+    if (i < n) acc += counts[idx[i]];
+  }
+  uint32_t tot;
+  block_exclusive_scan(acc, s_warp, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the block sums in place, total to *total.
+__global__ void __launch_bounds__(1024) scan_top_kernel(uint64_t* sums, int64_t nb, unsigned long long* total) {
+  __shared__ uint64_t s[1024];
+  __shared__ uint64_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int64_t base = 0; base < nb; base += 1024) {
+    int64_t i = base + threadIdx.x;
+    uint64_t v = i < nb ? sums[i] : 0;
+    s[threadIdx.x] = v;
+    __syncthreads();
+    for (int off = 1; off < 1024; off <<= 1) {
+      uint64_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
+      __syncthreads();
+      s[threadIdx.x] += t;
+      __syncthreads();
+    }
+    if (i < nb) sums[i] = carry + s[threadIdx.x] - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += s[1023];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *total = carry;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const uint32_t* __restrict__ counts,
+                                                                  const uint32_t* __restrict__ idx, int64_t n,
+                                                                  const uint64_t* __restrict__ sums,
+                                                                  uint32_t* __restrict__ out) {
+  // thread t owns the contiguous items [t*kScanItems, (t+1)*kScanItems) of the block
+  __shared__ uint32_t s_warp[kScanThreads / 32];
+  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t c[kScanItems];
+  uint32_t acc = 0;
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + k;
+    c[k] = i < n ? counts[idx[i]] : 0u;
+    acc += c[k];
+  }
+  uint32_t tot;
+  uint32_t run = block_exclusive_scan(acc, s_warp, &tot) + (uint32_t)sums[blockIdx.x];
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {
+    int64_t i = base + k;
+    if (i < n) out[i] = run;
+    run += c[k];
+  }
+}
+
+}  // namespace
+
+size_t radix_scratch_bytes(int64_t n, int bits) {
+  int passes = (bits + kRadixBits - 1) / kRadixBits;
+  return align_up((kMaxPasses * kRadix + kMaxPasses) * 4) +
+         align_up((size_t)passes * (size_t)sort_tiles(n) * kRadix * 4);
+}
+
+cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
+                             int64_t n, int bits, void* scratch, uint32_t* status, cudaStream_t stream,
+                             const char* tag) {
+  if (n <= 0 || bits <= 0) return cudaSuccess;
+  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  RadixScratch s = carve(scratch, n);
+  const int64_t tiles = sort_tiles(n);
+  cudaError_t e = cudaMemsetAsync(scratch, 0, radix_scratch_bytes(n, bits), stream);
+  if (e != cudaSuccess) return e;
+  int hist_blocks = (int)std::min<int64_t>(4 * 152, (n + 255) / 256);
+  const bool depth = tag && tag[0] == 'd';
+  GS_TIMED(depth ? "depth_sort_histogram" : "tile_sort_histogram", stream,
+           (radix_histogram_kernel<<<hist_blocks, 256, 0, stream>>>(keys, n, passes, s.hist)));
+  GS_TIMED(depth ? "depth_sort_scan_hist" : "tile_sort_scan_hist", stream,
+           (radix_scan_hist_kernel<<<passes, kRadix, 0, stream>>>(s.hist)));
+  uint32_t *kin = keys, *kout = keys_alt, *vin = vals, *vout = vals_alt;
+  for (int p = 0; p < passes; ++p) {
+    GS_TIMED(depth ? "depth_sort_onesweep" : "tile_sort_onesweep", stream,
+             (radix_onesweep_kernel<<<(unsigned)tiles, kSortThreads, 0, stream>>>(
+                 kin, vin, kout, vout, n, p * kRadixBits, s.hist + p * kRadix, s.counters + p,
+                 s.lookback + (size_t)p * tiles * kRadix, status)));
+    std::swap(kin, kout);
+    std::swap(vin, vout);
+  }
+  if (kin != keys) {   // odd number of passes: the result sits in the alt buffers
+    cudaMemcpyAsync(keys, kin, n * 4, cudaMemcpyDeviceToDevice, stream);
+    cudaMemcpyAsync(vals, vin, n * 4, cudaMemcpyDeviceToDevice, stream);
+  }
+  return cudaGetLastError();
+}
+
+size_t scan_block_bytes(int64_t n) { return align_up((size_t)ceil_div(std::max<int64_t>(n, 1), kScanTile) * 8); }
+
+cudaError_t gather_exclusive_scan(const uint32_t* counts, const uint32_t* idx, uint32_t* out, int64_t n,
+                                  uint64_t* block_scratch, unsigned long long* total, cudaStream_t stream) {
+  if (n <= 0) return cudaMemsetAsync(total, 0, 8, stream);
+  int nb = ceil_div(n, kScanTile);
+  GS_TIMED("scan_block_sums", stream,
+           (scan_block_sums_kernel<<<nb, kScanThreads, 0, stream>>>(counts, idx, n, block_scratch)));
+  GS_TIMED("scan_top", stream, (scan_top_kernel<<<1, 1024, 0, stream>>>(block_scratch, nb, total)));
+  GS_TIMED("scan_final", stream,
+           (scan_final_kernel<<<nb, kScanThreads, 0, stream>>>(counts, idx, n, block_scratch, out)));
+  return cudaGetLastError();
+}
+
+}  // namespace gs

@@ -1,0 +1,304 @@
+"""Python binding of the rasterizer: the four C-ABI calls on torch tensors,
+a reusable workspace holder and the torch.autograd.Function.
+
+PyTorch supplies device memory and the stream; every step of the path runs
+in libgs.so.  Functions named after the C ABI (preprocess, bin_sort,
+render_fwd, render_bwd, loss_l1) only marshal arguments.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import check, lib
+
+
+# ---------------------------------------------------------------- marshalling
+def _ptr(t: torch.Tensor | None):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_camera(cam) -> _lib.Camera:
+    """gs_camera from an object with R, t, fx, fy, cx, cy, width, height."""
+    c = _lib.Camera()
+    R = np.asarray(cam.R, np.float64).reshape(9)
+    t = np.asarray(cam.t, np.float64).reshape(3)
+    for k in range(9):
+        c.R[k] = float(R[k])
+    for k in range(3):
+        c.t[k] = float(t[k])
+    c.fx, c.fy, c.cx, c.cy = float(cam.fx), float(cam.fy), float(cam.cx), float(cam.cy)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def make_config(**kw) -> _lib.Config:
+    cfg = _lib.Config()
+    lib().gs_config_default(C.byref(cfg))
+    for k, v in kw.items():
+        if k == "bg":
+            for j in range(3):
+                cfg.bg[j] = float(v[j])
+        else:
+            setattr(cfg, k, v)
+    return cfg
+
+
+@dataclass
+class GaussianTensors:
+    """Device FP32 Gaussian attributes (activated values), gs_scene layout."""
+    means: torch.Tensor        # [N, 3]
+    scales: torch.Tensor       # [N, 3]
+    rotations: torch.Tensor    # [N, 4] (w, x, y, z)
+    opacities: torch.Tensor    # [N]
+    sh: torch.Tensor           # [N, K, 3]
+    sh_degree: int
+
+    @property
+    def n(self) -> int:
+        return int(self.means.shape[0])
+
+    @staticmethod
+    def from_scene(scene, device="cuda") -> "GaussianTensors":
+        f = lambda a: torch.as_tensor(np.ascontiguousarray(a, np.float32)).to(device)
+        return GaussianTensors(f(scene.means), f(scene.scales), f(scene.rotations),
+                               f(scene.opacities), f(scene.sh), int(scene.sh_degree))
+
+    def struct(self) -> _lib.Scene:
+        for name in ("means", "scales", "rotations", "opacities", "sh"):
+            t = getattr(self, name)
+            if t.dtype != torch.float32 or not t.is_contiguous() or not t.is_cuda:
+                raise ValueError(f"{name} must be a contiguous float32 CUDA tensor")
+        s = _lib.Scene()
+        s.means, s.scales, s.rotations = self.means.data_ptr(), self.scales.data_ptr(), self.rotations.data_ptr()
+        s.opacities, s.sh = self.opacities.data_ptr(), self.sh.data_ptr()
+        s.n = self.n
+        s.sh_degree = int(self.sh_degree)
+        s.sh_coeffs = int(self.sh.shape[1])
+        return s
+
+
+def make_plan(n: int, cams) -> _lib.Plan:
+    cam_arr = (_lib.Camera * len(cams))(*[make_camera(c) for c in cams])
+    plan = _lib.Plan()
+    check("gs_plan_init", lib().gs_plan_init(C.byref(plan), int(n), cam_arr, len(cams)))
+    return plan
+
+
+def preprocess_workspace_size(plan) -> int:
+    return int(lib().gs_preprocess_workspace_size(C.byref(plan)))
+
+
+def bin_sort_workspace_size(plan) -> int:
+    return int(lib().gs_bin_sort_workspace_size(C.byref(plan)))
+
+
+# ---------------------------------------------------------------- the C-ABI calls
+def preprocess(plan, scene: _lib.Scene, cfg: _lib.Config, pre_ws: torch.Tensor,
+               mask: torch.Tensor | None = None, stream=None) -> int:
+    check("gs_preprocess", lib().gs_preprocess(C.byref(plan), C.byref(scene), C.byref(cfg), _ptr(mask),
+                                               _ptr(pre_ws), pre_ws.numel(), _stream(stream)))
+    return int(plan.n_entries)
+
+
+def bin_sort(plan, pre_ws: torch.Tensor, sort_ws: torch.Tensor, stream=None) -> None:
+    check("gs_bin_sort", lib().gs_bin_sort(C.byref(plan), _ptr(pre_ws), _ptr(sort_ws), sort_ws.numel(),
+                                           _stream(stream)))
+
+
+def render_fwd(plan, cfg, pre_ws, sort_ws, outs: dict, stream=None) -> None:
+    o = _lib.FwdOutputs()
+    for name, _ in _lib.FwdOutputs._fields_:
+        t = outs.get(name)
+        setattr(o, name, None if t is None else t.data_ptr())
+    check("gs_render_fwd", lib().gs_render_fwd(C.byref(plan), C.byref(cfg), _ptr(pre_ws), _ptr(sort_ws),
+                                               C.byref(o), _stream(stream)))
+
+
+def render_bwd(plan, scene: _lib.Scene, cfg, pre_ws, sort_ws, dL_dimage, final_T, n_contrib,
+               grads: dict, stream=None) -> None:
+    g = _lib.Grads()
+    for name, _ in _lib.Grads._fields_:
+        t = grads.get(name)
+        setattr(g, name, None if t is None else t.data_ptr())
+    check("gs_render_bwd", lib().gs_render_bwd(C.byref(plan), C.byref(scene), C.byref(cfg), _ptr(pre_ws),
+                                               _ptr(sort_ws), _ptr(dL_dimage), _ptr(final_T),
+                                               _ptr(n_contrib), C.byref(g), _stream(stream)))
+
+
+def loss_l1(image, target, loss, dL_dimage, stream=None) -> None:
+    check("gs_loss_l1", lib().gs_loss_l1(_ptr(image), _ptr(target), image.numel(), _ptr(loss),
+                                         _ptr(dL_dimage), _stream(stream)))
+
+
+def device_status(plan, pre_ws, stream=None) -> int:
+    return int(lib().gs_device_status(C.byref(plan), _ptr(pre_ws), _stream(stream)))
+
+
+def inspect_preprocess(fr: "Frame") -> dict:
+    """Copies of the per-item projected state and depth order (for tests)."""
+    v = _lib.PreprocessView()
+    check("gs_inspect_preprocess", lib().gs_inspect_preprocess(C.byref(fr.plan), _ptr(fr.pre_ws), C.byref(v)))
+    base = fr.pre_ws.data_ptr()
+    I = int(fr.plan.n_items)
+
+    def sl(ptr, count, dtype):
+        off = ptr - base
+        esz = torch.empty(0, dtype=dtype).element_size()
+        return fr.pre_ws[off: off + count * esz].view(dtype).cpu()
+    return {"xy_tau_z": sl(v.xy_tau_z, 4 * I, torch.float32).view(I, 4),
+            "conic_o": sl(v.conic_o, 4 * I, torch.float32).view(I, 4),
+            "rgb": sl(v.rgb, 4 * I, torch.float32).view(I, 4),
+            "tiles": sl(v.tiles, I, torch.int32),
+            "rect": sl(v.rect, 2 * I, torch.int32).view(I, 2),
+            "sorted_items": sl(v.sorted_items, I, torch.int32),
+            "offsets": sl(v.offsets, I, torch.int32)}
+
+
+def inspect_sort(fr: "Frame") -> dict:
+    """Copies of the sorted tile entries and tile ranges (for tests)."""
+    v = _lib.SortView()
+    check("gs_inspect_sort", lib().gs_inspect_sort(C.byref(fr.plan), _ptr(fr.sort_ws), C.byref(v)))
+    base = fr.sort_ws.data_ptr()
+    E, K = int(fr.plan.n_entries), int(fr.plan.total_tiles)
+
+    def sl(ptr, count):
+        off = ptr - base
+        return fr.sort_ws[off: off + 4 * count].view(torch.int32).cpu()
+    return {"tile_ids": sl(v.tile_ids, E), "items": sl(v.items, E), "ranges": sl(v.ranges, 2 * K).view(K, 2)}
+
+
+# ---------------------------------------------------------------- outputs
+FWD_OUTPUTS = ("image", "final_T", "n_contrib", "imax", "wmax", "depth", "depth_blend",
+               "weight_sum", "max_area")
+
+
+def alloc_outputs(plan, device="cuda", want=FWD_OUTPUTS) -> dict:
+    P, I = int(plan.total_pixels), int(plan.n_items)
+    f32, i32 = torch.float32, torch.int32
+    spec = {"image": (3 * P, f32), "final_T": (P, f32), "n_contrib": (P, i32), "imax": (P, i32),
+            "wmax": (P, f32), "depth": (P, f32), "depth_blend": (P, f32),
+            "weight_sum": (I, f32), "max_area": (I, i32)}
+    out = {}
+    for k in FWD_OUTPUTS:
+        if k in want or k in ("image", "final_T", "n_contrib"):
+            n, dt = spec[k]
+            out[k] = torch.empty(max(n, 1), dtype=dt, device=device)[:n]
+    for k in ("weight_sum", "max_area"):
+        if k in out:
+            out[k].zero_()
+    return out
+
+
+def view_slice(plan, v: int):
+    """(pixel offset, H, W) of view v in the concatenated per-pixel outputs."""
+    c = plan.cams[v]
+    return int(plan.pixel_base[v]), int(c.height), int(c.width)
+
+
+def view_image(image: torch.Tensor, plan, v: int) -> torch.Tensor:
+    off, h, w = view_slice(plan, v)
+    return image[3 * off: 3 * (off + h * w)].view(3, h, w)
+
+
+def view_pixels(t: torch.Tensor, plan, v: int) -> torch.Tensor:
+    off, h, w = view_slice(plan, v)
+    return t[off: off + h * w].view(h, w)
+
+
+def alloc_grads(g: GaussianTensors) -> dict:
+    z = lambda t: torch.zeros_like(t)
+    return {"d_means": z(g.means), "d_scales": z(g.scales), "d_rotations": z(g.rotations),
+            "d_opacities": z(g.opacities), "d_sh": z(g.sh),
+            "d_mean2d_abs": torch.zeros(g.n, dtype=torch.float32, device=g.means.device)}
+
+
+# ---------------------------------------------------------------- one-shot passes
+@dataclass
+class Frame:
+    """The state of one forward pass: plan, workspaces and outputs."""
+    plan: _lib.Plan
+    cfg: _lib.Config
+    pre_ws: torch.Tensor
+    sort_ws: torch.Tensor | None
+    outs: dict = field(default_factory=dict)
+
+
+def forward(g: GaussianTensors, cams, cfg=None, mask=None, want=FWD_OUTPUTS, stream=None) -> Frame:
+    """Preprocess, bin/sort and render every camera in one batch."""
+    cfg = cfg or make_config()
+    dev = g.means.device
+    plan = make_plan(g.n, cams)
+    pre_ws = torch.empty(preprocess_workspace_size(plan), dtype=torch.uint8, device=dev)
+    preprocess(plan, g.struct(), cfg, pre_ws, mask, stream)
+    sort_ws = torch.empty(bin_sort_workspace_size(plan), dtype=torch.uint8, device=dev)
+    bin_sort(plan, pre_ws, sort_ws, stream)
+    outs = alloc_outputs(plan, dev, want)
+    render_fwd(plan, cfg, pre_ws, sort_ws, outs, stream)
+    return Frame(plan, cfg, pre_ws, sort_ws, outs)
+
+
+def backward(g: GaussianTensors, fr: Frame, dL_dimage: torch.Tensor, stream=None) -> dict:
+    """Gradients of the attributes given dL/d image of a forward Frame.  If
+    the frame's sorted lists were dropped, they are rebuilt first."""
+    if fr.sort_ws is None:
+        fr.sort_ws = torch.empty(bin_sort_workspace_size(fr.plan), dtype=torch.uint8, device=g.means.device)
+        bin_sort(fr.plan, fr.pre_ws, fr.sort_ws, stream)
+    grads = alloc_grads(g)
+    render_bwd(fr.plan, g.struct(), fr.cfg, fr.pre_ws, fr.sort_ws, dL_dimage.contiguous(),
+               fr.outs["final_T"], fr.outs["n_contrib"], grads, stream)
+    return grads
+
+
+class RasterizeGaussians(torch.autograd.Function):
+    """Differentiable rasterization of a batch of views.
+
+    forward(means, scales, rotations, opacities, sh, settings) returns
+    (image [3 * total_pixels], depth, imax, weight_sum, max_area) where only
+    the image is differentiable.  settings: RasterSettings."""
+
+    @staticmethod
+    def forward(ctx, means, scales, rotations, opacities, sh, settings):
+        g = GaussianTensors(means.detach().contiguous(), scales.detach().contiguous(),
+                            rotations.detach().contiguous(), opacities.detach().contiguous(),
+                            sh.detach().contiguous(), settings.sh_degree)
+        fr = forward(g, settings.cams, settings.cfg, settings.mask,
+                     want=("image", "depth", "imax", "weight_sum", "max_area"))
+        if settings.recompute_sort:
+            fr.sort_ws = None          # rebuilt in backward: the lists are not kept
+        ctx.frame = fr
+        ctx.g = g
+        o = fr.outs
+        ctx.mark_non_differentiable(o["depth"], o["imax"], o["weight_sum"], o["max_area"])
+        settings.last_plan = fr.plan
+        return o["image"], o["depth"], o["imax"], o["weight_sum"], o["max_area"]
+
+    @staticmethod
+    def backward(ctx, d_image, *unused):
+        grads = backward(ctx.g, ctx.frame, d_image)
+        ctx.frame = None
+        return grads["d_means"], grads["d_scales"], grads["d_rotations"], grads["d_opacities"], \
+            grads["d_sh"], None
+
+
+@dataclass
+class RasterSettings:
+    cams: list
+    sh_degree: int
+    cfg: _lib.Config = field(default_factory=make_config)
+    mask: torch.Tensor | None = None
+    recompute_sort: bool = False
+    last_plan: _lib.Plan | None = None
+
+
+def rasterize(means, scales, rotations, opacities, sh, settings: RasterSettings):
+    return RasterizeGaussians.apply(means, scales, rotations, opacities, sh, settings)

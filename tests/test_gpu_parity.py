@@ -1,0 +1,373 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+Stage by stage: projection (tolerance), binning / sort order / tile ranges
+(bit-exact, decided by the oracle on the CUDA path's own FP32 state), render
+outputs (tolerance, near-threshold pixels excluded and counted) and gradients
+(relative tolerance).  Tolerances, derived from FP32 arithmetic:
+  colour, T, w_max            max-abs 1e-4
+  depth (d^mid, d^blend)      1e-4 * max(1, |d|)   (values reach ~30)
+  I_i (summed weights)        1e-4 + 1e-5 * I      (sums of up to ~1e4 terms)
+  gradients                   |g - g_ref| <= 1e-3 max(|g_ref|, 1e-2 ||g_ref||_inf)
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+from oracle import OracleConfig, binning as OB, project as OP, render as OR
+from paper_2411_12788_gb300 import raster, scenes
+
+pytestmark = pytest.mark.gpu
+CFG = OracleConfig()
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _oracle_view(sc, cam, pix=None, want_depth=True):
+    with torch.no_grad():
+        pr = OP.project(sc.means, sc.scales, sc.rotations, sc.opacities, sc.sh, sc.sh_degree, cam)
+        out = OR.render_view(pr, cam, pix=pix, want_depth=want_depth)
+    return pr, out
+
+
+def _gpu_pixels(fr, v, name):
+    t = fr.outs[name]
+    off, h, w = raster.view_slice(fr.plan, v)
+    return t[off: off + h * w].cpu()
+
+
+def _gpu_colour(fr, v):
+    return raster.view_image(fr.outs["image"], fr.plan, v).cpu().double().permute(1, 2, 0).reshape(-1, 3)
+
+
+def _multiview_cams():
+    # three ragged views (sizes not multiples of 16) around the box scene
+    sizes = [(50, 37), (64, 64), (33, 20)]
+    eyes = [(0.0, 0.0, 0.0), (0.4, -0.2, 0.3), (-0.5, 0.3, -0.2)]
+    cams = []
+    for (w, h), e in zip(sizes, eyes):
+        R, t = scenes.look_at(e, (0.0, 0.0, 4.0))
+        cams.append(scenes.fov_camera(R, t, w, h, 50.0))
+    return cams
+
+
+SCENES = {
+    "box1024_deg0": lambda: (scenes.box_scene(1024, seed=0, sh_degree=0), [scenes.origin_camera()]),
+    "box512_deg3_multiview": lambda: (scenes.box_scene(512, seed=4, sh_degree=3), _multiview_cams()),
+}
+
+
+# ---------------------------------------------------------------- stage P
+@pytest.mark.parametrize("case", list(SCENES))
+def test_preprocess_matches_oracle(case):
+    _need_gpu()
+    sc, cams = SCENES[case]()
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, cams)
+    st = raster.inspect_preprocess(fr)
+    n = sc.n
+    for v, cam in enumerate(cams):
+        sl = slice(v * n, (v + 1) * n)
+        vis = st["tiles"][sl].numpy() > 0
+        with torch.no_grad():
+            pr = OP.project(sc.means, sc.scales, sc.rotations, sc.opacities, sc.sh, sc.sh_degree, cam)
+        assert vis.sum() > 0
+        assert np.all(pr["valid"].numpy()[vis])
+        xy = st["xy_tau_z"][sl].double().numpy()
+        co = st["conic_o"][sl].double().numpy()
+        rgb = st["rgb"][sl].double().numpy()
+        ref_m = pr["mean2d"].numpy()
+        np.testing.assert_allclose(xy[vis, :2], ref_m[vis], rtol=1e-5, atol=1e-3)
+        np.testing.assert_allclose(xy[vis, 3], pr["z"].numpy()[vis], rtol=1e-6)
+        np.testing.assert_allclose(xy[vis, 2], pr["tau"].numpy()[vis], rtol=1e-5, atol=1e-5)
+        ref_c = pr["conic"].numpy()
+        scale = np.abs(ref_c[vis]).max(axis=1, keepdims=True)
+        assert np.all(np.abs(co[vis, :3] - ref_c[vis]) <= 2e-5 * scale + 1e-7)
+        np.testing.assert_allclose(co[vis, 3], sc.opacities[vis], rtol=0, atol=0)
+        np.testing.assert_allclose(rgb[vis, :3], pr["rgb"].numpy()[vis], atol=2e-6)
+
+
+# ---------------------------------------------------------------- stage B
+@pytest.mark.parametrize("case", list(SCENES))
+def test_binning_sort_ranges_bit_exact(case):
+    """Tile lists: the oracle decides membership in float64 from the CUDA
+    path's FP32 state; they must agree except within 1e-4 of the boundary.
+    Order: stable (tile, float32 z, item) order of the CUDA path's own entries,
+    bit-exact; ranges bit-exact; scanned offsets bit-exact."""
+    _need_gpu()
+    sc, cams = SCENES[case]()
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, cams)
+    st = raster.inspect_preprocess(fr)
+    so = raster.inspect_sort(fr)
+    n = sc.n
+    bases, total_tiles = OB.view_tile_bases([(c.width, c.height) for c in cams])
+    assert total_tiles == fr.plan.total_tiles
+    tiles_ids = so["tile_ids"].numpy().astype(np.int64)
+    items = so["items"].numpy().astype(np.int64)
+    E = int(fr.plan.n_entries)
+    assert len(items) == E and E > 0
+    gpu_set = set(zip(tiles_ids.tolist(), items.tolist()))
+    assert len(gpu_set) == E                      # no duplicated entry
+    xyz = st["xy_tau_z"].numpy()
+    co = st["conic_o"].numpy()
+    cnt = st["tiles"].numpy().astype(np.int64)
+    near_total = 0
+    for v, cam in enumerate(cams):
+        sl = slice(v * n, (v + 1) * n)
+        vis = cnt[sl] > 0
+        gg, tt, near, rg, rt = OB.tile_lists(xyz[sl, :2], co[sl, :3], co[sl, 3], vis, cam.width, cam.height)
+        exp = set(zip((tt + bases[v]).tolist(), (gg + v * n).tolist()))
+        upper = bases[v + 1] if v + 1 < len(cams) else total_tiles
+        got = {(t, i) for (t, i) in gpu_set if bases[v] <= t < upper}
+        allowed = set(zip((tt[near] + bases[v]).tolist(), (gg[near] + v * n).tolist())) | \
+            set(zip((rt + bases[v]).tolist(), (rg + v * n).tolist()))
+        diff = exp ^ got
+        assert diff <= allowed, list(diff - allowed)[:5]
+        near_total += len(diff)
+    assert near_total <= max(2, 1e-3 * E)
+    # per-item counts and the depth-order scan
+    per_item = np.bincount(items, minlength=len(cnt))
+    np.testing.assert_array_equal(per_item, cnt)
+    order = st["sorted_items"].numpy().astype(np.int64)
+    zf = xyz[:, 3].astype(np.float32)
+    vis_all = cnt > 0
+    ref_order = np.nonzero(vis_all)[0][np.lexsort((np.nonzero(vis_all)[0], zf[vis_all]))]
+    np.testing.assert_array_equal(order[:len(ref_order)], ref_order)
+    np.testing.assert_array_equal(st["offsets"].numpy()[:len(ref_order)], OB.exclusive_scan(cnt[ref_order]))
+    # order of the entries: stable by (tile, z bits) over (item-major) input
+    inp = np.lexsort((tiles_ids, items))              # input order: item, then tile
+    # items within the same (tile, z) keep ascending item order
+    perm = OB.sort_entries(tiles_ids[inp], zf[items[inp]], None)
+    np.testing.assert_array_equal(tiles_ids[inp][perm], tiles_ids)
+    np.testing.assert_array_equal(items[inp][perm], items)
+    np.testing.assert_array_equal(so["ranges"].numpy(), OB.tile_ranges(tiles_ids, total_tiles))
+
+
+# ---------------------------------------------------------------- stage R
+def _check_render(sc, cams, fr, max_flag_frac=2e-3):
+    n = sc.n
+    for v, cam in enumerate(cams):
+        pr, out = _oracle_view(sc, cam)
+        ok = out["flags"].numpy() == 0
+        assert ok.mean() >= 1 - max_flag_frac, ok.mean()
+        col = _gpu_colour(fr, v).numpy()
+        ref = out["colour"].numpy()
+        assert np.abs(col - ref)[ok].max() <= 1e-4
+        T = _gpu_pixels(fr, v, "final_T").double().numpy()
+        assert np.abs(T - out["t_final"].numpy())[ok].max() <= 1e-4
+        wmax = _gpu_pixels(fr, v, "wmax").double().numpy()
+        assert np.abs(wmax - out["wmax"].numpy())[ok].max() <= 1e-4
+        imax = _gpu_pixels(fr, v, "imax").numpy()
+        np.testing.assert_array_equal(imax[ok], out["imax"].numpy()[ok])
+        d = _gpu_pixels(fr, v, "depth").double().numpy()
+        dref = out["depth"].numpy()
+        assert np.all(np.abs(d - dref)[ok] <= 1e-4 * np.maximum(1.0, np.abs(dref[ok])))
+        db = _gpu_pixels(fr, v, "depth_blend").double().numpy()
+        dbr = out["depth_blend"].numpy()
+        assert np.all(np.abs(db - dbr)[ok] <= 1e-4 * np.maximum(1.0, np.abs(dbr[ok])))
+        # n_contrib points at the last blended Gaussian in the tile's list
+        nc = _gpu_pixels(fr, v, "n_contrib").numpy().astype(np.int64)
+        last = out["last"].numpy()
+        so = raster.inspect_sort(fr)
+        rngs = so["ranges"].numpy()
+        items = so["items"].numpy()
+        base = fr.plan.tile_base[v]
+        tx_n = (cam.width + 15) // 16
+        uu, vv = out["u"].numpy(), out["v"].numpy()
+        tile = base + (vv // 16) * tx_n + uu // 16
+        has = (nc > 0) & ok
+        gpu_last = items[rngs[tile[has], 0] + nc[has] - 1] - v * n
+        np.testing.assert_array_equal(gpu_last, last[has])
+        assert np.all(last[(nc == 0) & ok] == -1)
+        # per-Gaussian sums of this view, compared where no flagged pixel is involved
+        bad = OR.contributors(pr, np.stack([uu[~ok], vv[~ok]], 1), CFG.alpha_min)
+        keep = np.ones(n, bool)
+        keep[bad] = False
+        ws = fr.outs["weight_sum"][v * n:(v + 1) * n].cpu().double().numpy()
+        wr = out["weight_sum"].numpy()
+        assert np.all(np.abs(ws - wr)[keep] <= 1e-4 + 1e-5 * np.abs(wr[keep]))
+        ma = fr.outs["max_area"][v * n:(v + 1) * n].cpu().numpy()
+        np.testing.assert_array_equal(ma[keep], out["max_area"].numpy()[keep])
+
+
+@pytest.mark.parametrize("case", list(SCENES))
+def test_render_matches_oracle(case):
+    _need_gpu()
+    sc, cams = SCENES[case]()
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, cams)
+    torch.cuda.synchronize()
+    assert raster.device_status(fr.plan, fr.pre_ws) == 0
+    _check_render(sc, cams, fr)
+
+
+def test_render_is_deterministic():
+    _need_gpu()
+    sc, cams = SCENES["box512_deg3_multiview"]()
+    g = raster.GaussianTensors.from_scene(sc)
+    a = raster.forward(g, cams).outs
+    b = raster.forward(g, cams).outs
+    for k in ("image", "final_T", "n_contrib", "imax", "depth", "max_area"):
+        assert torch.equal(a[k], b[k]), k
+
+
+# ---------------------------------------------------------------- gradients
+def _grad_case(seed=2, n=256, deg=3, size=64):
+    sc = scenes.box_scene(n, seed=seed, sh_degree=deg)
+    cam = scenes.origin_camera(size, size, float(size))
+    target = scenes.target_images([cam], seed=1)[0]
+    return sc, cam, target
+
+
+def _oracle_grads(sc, cam, target):
+    params = [torch.tensor(np.asarray(a, np.float64), requires_grad=True)
+              for a in (sc.means, sc.scales, sc.rotations, sc.opacities, sc.sh)]
+    pr = OP.project(*params, sc.sh_degree, cam)
+    out = OR.render_view(pr, cam, want_depth=False)
+    img = OR.planar(out["colour"], cam)
+    L = torch.abs(img - torch.as_tensor(target, dtype=torch.float64)).mean()
+    L.backward()
+    return L.item(), [p.grad.numpy() for p in params], out, pr
+
+
+def _assert_grad_close(name, g, ref, keep):
+    g = g[keep].reshape(-1)
+    ref = ref[keep].reshape(-1)
+    floor = 1e-2 * np.abs(ref).max()
+    bad = np.abs(g - ref) > 1e-3 * np.maximum(np.abs(ref), floor)
+    assert not bad.any(), (name, int(bad.sum()), g[bad][:4], ref[bad][:4])
+
+
+@pytest.mark.parametrize("deg,seed", [(3, 2), (0, 0), (1, 5)])
+def test_backward_matches_oracle(deg, seed):
+    _need_gpu()
+    sc, cam, target = _grad_case(seed=seed, deg=deg)
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, [cam])
+    img = fr.outs["image"]
+    tgt = torch.as_tensor(target.reshape(-1)).cuda()
+    loss = torch.zeros(1, device="cuda")
+    dL = torch.empty_like(img)
+    raster.loss_l1(img, tgt, loss, dL)
+    grads = raster.backward(g, fr, dL)
+    torch.cuda.synchronize()
+    L, ref, out, pr = _oracle_grads(sc, cam, target)
+    assert abs(loss.item() - L) <= 1e-6
+    ok = out["flags"].numpy() == 0
+    uu, vv = out["u"].numpy(), out["v"].numpy()
+    bad = OR.contributors(pr, np.stack([uu[~ok], vv[~ok]], 1), CFG.alpha_min)
+    keep = np.ones(sc.n, bool)
+    keep[bad] = False
+    assert keep.mean() > 0.9
+    names = ["d_means", "d_scales", "d_rotations", "d_opacities", "d_sh"]
+    for name, r in zip(names, ref):
+        gg = grads[name].cpu().double().numpy()
+        _assert_grad_close(name, gg, r, keep)
+
+
+def test_autograd_function_and_recompute():
+    """The torch.autograd.Function gives the same gradients whether the sorted
+    lists are kept or rebuilt in backward."""
+    _need_gpu()
+    sc, cam, target = _grad_case(seed=3, deg=1)
+    g = raster.GaussianTensors.from_scene(sc)
+    tgt = torch.as_tensor(target.reshape(-1)).cuda()
+    res = []
+    for recompute in (False, True):
+        ps = [t.clone().requires_grad_(True) for t in (g.means, g.scales, g.rotations, g.opacities, g.sh)]
+        st = raster.RasterSettings([cam], 1, recompute_sort=recompute)
+        img, depth, imax, wsum, area = raster.rasterize(*ps, st)
+        L = torch.abs(img - tgt).mean()
+        L.backward()
+        res.append([p.grad.clone() for p in ps])
+    for a, b in zip(*res):
+        assert torch.allclose(a, b, rtol=1e-5, atol=1e-7)
+
+
+# ---------------------------------------------------------------- edge cases
+def test_edge_cases():
+    _need_gpu()
+    cam = scenes.origin_camera(37, 21, 40.0)
+    # empty scene
+    sc = scenes.box_scene(0, seed=1)
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, [cam])
+    assert fr.plan.n_entries == 0
+    assert torch.all(fr.outs["image"] == 0) and torch.all(fr.outs["final_T"] == 1)
+    assert torch.all(fr.outs["imax"] == -1)
+    # everything behind the camera or too transparent
+    sc = scenes.box_scene(64, seed=1)
+    sc.means[:32, 2] = -3.0
+    sc.opacities[32:] = 1.0 / 512
+    fr = raster.forward(raster.GaussianTensors.from_scene(sc), [cam])
+    assert fr.plan.n_entries == 0
+    # one huge Gaussian covering every tile, plus the termination stack
+    zs = 4.0 + 0.25 * np.arange(20)
+    sc = scenes.box_scene(21, seed=1)
+    sc.means[:20, 2] = zs
+    sc.means[:20, 0] = (17 + 0.5 - 18.5) * zs / 40.0
+    sc.means[:20, 1] = (9 + 0.5 - 10.5) * zs / 40.0
+    sc.scales[:20] = 0.02
+    sc.opacities[:20] = 0.5
+    sc.rotations[:20] = [1, 0, 0, 0]
+    sc.means[20] = [0, 0, 30.0]
+    sc.scales[20] = 5.0
+    sc.opacities[20] = 0.3
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, [cam])
+    _check_render(sc, [cam], fr)
+    assert fr.plan.n_entries >= fr.plan.total_tiles
+
+
+def test_loss_l1_kernel():
+    _need_gpu()
+    rng = np.random.default_rng(0)
+    a = torch.tensor(rng.uniform(0, 1, 100003), dtype=torch.float32, device="cuda")
+    b = torch.tensor(rng.uniform(0, 1, 100003), dtype=torch.float32, device="cuda")
+    loss = torch.zeros(1, device="cuda")
+    dL = torch.empty_like(a)
+    raster.loss_l1(a, b, loss, dL)
+    ref = torch.abs(a.double() - b.double()).mean().item()
+    assert abs(loss.item() - ref) <= 1e-6
+    assert torch.equal(dL, torch.sign(a - b) / a.numel())
+
+
+# ---------------------------------------------------------------- full size
+def test_training_scale_sampled_pixels():
+    """500k Gaussians (SH 3), one 1600x1063 ring view: the oracle evaluates 96
+    sampled pixels one by one; sort invariants checked on the whole list."""
+    _need_gpu()
+    sc = scenes.cluster_scene(500_000, 64, seed=0, sh_degree=3)
+    cam = scenes.ring_camera(0.3, 1600, 1063)
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, [cam])
+    torch.cuda.synchronize()
+    assert raster.device_status(fr.plan, fr.pre_ws) == 0
+    rng = np.random.default_rng(7)
+    pix = np.stack([rng.integers(0, cam.width, 96), rng.integers(0, cam.height, 96)], 1)
+    _, out = _oracle_view(sc, cam, pix=pix)
+    ok = out["flags"].numpy() == 0
+    assert ok.sum() >= 90
+    lin = pix[:, 1] * cam.width + pix[:, 0]
+    col = _gpu_colour(fr, 0).numpy()[lin]
+    assert np.abs(col - out["colour"].numpy())[ok].max() <= 1e-4
+    d = _gpu_pixels(fr, 0, "depth").double().numpy()[lin]
+    dref = out["depth"].numpy()
+    assert np.all(np.abs(d - dref)[ok] <= 1e-4 * np.maximum(1, np.abs(dref[ok])))
+    np.testing.assert_array_equal(_gpu_pixels(fr, 0, "imax").numpy()[lin][ok], out["imax"].numpy()[ok])
+    so = raster.inspect_sort(fr)
+    st = raster.inspect_preprocess(fr)
+    t = so["tile_ids"].numpy().astype(np.int64)
+    it = so["items"].numpy().astype(np.int64)
+    assert np.all(np.diff(t) >= 0)
+    z = st["xy_tau_z"][:, 3].numpy()[it]
+    same = np.diff(t) == 0
+    dz = np.diff(z.view(np.uint32).astype(np.int64))
+    assert np.all(dz[same] >= 0)
+    assert np.all(np.diff(it)[same & (dz == 0)] > 0)
+    assert np.bincount(it, minlength=sc.n).sum() == fr.plan.n_entries
