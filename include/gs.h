@@ -201,6 +201,29 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
                         const float* final_T, const uint32_t* n_contrib,
                         const gs_grads* grads, void* stream);
 
+/* ---- allocation-free variant ------------------------------------------ */
+
+/* No counterpart in the paper: an engineering variant of gs_bin_sort for
+ * callers that cannot allocate device memory when they render (a host
+ * application that owns all GPU memory and hands out fixed buffers, code
+ * where an allocation could block or fail mid-frame).  It computes exactly
+ * what gs_bin_sort computes, but the caller passes the outputs directly
+ * (tile_ids and items: device [n_entries] uint32; ranges: device
+ * [total_tiles][2] uint32, [start, end) per tile) and the sort's scratch comes
+ * from a fixed file-scope device array of GS_NOALLOC_SCRATCH_BYTES that every
+ * GPU loading the library keeps until exit; nothing is allocated.
+ *  - plan->n_entries above GS_NOALLOC_MAX_ENTRIES: GS_ERR_CAPACITY, nothing
+ *    launched (use gs_bin_sort with a caller workspace instead).
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls share the array; each clears the parts that must start at
+ *    zero, but calls that overlap on the GPU (other streams or threads) race.
+ * pre_ws is the workspace of the gs_preprocess call that filled `plan`. */
+#define GS_NOALLOC_MAX_ENTRIES (1 << 19)
+#define GS_NOALLOC_SCRATCH_BYTES (5u << 20)
+gs_status gs_bin_sort_noalloc(const gs_plan* plan, void* pre_ws, uint32_t* tile_ids,
+                              uint32_t* items, uint32_t* ranges, void* stream);
+
 /* ---- training-step helpers ------------------------------------------- */
 
 /* Mean absolute error over `count` elements and its gradient (the L1 term

@@ -107,6 +107,18 @@ bool valid_plan(const gs_plan* p) {
 }
 
 }  // namespace
+
+// Pointers into a preprocess workspace for another translation unit.
+void preprocess_parts(const gs_plan* plan, void* pre_ws, const ViewDev** views, ItemState* st,
+                      const uint32_t** sorted_items, const uint32_t** offsets, uint32_t** status) {
+  const PreLayout L = pre_layout(*plan);
+  *views = at<ViewDev>(pre_ws, L.views);
+  *st = item_state(pre_ws, L);
+  *sorted_items = at<uint32_t>(pre_ws, L.sorted_items);
+  *offsets = at<uint32_t>(pre_ws, L.offsets);
+  *status = at<uint32_t>(pre_ws, L.status);
+}
+
 }  // namespace gs
 
 using namespace gs;
