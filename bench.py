@@ -163,7 +163,7 @@ class Step:
         r.render_fwd(self.plan, self.cfg, self.pre_ws, self.sort_ws, self.outs)
         r.loss_l1(self.outs["image"], self.target, self.loss, self.dL)
         r.render_bwd(self.plan, self.g.struct(), self.cfg, self.pre_ws, self.sort_ws, self.dL,
-                     self.outs["final_T"], self.outs["n_contrib"], self.grads)
+                     self.outs["image"], self.outs["n_contrib"], self.grads)
 
 
 def kernel_times(collect=True) -> dict:

@@ -113,8 +113,8 @@ typedef struct gs_plan {
   int64_t pixel_base[GS_MAX_VIEWS + 1];
 } gs_plan;
 
-/* Forward outputs, device.  image and final_T / n_contrib are required (the
- * backward pass reads the last two); the rest may be NULL.  The per-view
+/* Forward outputs, device.  image, final_T and n_contrib are required (the
+ * backward pass reads image and n_contrib); the rest may be NULL.  The per-view
  * per-Gaussian arrays are indexed by item and ACCUMULATED (+=). */
 typedef struct gs_fwd_outputs {
   float* image;             /* [3 * total_pixels] planar per view: c(x) + T bg (Eq. 1) */
@@ -190,15 +190,17 @@ gs_status gs_render_fwd(const gs_plan* plan, const gs_config* cfg, void* pre_ws,
 
 /* Gradients of a loss L with respect to the Gaussian attributes, given
  * dL/d image (device, [3 * total_pixels], planar like the image) and the
- * forward's final_T and n_contrib: reverse replay of Eq. 1 per pixel, then
- * the chain rule through the projection and SH colour.  The clamps pass no
- * gradient (alpha at alpha_max, colour at 0, the clamped Jacobian
- * coordinate); the thresholds are constants.  The scene must be the one
- * passed to gs_preprocess.  pre_ws is also written (its 2-D gradient
- * scratch). */
+ * forward's image and n_contrib: for every blended entry l of a pixel,
+ * dI/dc_l = w_l and dI/dalpha_l = T_l c_l - (I - F_l) / (1 - alpha_l) with
+ * F_l the colour blended up to and including l (the derivative of Eq. 1),
+ * then the chain rule through alpha = min(alpha_max, o G), the conic, the
+ * projection and the SH colour.  The clamps pass no gradient (alpha at
+ * alpha_max, colour below 0, the clamped Jacobian coordinate); the
+ * thresholds are constants.  The scene must be the one passed to
+ * gs_preprocess.  pre_ws is also written (its 2-D gradient scratch). */
 gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_config* cfg,
                         void* pre_ws, const void* sort_ws, const float* dL_dimage,
-                        const float* final_T, const uint32_t* n_contrib,
+                        const float* image, const uint32_t* n_contrib,
                         const gs_grads* grads, void* stream);
 
 /* ---- allocation-free variant ------------------------------------------ */

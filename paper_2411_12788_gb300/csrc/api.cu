@@ -284,10 +284,10 @@ gs_status gs_render_fwd(const gs_plan* plan, const gs_config* cfg, void* pre_ws,
 }
 
 gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_config* cfg, void* pre_ws,
-                        const void* sort_ws, const float* dL_dimage, const float* final_T,
+                        const void* sort_ws, const float* dL_dimage, const float* image,
                         const uint32_t* n_contrib, const gs_grads* g, void* stream_) {
   if (!valid_plan(plan) || !valid_config(cfg) || !valid_scene(plan, scene) || plan->n_entries < 0 || !pre_ws ||
-      !sort_ws || !dL_dimage || !final_T || !n_contrib || !g)
+      !sort_ws || !dL_dimage || !image || !n_contrib || !g)
     return GS_ERR_INVALID_ARG;
   if (!g->d_means || !g->d_scales || !g->d_rotations || !g->d_opacities || !g->d_sh) return GS_ERR_INVALID_ARG;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
@@ -307,7 +307,7 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
   const ItemState st = item_state(pre_ws, L);
   float4* grad2d = at<float4>(pre_ws, L.grad2d);
   e = launch_render_bwd(at<ViewDev>(pre_ws, L.views), plan->n_views, n, plan->total_tiles,
-                        at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals), st, *cfg, dL_dimage, final_T,
+                        at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals), st, *cfg, dL_dimage, image,
                         n_contrib, grad2d, stream);
   if (e == cudaSuccess)
     e = launch_preprocess_backward(*scene, at<ViewDev>(pre_ws, L.views), plan->n_views, *cfg, st.tiles, grad2d, *g,

@@ -15,11 +15,12 @@
 // global atomic per (tile, entry)) and the maximum-contribution area S_i
 // (Sec. 4.1; warp-aggregated atomics).
 //
-// Backward: per pixel, entries are replayed back to front from n_contrib,
-// recovering T_k by division, and the nine per-entry gradients
-// (centre 2, conic 3, opacity 1, colour 3) are reduced across the warp with
-// shuffles before touching shared memory, then added to the per-item
-// gradient buffer with one vector atomic per (tile, entry).
+// Backward: one lane per entry, a warp walking its pixels front to back with
+// lane scans for the transmittance and the colour in front (see the kernel),
+// so each entry's nine gradients (centre 2, conic 3, opacity 1, colour 3)
+// accumulate in registers; they are combined across the CTA's warps in
+// shared memory and added to the per-item gradient buffer with one vector
+// atomic per (tile, entry).
 #include "project.cuh"
 
 namespace gs {
@@ -209,7 +210,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(RenderParams
 
 struct BwdIn {
   const float* dL_dimage;
-  const float* final_T;
+  const float* image;           // forward output c(x) + T_final bg
   const uint32_t* n_contrib;
   float4* grad2d;               // 3 x float4 per item
 };
@@ -218,7 +219,22 @@ __device__ __forceinline__ void atomic_add_f4(float4* addr, float4 v) {
   atomicAdd(addr, v);
 }
 
+// Backward of Eq. 1, one lane per entry.  For pixel x with blended entries
+// k (alpha_k, colour c_k, w_k = alpha_k T_k) and image I = sum w_k c_k + T bg:
+//   dI/dc_l     = w_l
+//   dI/dalpha_l = T_l c_l - (I - F_l) / (1 - alpha_l),  F_l = sum_{k<=l} w_k c_k
+// so with g = dL/dI the only per-pixel quantities a lane needs are the
+// exclusive product T_l of (1 - alpha) and the inclusive sum of
+// w_k (c_k . g) over the entries in front of it.  A warp takes 32 consecutive
+// entries of the tile's list (one per lane) and walks its 32 pixels; both
+// prefix quantities are 5-step shuffle scans across the lanes, continued from
+// chunk to chunk through per-pixel state in shared memory.  Each lane sums
+// its entry's nine gradients over the pixels in registers, so no per-entry
+// reduction across pixels is needed.  Entries at or after a pixel's
+// n_contrib and entries with alpha < alpha_min do not take part, exactly as
+// in the forward pass.
 __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams P, BwdIn B) {
+  constexpr int kWarps = kRenderThreads / 32;
   __shared__ int s_view;
   __shared__ uint32_t s_max_nc;
   __shared__ float2 s_xy[kRenderThreads];
@@ -226,49 +242,61 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
   __shared__ float4 s_rgb[kRenderThreads];
   __shared__ uint32_t s_item[kRenderThreads];
   __shared__ float s_g[9][kRenderThreads];
+  // per-pixel state, indexed by the pixel's thread id (warp w owns 32w..32w+31)
+  __shared__ float4 s_pg[kRenderThreads];     // dL/dI (r, g, b) and I . dL/dI
+  __shared__ float s_T[kRenderThreads];       // transmittance before the next chunk
+  __shared__ float s_F[kRenderThreads];       // sum of w (c . g) so far
+  __shared__ uint32_t s_nc[kRenderThreads];
+  __shared__ uint32_t s_warp_nc[kWarps];
 
   const int tile = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     s_view = find_view(P.views, P.n_views, tile);
     s_max_nc = 0;
   }
+  __syncthreads();
+  const ViewDev& V = P.views[s_view];
+  const uint2 range = P.ranges[tile];
+  // this thread's pixel: load its state
+  {
+    int px, py;
+    pixel_of(V, tile, &px, &py);
+    const bool inside = px < V.width && py < V.height;
+    float4 pg = make_float4(0.f, 0.f, 0.f, 0.f);
+    uint32_t nc = 0;
+    if (inside) {
+      const int64_t pix = V.pixel_base + (int64_t)py * V.width + px;
+      const int64_t hw = (int64_t)V.width * V.height;
+      const int64_t o3 = 3 * V.pixel_base + (int64_t)py * V.width + px;
+      pg.x = B.dL_dimage[o3];
+      pg.y = B.dL_dimage[o3 + hw];
+      pg.z = B.dL_dimage[o3 + 2 * hw];
+      pg.w = B.image[o3] * pg.x + B.image[o3 + hw] * pg.y + B.image[o3 + 2 * hw] * pg.z;
+      nc = B.n_contrib[pix];
+    }
+    s_pg[tid] = pg;
+    s_T[tid] = 1.f;
+    s_F[tid] = 0.f;
+    s_nc[tid] = nc;
+    const uint32_t wm = __reduce_max_sync(0xffffffffu, nc);
+    if (lane == 0) {
+      s_warp_nc[warp] = wm;
+      atomicMax(&s_max_nc, wm);
+    }
+  }
 #pragma unroll
   for (int k = 0; k < 9; ++k) s_g[k][tid] = 0.f;
   __syncthreads();
-  const ViewDev& V = P.views[s_view];
-  int px, py;
-  pixel_of(V, tile, &px, &py);
-  const bool inside = px < V.width && py < V.height;
-  const float fxp = (float)px + 0.5f, fyp = (float)py + 0.5f;
-  const uint2 range = P.ranges[tile];
-
-  float T = 1.f, Tfin = 1.f, dpix[3] = {0.f, 0.f, 0.f};
-  uint32_t nc = 0;
-  if (inside) {
-    const int64_t pix = V.pixel_base + (int64_t)py * V.width + px;
-    const int64_t hw = (int64_t)V.width * V.height;
-    const float* g = B.dL_dimage + 3 * V.pixel_base + (int64_t)py * V.width + px;
-    dpix[0] = g[0];
-    dpix[1] = g[hw];
-    dpix[2] = g[2 * hw];
-    Tfin = B.final_T[pix];
-    T = Tfin;
-    nc = B.n_contrib[pix];
-  }
-  {
-    const uint32_t wm = __reduce_max_sync(0xffffffffu, nc);
-    if (lane == 0) atomicMax(&s_max_nc, wm);
-  }
-  __syncthreads();
   const uint32_t max_nc = s_max_nc;
-  const float bg_dot = P.bg[0] * dpix[0] + P.bg[1] * dpix[1] + P.bg[2] * dpix[2];
-  float acc[3] = {0.f, 0.f, 0.f}, last_alpha = 0.f, last_col[3] = {0.f, 0.f, 0.f};
+  const uint32_t warp_nc = s_warp_nc[warp];
+  // pixel centres of this warp's 32 pixels (same layout as pixel_of)
+  const int local = tile - V.tile_base;
+  const float tx0 = (float)((local % V.tiles_x) * kTile) + (float)((warp & 1) * 8) + 0.5f;
+  const float ty0 = (float)((local / V.tiles_x) * kTile) + (float)((warp >> 1) * 4) + 0.5f;
 
-  for (int bend = (int)max_nc; bend > 0; bend -= kRenderThreads) {
-    const int bstart = max(bend - kRenderThreads, 0);
-    const int nb = bend - bstart;
-    __syncthreads();
+  for (uint32_t bstart = 0; bstart < max_nc; bstart += kRenderThreads) {
+    const int nb = (int)min(max_nc - bstart, (uint32_t)kRenderThreads);
     if (tid < nb) {
       const uint32_t item = P.vals[range.x + bstart + tid];
       s_item[tid] = item;
@@ -278,55 +306,76 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
       s_rgb[tid] = P.rgb[item];
     }
     __syncthreads();
-    for (int jj = nb - 1; jj >= 0; --jj) {
-      const uint32_t pos = (uint32_t)(bstart + jj);
-      float g[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      bool act = false;
-      if (pos < nc) {
-        const float2 m = s_xy[jj];
-        const float4 co = s_co[jj];
-        const float dx = fxp - m.x, dy = fyp - m.y;
+    for (int c = 0; c < nb; c += 32) {
+      const uint32_t c0 = bstart + c;
+      if (c0 >= warp_nc) break;
+      const int e = c + lane;                         // my entry in the batch
+      const bool valid = e < nb;
+      const float2 m = valid ? s_xy[e] : make_float2(0.f, 0.f);
+      const float4 co = valid ? s_co[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float4 col = valid ? s_rgb[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const uint32_t pos = c0 + lane;
+      float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int p = 0; p < 32; ++p) {
+        const int pt = warp * 32 + p;                 // the pixel's thread id
+        const uint32_t nc = s_nc[pt];
+        if (c0 >= nc) continue;                       // pixel stopped before this chunk
+        const float dx = tx0 + (float)(p & 7) - m.x, dy = ty0 + (float)(p >> 3) - m.y;
         float G;
         bool clamped;
         const float alpha = splat_alpha(co, dx, dy, P.alpha_max, &G, &clamped);
-        if (alpha >= P.alpha_min) {
-          act = true;
-          const float one_m = 1.f - alpha;
-          T = T / one_m;
-          const float w = alpha * T;
-          const float4 c = s_rgb[jj];
-          g[6] = w * dpix[0];
-          g[7] = w * dpix[1];
-          g[8] = w * dpix[2];
-          acc[0] = last_alpha * last_col[0] + (1.f - last_alpha) * acc[0];
-          acc[1] = last_alpha * last_col[1] + (1.f - last_alpha) * acc[1];
-          acc[2] = last_alpha * last_col[2] + (1.f - last_alpha) * acc[2];
-          float dal = (c.x - acc[0]) * dpix[0] + (c.y - acc[1]) * dpix[1] + (c.z - acc[2]) * dpix[2];
-          dal *= T;
-          last_alpha = alpha;
-          last_col[0] = c.x;
-          last_col[1] = c.y;
-          last_col[2] = c.z;
-          dal += -Tfin / one_m * bg_dot;
+        const bool act = valid && pos < nc && alpha >= P.alpha_min;
+        if (!__any_sync(0xffffffffu, act)) continue;
+        const float a = act ? alpha : 0.f;
+        // exclusive product of (1 - a) over lanes, continued from s_T
+        float prod = 1.f - a;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const float t = __shfl_up_sync(0xffffffffu, prod, off);
+          if (lane >= off) prod *= t;
+        }
+        float excl = __shfl_up_sync(0xffffffffu, prod, 1);
+        if (lane == 0) excl = 1.f;
+        const float T0 = s_T[pt];
+        const float Tl = T0 * excl;
+        const float w = a * Tl;
+        const float4 pg = s_pg[pt];
+        const float cg = col.x * pg.x + col.y * pg.y + col.z * pg.z;
+        float fs = w * cg;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+          const float t = __shfl_up_sync(0xffffffffu, fs, off);
+          if (lane >= off) fs += t;
+        }
+        const float F0 = s_F[pt];
+        const float total_prod = __shfl_sync(0xffffffffu, prod, 31);
+        const float total_fs = __shfl_sync(0xffffffffu, fs, 31);
+        __syncwarp();
+        if (lane == 0) {
+          s_T[pt] = T0 * total_prod;
+          s_F[pt] = F0 + total_fs;
+        }
+        if (act) {
+          acc[6] += w * pg.x;
+          acc[7] += w * pg.y;
+          acc[8] += w * pg.z;
           if (!clamped) {
-            const float dG = co.w * dal;
-            g[5] = G * dal;
-            const float dq = -0.5f * G * dG;
-            g[2] = dq * dx * dx;
-            g[3] = dq * 2.f * dx * dy;
-            g[4] = dq * dy * dy;
+            const float dal = Tl * cg - (pg.w - (F0 + fs)) / (1.f - a);
+            acc[5] += G * dal;
+            const float dq = -0.5f * G * co.w * dal;
+            acc[2] += dq * dx * dx;
+            acc[3] += dq * 2.f * dx * dy;
+            acc[4] += dq * dy * dy;
             // d = pixel - centre, so dq/dcentre = -(2 A dx + 2 B dy, 2 B dx + 2 C dy)
-            g[0] = -dq * (2.f * co.x * dx + 2.f * co.y * dy);
-            g[1] = -dq * (2.f * co.y * dx + 2.f * co.z * dy);
+            acc[0] -= dq * (2.f * co.x * dx + 2.f * co.y * dy);
+            acc[1] -= dq * (2.f * co.y * dx + 2.f * co.z * dy);
           }
         }
       }
-      if (__any_sync(0xffffffffu, act)) {
+      if (valid) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          const float s = warp_sum(g[k]);
-          if (lane == 0 && s != 0.f) atomicAdd(&s_g[k][jj], s);
-        }
+        for (int k = 0; k < 9; ++k)
+          if (acc[k] != 0.f) atomicAdd(&s_g[k][e], acc[k]);
       }
     }
     __syncthreads();
@@ -343,6 +392,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
       if (v[4] != 0.f || v[5] != 0.f || v[6] != 0.f || v[7] != 0.f) atomic_add_f4(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
       if (v[8] != 0.f) atomicAdd(&dst[2].x, v[8]);
     }
+    __syncthreads();
   }
 }
 
@@ -381,10 +431,10 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
 
 cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
                               const uint32_t* vals, const ItemState& st, const gs_config& cfg,
-                              const float* dL_dimage, const float* final_T, const uint32_t* n_contrib,
+                              const float* dL_dimage, const float* image, const uint32_t* n_contrib,
                               float4* grad2d, cudaStream_t stream) {
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
-  BwdIn B{dL_dimage, final_T, n_contrib, grad2d};
+  BwdIn B{dL_dimage, image, n_contrib, grad2d};
   if (total_tiles > 0) GS_TIMED("render_bwd", stream, (render_bwd_kernel<<<total_tiles, kRenderThreads, 0, stream>>>(P, B)));
   return cudaGetLastError();
 }

@@ -124,14 +124,14 @@ def render_fwd(plan, cfg, pre_ws, sort_ws, outs: dict, stream=None) -> None:
                                                C.byref(o), _stream(stream)))
 
 
-def render_bwd(plan, scene: _lib.Scene, cfg, pre_ws, sort_ws, dL_dimage, final_T, n_contrib,
+def render_bwd(plan, scene: _lib.Scene, cfg, pre_ws, sort_ws, dL_dimage, image, n_contrib,
                grads: dict, stream=None) -> None:
     g = _lib.Grads()
     for name, _ in _lib.Grads._fields_:
         t = grads.get(name)
         setattr(g, name, None if t is None else t.data_ptr())
     check("gs_render_bwd", lib().gs_render_bwd(C.byref(plan), C.byref(scene), C.byref(cfg), _ptr(pre_ws),
-                                               _ptr(sort_ws), _ptr(dL_dimage), _ptr(final_T),
+                                               _ptr(sort_ws), _ptr(dL_dimage), _ptr(image),
                                                _ptr(n_contrib), C.byref(g), _stream(stream)))
 
 
@@ -255,7 +255,7 @@ def backward(g: GaussianTensors, fr: Frame, dL_dimage: torch.Tensor, stream=None
         bin_sort(fr.plan, fr.pre_ws, fr.sort_ws, stream)
     grads = alloc_grads(g)
     render_bwd(fr.plan, g.struct(), fr.cfg, fr.pre_ws, fr.sort_ws, dL_dimage.contiguous(),
-               fr.outs["final_T"], fr.outs["n_contrib"], grads, stream)
+               fr.outs["image"], fr.outs["n_contrib"], grads, stream)
     return grads
 
 
