@@ -103,12 +103,21 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* _
   if (cnt > 0 && written != cnt) atomicOr(status, kStatusEntryMismatch);
 }
 
-__global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges) {
-  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= n) return;
-  const uint32_t t = keys[e];
-  if (e == 0 || keys[e - 1] != t) ranges[t].x = (uint32_t)e;
-  if (e == n - 1 || keys[e + 1] != t) ranges[t].y = (uint32_t)(e + 1);
+// [start, end) of every tile in the sorted key list by binary search: thread
+// t finds the first entry with key >= t, which starts tile t and ends tile
+// t - 1 (t = total_tiles closes the last tile).
+__global__ void ranges_kernel(const uint32_t* __restrict__ keys, int64_t n, uint2* __restrict__ ranges,
+                              int total_tiles) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t > total_tiles) return;
+  int64_t lo = 0, hi = n;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (keys[mid] < (uint32_t)t) lo = mid + 1;
+    else hi = mid;
+  }
+  if (t < total_tiles) ranges[t].x = (uint32_t)lo;
+  if (t > 0) ranges[t - 1].y = (uint32_t)lo;
 }
 
 __global__ void l1_kernel(const float* __restrict__ img, const float* __restrict__ tgt, int64_t count,
@@ -154,10 +163,10 @@ cudaError_t launch_duplicate(const ViewDev* views, int n_views, int64_t n_items,
 
 cudaError_t launch_ranges(const uint32_t* keys, int64_t n_entries, uint2* ranges, int total_tiles,
                           cudaStream_t stream) {
-  cudaError_t e = cudaMemsetAsync(ranges, 0, (size_t)total_tiles * sizeof(uint2), stream);
-  if (e != cudaSuccess) return e;
-  if (n_entries > 0)
-    GS_TIMED("ranges", stream, (ranges_kernel<<<ceil_div(n_entries, 256), 256, 0, stream>>>(keys, n_entries, ranges)));
+  if (total_tiles > 0)
+    GS_TIMED("ranges", stream,
+             (ranges_kernel<<<ceil_div((int64_t)total_tiles + 1, 256), 256, 0, stream>>>(keys, n_entries, ranges,
+                                                                                         total_tiles)));
   return cudaGetLastError();
 }
 

@@ -16,6 +16,8 @@ namespace gs {
 namespace {
 
 constexpr int kPreThreads = 128;
+constexpr float kLog2eF = 1.4426950408889634f;
+constexpr float kLn2F = 0.6931471805599453f;
 
 struct PreParams {
   const float* means;
@@ -260,6 +262,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(PreBwd
                         M[0] * M[6] + M[1] * M[7] + M[2] * M[8], M[3] * M[3] + M[4] * M[4] + M[5] * M[5],
                         M[3] * M[6] + M[4] * M[7] + M[5] * M[8], M[6] * M[6] + M[7] * M[7] + M[8] * M[8]};
   const float* shrow = P.sh + i * (int64_t)P.sh_coeffs * 3;
+  const float opac_i = P.opac[i];
 
   float dp[3] = {0.f, 0.f, 0.f};
   float dSig[6] = {0, 0, 0, 0, 0, 0};       // symmetric dL/dSigma (00,01,02,11,12,22)
@@ -274,8 +277,11 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(PreBwd
     any = true;
     const ViewDev& V = P.views[v];
     const float4 g0 = P.grad2d[3 * item], g1 = P.grad2d[3 * item + 1], g2 = P.grad2d[3 * item + 2];
-    const float dmx = g0.x, dmy = g0.y, dA = g0.z, dB = g0.w, dC = g1.x;
-    dop += g1.y;
+    // the render backward differentiates the exponent form
+    // e = log2 o - log2(e) (A dx^2 / 2 + B dx dy + C dy^2 / 2): convert to (A, B, C, o)
+    const float dmx = g0.x, dmy = g0.y;
+    const float dA = -0.5f * kLog2eF * g0.z, dB = -kLog2eF * g0.w, dC = -0.5f * kLog2eF * g1.x;
+    dop += g1.y / (opac_i * kLn2F);
     m2abs += sqrtf(dmx * dmx + dmy * dmy);
     const float drgb[3] = {g1.z, g1.w, g2.x};
 

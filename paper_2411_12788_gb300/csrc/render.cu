@@ -1,26 +1,33 @@
-// Per-tile front-to-back alpha blending (Eq. 1) and its reverse replay.
+// Per-tile front-to-back alpha blending (Eq. 1) and its derivative.
 //
-// One CTA of 256 threads per 16x16 tile, one thread per pixel; each warp
-// owns an 8x4 block of the tile so that a Gaussian's footprint touches few
-// warps.  The tile's depth-ordered list is streamed through shared memory in
-// batches of 256 entries ({centre, conic, opacity, colour, depth}, gathered
-// by item id); a thread stops when its transmittance would drop below t_min
-// and the CTA leaves the list once all its pixels have stopped.
+// One CTA of 256 threads per 16x16 tile; each warp owns an 8x4 block of the
+// tile.  The tile's depth-ordered list is streamed through shared memory in
+// batches of 256 entries, gathered by item id.  Per entry the batch holds its
+// centre, colour, depth and the 2-D Gaussian in exponent form:
+//   alpha_raw(x) = o exp(-q/2) = 2^e,  e = log2 o + a2 dx^2 + b2 dx dy + c2 dy^2
+// with (a2, b2, c2) = -log2(e) (A/2, B, C/2) for the conic (A, B, C).  An entry
+// takes part at a pixel iff e >= log2(alpha_min) (that is alpha >= alpha_min);
+// then alpha = min(alpha_max, 2^e).  Forward and backward evaluate e with the
+// same explicitly rounded operations, so they make identical decisions.
 //
-// Forward side outputs (what the paper's reorganisation reads): i_max =
-// argmax_i w_i with its weight, the midpoint depth d^mid_{i_max} (Eq. 2,
+// Forward (one thread per pixel): front-to-back blending with a per-pixel
+// stop before T (1 - alpha) < t_min, the CTA leaving the list once all its
+// pixels stopped.  Side outputs (what the paper's reorganisation reads):
+// i_max = argmax_i w_i and w_max, the midpoint depth d^mid_{i_max} (Eq. 2,
 // Sec. 4.1) evaluated once per pixel from the winner's ellipsoid frame, the
 // blended depth sum_i w_i z_i, the per-Gaussian accumulated weight I_i
-// (Sec. 3.2; warp-reduced, then one shared-memory add per warp and one
-// global atomic per (tile, entry)) and the maximum-contribution area S_i
-// (Sec. 4.1; warp-aggregated atomics).
+// (Sec. 3.2; each warp's weights are summed in 2^-24 fixed point by one
+// redux.sync, then one shared add per warp and one global atomic per
+// (tile, entry)) and the maximum-contribution area S_i (Sec. 4.1;
+// warp-aggregated atomics).
 //
-// Backward: one lane per entry, a warp walking its pixels front to back with
-// lane scans for the transmittance and the colour in front (see the kernel),
-// so each entry's nine gradients (centre 2, conic 3, opacity 1, colour 3)
-// accumulate in registers; they are combined across the CTA's warps in
-// shared memory and added to the per-item gradient buffer with one vector
-// atomic per (tile, entry).
+// Backward: one lane per entry, a warp walking its pixels with lane scans
+// for the transmittance and the colour in front (see render_bwd_kernel);
+// gradients accumulate in registers, are combined across the CTA's warps in
+// shared memory and added to the per-item buffer with one vector atomic per
+// (tile, entry).  They are taken with respect to (centre, a2, b2, c2,
+// log2 o, colour); the preprocess backward converts them to the conic and
+// the opacity.
 #include "project.cuh"
 
 namespace gs {
@@ -28,6 +35,8 @@ namespace gs {
 namespace {
 
 constexpr int kRenderThreads = kTilePixels;
+constexpr float kLog2e = 1.4426950408889634f;
+constexpr float kLn2 = 0.6931471805599453f;
 
 struct RenderParams {
   const ViewDev* views;
@@ -39,7 +48,7 @@ struct RenderParams {
   const float4* conic_o;
   const float4* rgb;
   const float4* depth_frame;
-  float alpha_max, alpha_min, t_min;
+  float alpha_max, e_min, t_min;   // e_min = log2(alpha_min)
   float bg[3];
 };
 
@@ -55,16 +64,52 @@ struct FwdOut {
   uint32_t* max_area;
 };
 
-// alpha = min(alpha_max, o exp(-q/2)) with explicit rounding so that the
-// forward and backward kernels make identical skip decisions.
-__device__ __forceinline__ float splat_alpha(float4 co, float dx, float dy, float alpha_max, float* G_out,
-                                             bool* clamped) {
-  const float q = conic_q(co.x, co.y, co.z, dx, dy);
-  const float G = __expf(__fmul_rn(-0.5f, q));
-  const float a = __fmul_rn(co.w, G);
-  *G_out = G;
-  *clamped = a > alpha_max;
-  return fminf(alpha_max, a);
+// Exponent form of an entry's 2-D Gaussian (identical in both kernels).
+__device__ __forceinline__ float4 exponent_form(float4 co) {
+  return make_float4(__fmul_rn(-0.5f * kLog2e, co.x), __fmul_rn(-kLog2e, co.y), __fmul_rn(-0.5f * kLog2e, co.z),
+                     __log2f(co.w));
+}
+
+// e = lo + a2 dx^2 + b2 dx dy + c2 dy^2, explicitly rounded.
+__device__ __forceinline__ float expo(float4 ex, float dx, float dy) {
+  const float t = __fmaf_rn(ex.x, dx, __fmul_rn(ex.y, dy));
+  const float u = __fmaf_rn(__fmul_rn(ex.z, dy), dy, ex.w);
+  return __fmaf_rn(t, dx, u);
+}
+
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float y;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// Inclusive lane scans (product / sum) in 2 instructions per step.
+__device__ __forceinline__ float scan_mul(float x) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1)
+    asm("{\n\t.reg .f32 t;\n\t.reg .pred p;\n\t"
+        "shfl.sync.up.b32 t|p, %0, %1, 0, 0xffffffff;\n\t"
+        "@p mul.f32 %0, %0, t;\n\t}"
+        : "+f"(x)
+        : "r"(off));
+  return x;
+}
+
+__device__ __forceinline__ float scan_add(float x) {
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1)
+    asm("{\n\t.reg .f32 t;\n\t.reg .pred p;\n\t"
+        "shfl.sync.up.b32 t|p, %0, %1, 0, 0xffffffff;\n\t"
+        "@p add.f32 %0, %0, t;\n\t}"
+        : "+f"(x)
+        : "r"(off));
+  return x;
 }
 
 __device__ __forceinline__ int find_view(const ViewDev* views, int n_views, int tile) {
@@ -74,43 +119,39 @@ __device__ __forceinline__ int find_view(const ViewDev* views, int n_views, int 
   return v;
 }
 
-__device__ __forceinline__ void pixel_of(const ViewDev& V, int tile, int* px, int* py) {
+// Pixel of thread `t` in the tile: warp t/32 owns the 8x4 block at
+// ((w & 1) * 8, (w >> 1) * 4), lane l is pixel (l & 7, l >> 3) of it.
+__device__ __forceinline__ void pixel_of(const ViewDev& V, int tile, int t, int* px, int* py) {
   const int local = tile - V.tile_base;
   const int tx = local % V.tiles_x, ty = local / V.tiles_x;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int warp = t >> 5, lane = t & 31;
   *px = tx * kTile + (warp & 1) * 8 + (lane & 7);
   *py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
-}
-
-__device__ __forceinline__ float warp_sum(float v) {
-#pragma unroll
-  for (int off = 16; off >= 1; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-  return v;
 }
 
 __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(RenderParams P, FwdOut O) {
   __shared__ int s_view;
   __shared__ float2 s_xy[kRenderThreads];
-  __shared__ float4 s_co[kRenderThreads];
+  __shared__ float4 s_ex[kRenderThreads];
   __shared__ float4 s_rgbz[kRenderThreads];
   __shared__ uint32_t s_item[kRenderThreads];
-  __shared__ float s_wsum[kRenderThreads];
+  __shared__ uint32_t s_wsum[kRenderThreads];    // 2^-24 fixed point
 
   const int tile = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) s_view = find_view(P.views, P.n_views, tile);
-  s_wsum[tid] = 0.f;
+  s_wsum[tid] = 0u;
   __syncthreads();
   const ViewDev& V = P.views[s_view];
   int px, py;
-  pixel_of(V, tile, &px, &py);
+  pixel_of(V, tile, tid, &px, &py);
   const bool inside = px < V.width && py < V.height;
   const float fxp = (float)px + 0.5f, fyp = (float)py + 0.5f;
   const uint2 range = P.ranges[tile];
   const bool want_w = O.weight_sum != nullptr;
 
   float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dblend = 0.f, wmax = 0.f;
-  int64_t imax_item = -1;
+  int imax_pos = -1;
   uint32_t last = 0;
   bool done = !inside;
 
@@ -122,7 +163,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(RenderParams
       s_item[tid] = item;
       const float4 a = P.xy_tau_z[item];
       s_xy[tid] = make_float2(a.x, a.y);
-      s_co[tid] = P.conic_o[item];
+      s_ex[tid] = exponent_form(P.conic_o[item]);
       const float4 c = P.rgb[item];
       s_rgbz[tid] = make_float4(c.x, c.y, c.z, a.w);
     }
@@ -133,11 +174,9 @@ __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(RenderParams
       float w = 0.f;
       if (!done) {
         const float2 m = s_xy[j];
-        const float4 co = s_co[j];
-        float G;
-        bool cl;
-        const float alpha = splat_alpha(co, fxp - m.x, fyp - m.y, P.alpha_max, &G, &cl);
-        if (alpha >= P.alpha_min) {
+        const float e = expo(s_ex[j], fxp - m.x, fyp - m.y);
+        if (e >= P.e_min) {
+          const float alpha = fminf(P.alpha_max, ex2_approx(e));
           const float Tn = T * (1.f - alpha);
           if (Tn < P.t_min) {
             done = true;
@@ -150,7 +189,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(RenderParams
             dblend += w * c.w;
             if (w > wmax) {
               wmax = w;
-              imax_item = s_item[j];
+              imax_pos = (int)(bstart - range.x) + j;
             }
             T = Tn;
             last = bstart - range.x + j + 1;
@@ -158,18 +197,19 @@ __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(RenderParams
         }
       }
       if (want_w && __any_sync(0xffffffffu, w > 0.f)) {
-        const float s = warp_sum(w);
+        const uint32_t s = __reduce_add_sync(0xffffffffu, __float2uint_rn(w * 16777216.f));
         if (lane == 0) atomicAdd(&s_wsum[j], s);
       }
     }
     __syncthreads();
     if (want_w && tid < nb) {
-      const float s = s_wsum[tid];
-      if (s > 0.f) atomicAdd(&O.weight_sum[s_item[tid]], s);
-      s_wsum[tid] = 0.f;
+      const uint32_t s = s_wsum[tid];
+      if (s) atomicAdd(&O.weight_sum[s_item[tid]], (float)s * (1.f / 16777216.f));
+      s_wsum[tid] = 0u;
     }
   }
 
+  const int64_t imax_item = imax_pos >= 0 ? (int64_t)P.vals[range.x + imax_pos] : -1;
   // S_i: pixels whose i_max is i (warp-aggregated)
   if (O.max_area) {
     const bool has = inside && imax_item >= 0;
@@ -215,10 +255,6 @@ struct BwdIn {
   float4* grad2d;               // 3 x float4 per item
 };
 
-__device__ __forceinline__ void atomic_add_f4(float4* addr, float4 v) {
-  atomicAdd(addr, v);
-}
-
 // Backward of Eq. 1, one lane per entry.  For pixel x with blended entries
 // k (alpha_k, colour c_k, w_k = alpha_k T_k) and image I = sum w_k c_k + T bg:
 //   dI/dc_l     = w_l
@@ -229,16 +265,16 @@ __device__ __forceinline__ void atomic_add_f4(float4* addr, float4 v) {
 // entries of the tile's list (one per lane) and walks its 32 pixels; both
 // prefix quantities are 5-step shuffle scans across the lanes, continued from
 // chunk to chunk through per-pixel state in shared memory.  Each lane sums
-// its entry's nine gradients over the pixels in registers, so no per-entry
+// its entry's gradients over the pixels in registers, so no per-entry
 // reduction across pixels is needed.  Entries at or after a pixel's
-// n_contrib and entries with alpha < alpha_min do not take part, exactly as
-// in the forward pass.
+// n_contrib and entries with e < log2(alpha_min) do not take part, exactly as
+// in the forward pass.  With alpha_raw = 2^e unclamped, dalpha/de = alpha ln 2.
 __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams P, BwdIn B) {
   constexpr int kWarps = kRenderThreads / 32;
   __shared__ int s_view;
   __shared__ uint32_t s_max_nc;
   __shared__ float2 s_xy[kRenderThreads];
-  __shared__ float4 s_co[kRenderThreads];
+  __shared__ float4 s_ex[kRenderThreads];
   __shared__ float4 s_rgb[kRenderThreads];
   __shared__ uint32_t s_item[kRenderThreads];
   __shared__ float s_g[9][kRenderThreads];
@@ -258,10 +294,9 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
   __syncthreads();
   const ViewDev& V = P.views[s_view];
   const uint2 range = P.ranges[tile];
-  // this thread's pixel: load its state
   {
     int px, py;
-    pixel_of(V, tile, &px, &py);
+    pixel_of(V, tile, tid, &px, &py);
     const bool inside = px < V.width && py < V.height;
     float4 pg = make_float4(0.f, 0.f, 0.f, 0.f);
     uint32_t nc = 0;
@@ -290,10 +325,9 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
   __syncthreads();
   const uint32_t max_nc = s_max_nc;
   const uint32_t warp_nc = s_warp_nc[warp];
-  // pixel centres of this warp's 32 pixels (same layout as pixel_of)
-  const int local = tile - V.tile_base;
-  const float tx0 = (float)((local % V.tiles_x) * kTile) + (float)((warp & 1) * 8) + 0.5f;
-  const float ty0 = (float)((local / V.tiles_x) * kTile) + (float)((warp >> 1) * 4) + 0.5f;
+  int bx, by;
+  pixel_of(V, tile, warp * 32, &bx, &by);        // this warp's first pixel
+  const float bxf = (float)bx + 0.5f, byf = (float)by + 0.5f;
 
   for (uint32_t bstart = 0; bstart < max_nc; bstart += kRenderThreads) {
     const int nb = (int)min(max_nc - bstart, (uint32_t)kRenderThreads);
@@ -302,38 +336,35 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
       s_item[tid] = item;
       const float4 a = P.xy_tau_z[item];
       s_xy[tid] = make_float2(a.x, a.y);
-      s_co[tid] = P.conic_o[item];
+      s_ex[tid] = exponent_form(P.conic_o[item]);
       s_rgb[tid] = P.rgb[item];
     }
     __syncthreads();
     for (int c = 0; c < nb; c += 32) {
       const uint32_t c0 = bstart + c;
       if (c0 >= warp_nc) break;
-      const int e = c + lane;                         // my entry in the batch
-      const bool valid = e < nb;
-      const float2 m = valid ? s_xy[e] : make_float2(0.f, 0.f);
-      const float4 co = valid ? s_co[e] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const float4 col = valid ? s_rgb[e] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const int e_idx = c + lane;                   // my entry in the batch
+      const bool valid = e_idx < nb;
+      const float2 m = valid ? s_xy[e_idx] : make_float2(0.f, 0.f);
+      // an invalid lane gets an exponent that never passes the e_min test
+      const float4 ex = valid ? s_ex[e_idx] : make_float4(0.f, 0.f, 0.f, -1e30f);
+      const float4 col = valid ? s_rgb[e_idx] : make_float4(0.f, 0.f, 0.f, 0.f);
       const uint32_t pos = c0 + lane;
+      const float dx0 = bxf - m.x, dy0 = byf - m.y;
       float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll 8
       for (int p = 0; p < 32; ++p) {
         const int pt = warp * 32 + p;                 // the pixel's thread id
         const uint32_t nc = s_nc[pt];
         if (c0 >= nc) continue;                       // pixel stopped before this chunk
-        const float dx = tx0 + (float)(p & 7) - m.x, dy = ty0 + (float)(p >> 3) - m.y;
-        float G;
-        bool clamped;
-        const float alpha = splat_alpha(co, dx, dy, P.alpha_max, &G, &clamped);
-        const bool act = valid && pos < nc && alpha >= P.alpha_min;
+        const float dx = dx0 + (float)(p & 7), dy = dy0 + (float)(p >> 3);
+        const float e = expo(ex, dx, dy);
+        const bool act = pos < nc && e >= P.e_min;
         if (!__any_sync(0xffffffffu, act)) continue;
-        const float a = act ? alpha : 0.f;
-        // exclusive product of (1 - a) over lanes, continued from s_T
-        float prod = 1.f - a;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const float t = __shfl_up_sync(0xffffffffu, prod, off);
-          if (lane >= off) prod *= t;
-        }
+        const float araw = ex2_approx(e);
+        const float a = act ? fminf(P.alpha_max, araw) : 0.f;
+        // exclusive product of (1 - a) over the lanes, continued from s_T
+        const float prod = scan_mul(1.f - a);
         float excl = __shfl_up_sync(0xffffffffu, prod, 1);
         if (lane == 0) excl = 1.f;
         const float T0 = s_T[pt];
@@ -341,12 +372,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
         const float w = a * Tl;
         const float4 pg = s_pg[pt];
         const float cg = col.x * pg.x + col.y * pg.y + col.z * pg.z;
-        float fs = w * cg;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-          const float t = __shfl_up_sync(0xffffffffu, fs, off);
-          if (lane >= off) fs += t;
-        }
+        const float fs = scan_add(w * cg);
         const float F0 = s_F[pt];
         const float total_prod = __shfl_sync(0xffffffffu, prod, 31);
         const float total_fs = __shfl_sync(0xffffffffu, fs, 31);
@@ -359,23 +385,23 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
           acc[6] += w * pg.x;
           acc[7] += w * pg.y;
           acc[8] += w * pg.z;
-          if (!clamped) {
-            const float dal = Tl * cg - (pg.w - (F0 + fs)) / (1.f - a);
-            acc[5] += G * dal;
-            const float dq = -0.5f * G * co.w * dal;
-            acc[2] += dq * dx * dx;
-            acc[3] += dq * 2.f * dx * dy;
-            acc[4] += dq * dy * dy;
-            // d = pixel - centre, so dq/dcentre = -(2 A dx + 2 B dy, 2 B dx + 2 C dy)
-            acc[0] -= dq * (2.f * co.x * dx + 2.f * co.y * dy);
-            acc[1] -= dq * (2.f * co.y * dx + 2.f * co.z * dy);
+          if (araw <= P.alpha_max) {
+            const float dal = Tl * cg - (pg.w - (F0 + fs)) * rcp_approx(1.f - a);
+            const float de = dal * a * kLn2;          // dL/de
+            acc[5] += de;                             // d log2 o
+            acc[2] += de * dx * dx;                   // d a2
+            acc[3] += de * dx * dy;                   // d b2
+            acc[4] += de * dy * dy;                   // d c2
+            // d = pixel - centre: de/dcentre = -(2 a2 dx + b2 dy, b2 dx + 2 c2 dy)
+            acc[0] -= de * (2.f * ex.x * dx + ex.y * dy);
+            acc[1] -= de * (ex.y * dx + 2.f * ex.z * dy);
           }
         }
       }
       if (valid) {
 #pragma unroll
         for (int k = 0; k < 9; ++k)
-          if (acc[k] != 0.f) atomicAdd(&s_g[k][e], acc[k]);
+          if (acc[k] != 0.f) atomicAdd(&s_g[k][e_idx], acc[k]);
       }
     }
     __syncthreads();
@@ -388,8 +414,10 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
         s_g[k][tid] = 0.f;
       }
       float4* dst = B.grad2d + 3 * item;
-      if (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f) atomic_add_f4(dst, make_float4(v[0], v[1], v[2], v[3]));
-      if (v[4] != 0.f || v[5] != 0.f || v[6] != 0.f || v[7] != 0.f) atomic_add_f4(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
+      if (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f)
+        atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
+      if (v[4] != 0.f || v[5] != 0.f || v[6] != 0.f || v[7] != 0.f)
+        atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
       if (v[8] != 0.f) atomicAdd(&dst[2].x, v[8]);
     }
     __syncthreads();
@@ -409,7 +437,7 @@ RenderParams make_params(const ViewDev* views, int n_views, int64_t n, const uin
   P.rgb = st.rgb;
   P.depth_frame = st.depth_frame;
   P.alpha_max = cfg.alpha_max;
-  P.alpha_min = cfg.alpha_min;
+  P.e_min = (float)log2((double)cfg.alpha_min);
   P.t_min = cfg.t_min;
   P.bg[0] = cfg.bg[0];
   P.bg[1] = cfg.bg[1];
@@ -425,7 +453,8 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
   FwdOut O{out.image, out.final_T, out.n_contrib, out.imax, out.wmax, out.depth, out.depth_blend,
            out.weight_sum, out.max_area};
-  if (total_tiles > 0) GS_TIMED("render_fwd", stream, (render_fwd_kernel<<<total_tiles, kRenderThreads, 0, stream>>>(P, O)));
+  if (total_tiles > 0)
+    GS_TIMED("render_fwd", stream, (render_fwd_kernel<<<total_tiles, kRenderThreads, 0, stream>>>(P, O)));
   return cudaGetLastError();
 }
 
@@ -435,7 +464,8 @@ cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int 
                               float4* grad2d, cudaStream_t stream) {
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
   BwdIn B{dL_dimage, image, n_contrib, grad2d};
-  if (total_tiles > 0) GS_TIMED("render_bwd", stream, (render_bwd_kernel<<<total_tiles, kRenderThreads, 0, stream>>>(P, B)));
+  if (total_tiles > 0)
+    GS_TIMED("render_bwd", stream, (render_bwd_kernel<<<total_tiles, kRenderThreads, 0, stream>>>(P, B)));
   return cudaGetLastError();
 }
 

@@ -52,25 +52,45 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// Counts the digits of every pass in one read of the keys.
+// Counts the digits of every pass in one read of the keys.  Each thread
+// takes 8 consecutive keys and adds runs of equal digits with one shared
+// atomic per run, which keeps nearly-sorted inputs (long runs of one high
+// digit) from serialising on a single counter.
+constexpr int kHistKeys = 8;
+
 __global__ void __launch_bounds__(256) radix_histogram_kernel(const uint32_t* __restrict__ keys, int64_t n,
                                                               int passes, uint32_t* __restrict__ hist) {
   __shared__ uint32_t sh[kMaxPasses * kRadix];
   for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) sh[i] = 0;
   __syncthreads();
-  const int lane = threadIdx.x & 31;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += (int64_t)gridDim.x * blockDim.x) {
-    int64_t i = base + threadIdx.x;
-    bool valid = i < n;
-    uint32_t k = valid ? keys[i] : 0u;
-    uint32_t vmask = __ballot_sync(0xffffffffu, valid);
-    if (valid) {
-      for (int p = 0; p < passes; ++p) {
-        uint32_t d = (k >> (p * kRadixBits)) & (kRadix - 1);
-        uint32_t peers = __match_any_sync(vmask, d);
-        int leader = __ffs(peers) - 1;
-        if (lane == leader) atomicAdd(&sh[p * kRadix + d], __popc(peers));
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x * kHistKeys;
+  for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kHistKeys; base < n; base += stride) {
+    uint32_t k[kHistKeys];
+    const int cnt = (int)((n - base < kHistKeys) ? (n - base) : (int64_t)kHistKeys);
+    if (cnt == kHistKeys && (base & 3) == 0) {
+      const uint4 a = *reinterpret_cast<const uint4*>(keys + base);
+      const uint4 b = *reinterpret_cast<const uint4*>(keys + base + 4);
+      k[0] = a.x; k[1] = a.y; k[2] = a.z; k[3] = a.w; k[4] = b.x; k[5] = b.y; k[6] = b.z; k[7] = b.w;
+    } else {
+#pragma unroll
+      for (int j = 0; j < kHistKeys; ++j) k[j] = j < cnt ? keys[base + j] : 0u;
+    }
+    for (int p = 0; p < passes; ++p) {
+      const int sh_p = p * kRadixBits;
+      uint32_t cur = (k[0] >> sh_p) & (kRadix - 1), run = 1;
+#pragma unroll
+      for (int j = 1; j < kHistKeys; ++j) {
+        if (j >= cnt) break;
+        const uint32_t d = (k[j] >> sh_p) & (kRadix - 1);
+        if (d == cur) {
+          ++run;
+        } else {
+          atomicAdd(&sh[p * kRadix + cur], run);
+          cur = d;
+          run = 1;
+        }
       }
+      atomicAdd(&sh[p * kRadix + cur], run);
     }
   }
   __syncthreads();
@@ -120,11 +140,18 @@ __global__ void __launch_bounds__(kSortThreads) radix_onesweep_kernel(
   uint32_t key[kSortItemsPerThread];
   uint32_t rank[kSortItemsPerThread];
   const uint32_t lt = lanemask_lt();
+  const int64_t warp_start = tile_start + warp * kWarpKeys;
+  // issue every load of this thread before ranking (the ranking steps below
+  // are ordered by __syncwarp, which would otherwise serialise the loads)
 #pragma unroll
   for (int k = 0; k < kSortItemsPerThread; ++k) {
-    int64_t i = tile_start + warp * kWarpKeys + k * 32 + lane;
+    const int64_t i = warp_start + k * 32 + lane;
+    key[k] = i < n ? keys_in[i] : 0u;
+  }
+#pragma unroll
+  for (int k = 0; k < kSortItemsPerThread; ++k) {
+    int64_t i = warp_start + k * 32 + lane;
     bool valid = i < n;
-    key[k] = valid ? keys_in[i] : 0u;
     uint32_t vmask = __ballot_sync(0xffffffffu, valid);
     rank[k] = 0;
     if (valid) {
@@ -333,7 +360,7 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
   const int64_t tiles = sort_tiles(n);
   cudaError_t e = cudaMemsetAsync(scratch, 0, radix_scratch_bytes(n, bits), stream);
   if (e != cudaSuccess) return e;
-  int hist_blocks = (int)std::min<int64_t>(4 * 152, (n + 255) / 256);
+  int hist_blocks = (int)std::min<int64_t>(4 * 152, (n + 256 * kHistKeys - 1) / (256 * kHistKeys));
   const bool depth = tag && tag[0] == 'd';
   GS_TIMED(depth ? "depth_sort_histogram" : "tile_sort_histogram", stream,
            (radix_histogram_kernel<<<hist_blocks, 256, 0, stream>>>(keys, n, passes, s.hist)));
