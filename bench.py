@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-serve", action="store_true")
+    ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--serve-requests", type=int, default=2200)
     return ap.parse_args()
 
 
@@ -268,6 +271,8 @@ def run_ours(args, rank, world):
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(st, args, world)
+    serving = None if args.no_serve else run_serving(st, args)
+    dense = None if args.no_dense else run_dense(args)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(st.scene, st.cams)
@@ -280,6 +285,7 @@ def run_ours(args, rank, world):
                        "l2": "inputs larger than L2 (236 MB scene, 1.5 GB workspace)",
                        "parallelism": f"replicas x{world}"},
             "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
+            "serving": serving, "dense_phase": dense,
             "clocks": ck, "kernels": kt}
     return line
 
@@ -321,6 +327,83 @@ def run_e2e(st: Step, args, world) -> dict:
     units, sec_max = aggregate(st.pixels * args.steps, sec, world)
     return {"value": units / sec_max / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": sec_max * 1e3 / args.steps}
+
+
+def run_serving(st: Step, args) -> dict:
+    """Serving loop on the resident 1M scene: Poisson arrivals at 200 req/s
+    (seed 3), poses on a sphere of radius U[3, 6], resolutions uniform over
+    640x480 / 1280x720 / 1920x1080 / 3840x2160, 24 GB admission budget; the
+    first 10 % of requests are warm-up.  Batched (3 stream slots, up to 16
+    views per batch) against the same trace served one request at a time."""
+    import torch
+    from paper_2411_12788_gb300 import serve
+    n = args.serve_requests
+    skip = n // 11
+    out = {"rate_per_s": 200.0, "requests_timed": n - skip, "warmup_requests": skip, "budget_gb": 24,
+           "scene_gaussians": st.g.n}
+    for name, streams, views in (("batched", 3, 16), ("one_at_a_time", 1, 1)):
+        trace = serve.poisson_trace(n, rate=200.0, seed=3)
+        srv = serve.RenderServer(st.g, budget_bytes=24 << 30, streams=streams, max_views=views)
+        srv.serve(trace)
+        stats = serve.latency_stats(trace, skip=skip)
+        stats.update({"streams": streams, "max_views": views, "batches": srv.batches_run,
+                      "mean_views_per_batch": srv.views_run / max(1, srv.batches_run),
+                      "peak_reserved_gb": srv.peak_reserved / 2**30})
+        out[name] = stats
+        torch.cuda.synchronize()
+    out["p99_speedup"] = out["one_at_a_time"]["p99_ms"] / out["batched"]["p99_ms"]
+    return out
+
+
+def run_dense(args, iters: int = 3) -> dict:
+    """Dense-phase step (MSv2-D): 3M Gaussians (256 clusters, SH 3), one
+    1920x1080 view: fwd+bwd with L1, keep the top 25 % by accumulated weight,
+    gather them and re-render the sparse set."""
+    import torch
+    from paper_2411_12788_gb300 import raster, scenes
+    sc = scenes.cluster_scene(3_000_000, 256, seed=0, sh_degree=3)
+    cam = scenes.ring_camera(0.3, 1920, 1080)
+    g = raster.GaussianTensors.from_scene(sc, "cuda")
+    target = torch.as_tensor(scenes.target_images([cam], seed=1)[0].reshape(-1)).cuda()
+    cfg = raster.make_config(flags=raster._lib.GS_FLAG_ZERO_ACCUM)
+    k = math.ceil(0.25 * sc.n)
+    loss = torch.zeros(1, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    times = {"fwd_bwd": 0.0, "prune_gather": 0.0, "rerender": 0.0}
+
+    def once(record):
+        s = torch.cuda.current_stream()
+        if record:
+            ev[0].record(s)
+        fr = raster.forward(g, [cam], cfg)
+        dL = torch.empty_like(fr.outs["image"])
+        raster.loss_l1(fr.outs["image"], target, loss, dL)
+        raster.backward(g, fr, dL)
+        if record:
+            ev[1].record(s)
+        keep = raster.prune_select(fr.outs["weight_sum"], k)
+        h = raster.gather_scene(g, keep)
+        if record:
+            ev[2].record(s)
+        fr2 = raster.forward(h, [cam], cfg)
+        if record:
+            ev[3].record(s)
+            torch.cuda.synchronize()
+            times["fwd_bwd"] += ev[0].elapsed_time(ev[1])
+            times["prune_gather"] += ev[1].elapsed_time(ev[2])
+            times["rerender"] += ev[2].elapsed_time(ev[3])
+        return fr, fr2
+    once(False)
+    torch.cuda.synchronize()
+    for _ in range(iters):
+        fr, fr2 = once(True)
+    ms = {k2: v / iters for k2, v in times.items()}
+    total = sum(ms.values())
+    pix = cam.width * cam.height
+    return {"workload": "3M Gaussians SH3 (256 clusters), 1920x1080: fwd+bwd, top-25% prune, re-render",
+            "ms": ms, "ms_total": total, "kept": k, "entries": int(fr.plan.n_entries),
+            "entries_after_prune": int(fr2.plan.n_entries), "mpix_per_s": 2 * pix / total / 1e3,
+            "note": "each phase allocates its workspaces from the torch caching allocator"}
 
 
 # ---------------------------------------------------------------- oracle arm

@@ -226,6 +226,38 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
 gs_status gs_bin_sort_noalloc(const gs_plan* plan, void* pre_ws, uint32_t* tile_ids,
                               uint32_t* items, uint32_t* ranges, void* stream);
 
+/* ---- importance pruning (MSv2-D) -------------------------------------- */
+
+/* Writable Gaussian attributes, device, same layout as gs_scene. */
+typedef struct gs_scene_buf {
+  float* means;
+  float* scales;
+  float* rotations;
+  float* opacities;
+  float* sh;
+  int64_t n;                /* rows available */
+  int32_t sh_degree;
+  int32_t sh_coeffs;
+} gs_scene_buf;
+
+/* Bytes of the workspace gs_prune_select needs for n importances. */
+size_t gs_prune_workspace_size(int64_t n);
+
+/* Importance-based pruning of MSv2-D (Sec. 6.1): the importance of Gaussian
+ * i is its accumulated blending weight I_i (Sec. 3.2; e.g. the weight_sum of
+ * gs_render_fwd summed over views).  Writes to keep_idx (device [k]) the
+ * indices of the k largest importances, ties broken towards the lower index,
+ * in ascending order.  importance: device [n], non-negative floats (their bit
+ * patterns are compared).  0 <= k <= n < 2^32; workspace from
+ * gs_prune_workspace_size, 256-byte aligned.  Asynchronous. */
+gs_status gs_prune_select(const float* importance, int64_t n, int64_t k, uint32_t* keep_idx,
+                          void* ws, size_t ws_bytes, void* stream);
+
+/* dst rows r = 0..k-1 <- src rows idx[r] of every attribute array (the
+ * compaction before the re-render).  dst->n >= k, equal sh_coeffs. */
+gs_status gs_gather_scene(const gs_scene* src, const uint32_t* idx, int64_t k,
+                          const gs_scene_buf* dst, void* stream);
+
 /* ---- training-step helpers ------------------------------------------- */
 
 /* Mean absolute error over `count` elements and its gradient (the L1 term

@@ -13,9 +13,14 @@ import math
 import numpy as np
 
 
-def keep_top(weight_sum, frac: float) -> np.ndarray:
+def keep_top_k(weight_sum, k: int) -> np.ndarray:
+    """The k largest weights, ties towards the lower index, ascending indices."""
     w = np.asarray(weight_sum, np.float64)
     n = len(w)
-    k = min(n, math.ceil(frac * n))
     order = np.lexsort((np.arange(n), -w))      # descending weight, then index
-    return np.sort(order[:k])
+    return np.sort(order[:min(k, n)])
+
+
+def keep_top(weight_sum, frac: float) -> np.ndarray:
+    n = len(weight_sum)
+    return keep_top_k(weight_sum, min(n, math.ceil(frac * n)))

@@ -141,7 +141,10 @@ def render_view(proj: dict, cam, cfg: OracleConfig | None = None, pix=None,
     return out
 
 
-DEFAULT_FLAG_EPS = dict(alpha=1e-4, t=1e-4, w=1e-5, z=1e-6, clamp=1e-5)
+# z: the CUDA path's FP32 z (three rounded operations) and float32 of the
+# float64 z differ by at most ~2 ulp (2^-23 relative each), so only depths
+# within 3e-7 relative can swap order.
+DEFAULT_FLAG_EPS = dict(alpha=1e-4, t=1e-4, w=1e-5, z=3e-7, clamp=1e-5)
 
 
 def _flags(alpha_raw, w, blended, zs, cfg, eps=None):

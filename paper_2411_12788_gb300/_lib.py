@@ -51,6 +51,12 @@ class Plan(C.Structure):
                 ("pixel_base", C.c_int64 * (GS_MAX_VIEWS + 1))]
 
 
+class SceneBuf(C.Structure):
+    _fields_ = [("means", C.c_void_p), ("scales", C.c_void_p), ("rotations", C.c_void_p),
+                ("opacities", C.c_void_p), ("sh", C.c_void_p), ("n", C.c_int64),
+                ("sh_degree", C.c_int32), ("sh_coeffs", C.c_int32)]
+
+
 class FwdOutputs(C.Structure):
     _fields_ = [("image", C.c_void_p), ("final_T", C.c_void_p), ("n_contrib", C.c_void_p),
                 ("imax", C.c_void_p), ("wmax", C.c_void_p), ("depth", C.c_void_p),
@@ -92,6 +98,10 @@ SIGNATURES = {
                                 C.c_void_p]),
     "gs_bin_sort_noalloc": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                       C.c_void_p]),
+    "gs_prune_workspace_size": (C.c_size_t, [C.c_int64]),
+    "gs_prune_select": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t,
+                                  C.c_void_p]),
+    "gs_gather_scene": (C.c_int, [C.POINTER(Scene), C.c_void_p, C.c_int64, C.POINTER(SceneBuf), C.c_void_p]),
     "gs_loss_l1": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_device_status": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.c_void_p]),
     "gs_inspect_preprocess": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.POINTER(PreprocessView)]),

@@ -83,7 +83,8 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 size_t scan_block_bytes(int64_t n);
-// out[k] = sum_{j<k} counts[idx[k]]; *total = sum of all (device, 64-bit).
+// out[k] = sum_{j<k} counts[idx[j]] (idx == nullptr: counts[j]); *total = sum of
+// all (device, 64-bit).
 cudaError_t gather_exclusive_scan(const uint32_t* counts, const uint32_t* idx, uint32_t* out,
                                   int64_t n, uint64_t* block_scratch, unsigned long long* total,
                                   cudaStream_t stream);

@@ -286,7 +286,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_block_sums_kernel(const uin
   uint32_t acc = 0;
   for (int k = 0; k < kScanItems; ++k) {
     int64_t i = base + k * kScanThreads + threadIdx.x;
-    if (i < n) acc += counts[idx[i]];
+    if (i < n) acc += counts[idx ? idx[i] : i];
   }
   uint32_t tot;
   block_exclusive_scan(acc, s_warp, &tot);
@@ -330,7 +330,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const uint32_t
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     int64_t i = base + k;
-    c[k] = i < n ? counts[idx[i]] : 0u;
+    c[k] = i < n ? counts[idx ? idx[i] : i] : 0u;
     acc += c[k];
   }
   uint32_t tot;

@@ -140,6 +140,31 @@ def loss_l1(image, target, loss, dL_dimage, stream=None) -> None:
                                          _ptr(dL_dimage), _stream(stream)))
 
 
+def prune_select(importance: torch.Tensor, k: int, stream=None) -> torch.Tensor:
+    """Indices (ascending, int32 storage of uint32) of the k largest
+    importances, ties to the lower index (gs_prune_select)."""
+    n = importance.numel()
+    ws = torch.empty(max(int(lib().gs_prune_workspace_size(n)), 1), dtype=torch.uint8, device=importance.device)
+    keep = torch.empty(max(k, 1), dtype=torch.int32, device=importance.device)
+    check("gs_prune_select", lib().gs_prune_select(_ptr(importance), n, int(k), _ptr(keep), _ptr(ws),
+                                                   ws.numel(), _stream(stream)))
+    return keep[:k]
+
+
+def gather_scene(g: "GaussianTensors", idx: torch.Tensor, stream=None) -> "GaussianTensors":
+    """A compact copy of the rows idx of every attribute (gs_gather_scene)."""
+    k = int(idx.numel())
+    out = GaussianTensors(torch.empty((k, 3), device=g.means.device), torch.empty((k, 3), device=g.means.device),
+                          torch.empty((k, 4), device=g.means.device), torch.empty((k,), device=g.means.device),
+                          torch.empty((k,) + tuple(g.sh.shape[1:]), device=g.means.device), g.sh_degree)
+    if k == 0:
+        return out
+    d = _lib.SceneBuf(out.means.data_ptr(), out.scales.data_ptr(), out.rotations.data_ptr(),
+                      out.opacities.data_ptr(), out.sh.data_ptr(), k, g.sh_degree, int(g.sh.shape[1]))
+    check("gs_gather_scene", lib().gs_gather_scene(C.byref(g.struct()), _ptr(idx), k, C.byref(d), _stream(stream)))
+    return out
+
+
 def device_status(plan, pre_ws, stream=None) -> int:
     return int(lib().gs_device_status(C.byref(plan), _ptr(pre_ws), _stream(stream)))
 

@@ -1,0 +1,184 @@
+"""Continuous-batching render server over a resident Gaussian scene.
+
+Requests (a camera each, any resolution) arrive over time.  Whenever one of
+`streams` slots is free, the server takes the requests that have arrived, in
+arrival order, as long as they fit the memory budget for sort and tile
+buffers and the batch has at most `max_views` views, and renders them as one
+batch on that slot's CUDA stream: one gs_preprocess over all the batch's
+views, one shared gs_bin_sort (the view is part of the global tile id) and
+one gs_render_fwd launch over every tile of every view.  Batches on
+different slots overlap on the device.  Completion is stamped with a CUDA
+event on the batch's stream, so latencies are device-accurate:
+latency = completion - arrival, queueing included.
+
+With streams=1 and max_views=1 the same loop serves one request at a time
+in arrival order (the baseline).
+
+Admission is two-phase because a batch's sort memory is only known after
+preprocessing: a request is admitted on an estimate (its tiles times a
+running entries-per-tile estimate), and the reservation is corrected to the
+exact workspace sizes once the batch's entry count is known.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+from . import raster
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float              # seconds after the trace start
+    cam: object
+    done: float | None = None   # seconds after the trace start (device time)
+    batch: int = -1
+    image: torch.Tensor | None = None
+
+    @property
+    def pixels(self) -> int:
+        return int(self.cam.width) * int(self.cam.height)
+
+
+@dataclass
+class _Batch:
+    bid: int
+    reqs: list
+    stream: torch.cuda.Stream
+    reserved: int
+    event: torch.cuda.Event
+    keep: list = field(default_factory=list)    # tensors alive until completion
+
+
+class RenderServer:
+    def __init__(self, g: raster.GaussianTensors, budget_bytes: int = 24 << 30, streams: int = 3,
+                 max_views: int = 16, keep_images: bool = False, cfg=None, entries_per_tile: float = 3000.0):
+        self.g = g
+        self.budget = int(budget_bytes)
+        self.n_slots = int(streams)
+        self.max_views = int(max_views)
+        self.keep_images = keep_images
+        self.cfg = cfg or raster.make_config()
+        self.ept = float(entries_per_tile)          # running estimate of entries per tile
+        self.streams = [torch.cuda.Stream() for _ in range(self.n_slots)]
+        self.reserved = 0
+        self.peak_reserved = 0
+        self.batches_run = 0
+        self.views_run = 0
+
+    # -------------------------------------------------------------- memory
+    @staticmethod
+    def _tiles(cam) -> int:
+        return math.ceil(cam.width / 16) * math.ceil(cam.height / 16)
+
+    def _estimate(self, cam) -> int:
+        """Bytes a request is admitted on: its share of the preprocess
+        workspace, its estimated sort workspace and its outputs."""
+        pre = self.g.n * 176
+        sort = int(self._tiles(cam) * self.ept * 16 * 1.25) + (2 << 20)
+        out = cam.width * cam.height * 24
+        return pre + sort + out
+
+    # -------------------------------------------------------------- one batch
+    def _launch(self, reqs: list, slot: int, bid: int) -> _Batch:
+        s = self.streams[slot]
+        est = sum(self._estimate(r.cam) for r in reqs)
+        with torch.cuda.stream(s):
+            cams = [r.cam for r in reqs]
+            plan = raster.make_plan(self.g.n, cams)
+            pre_ws = torch.empty(raster.preprocess_workspace_size(plan), dtype=torch.uint8, device="cuda")
+            raster.preprocess(plan, self.g.struct(), self.cfg, pre_ws, stream=s)
+            sort_ws = torch.empty(max(raster.bin_sort_workspace_size(plan), 1), dtype=torch.uint8, device="cuda")
+            raster.bin_sort(plan, pre_ws, sort_ws, stream=s)
+            outs = raster.alloc_outputs(plan, "cuda", want=("image", "final_T", "n_contrib", "depth", "imax"))
+            raster.render_fwd(plan, self.cfg, pre_ws, sort_ws, outs, stream=s)
+            ev = torch.cuda.Event(enable_timing=True)
+            ev.record(s)
+        actual = pre_ws.numel() + sort_ws.numel() + sum(t.numel() * t.element_size() for t in outs.values())
+        tiles = sum(self._tiles(c) for c in cams)
+        if tiles:
+            self.ept = 0.8 * self.ept + 0.2 * (plan.n_entries / tiles)
+        self.reserved += actual - est               # correct the admission estimate
+        self.peak_reserved = max(self.peak_reserved, self.reserved)
+        b = _Batch(bid, reqs, s, actual, ev, [pre_ws, sort_ws, outs])
+        if self.keep_images:
+            for v, r in enumerate(reqs):
+                r.image = raster.view_image(outs["image"], plan, v)
+        return b
+
+    # -------------------------------------------------------------- the loop
+    def serve(self, trace: list) -> list:
+        """Serves `trace` (Requests sorted by arrival) in real time; returns it
+        with `done` filled in."""
+        pending = list(trace)
+        queue: list = []
+        inflight: dict = {}
+        free_slots = list(range(self.n_slots))
+        torch.cuda.synchronize()
+        t0_ev = torch.cuda.Event(enable_timing=True)
+        t0_ev.record(torch.cuda.current_stream())
+        t0 = time.perf_counter()
+        bid = 0
+        while pending or queue or inflight:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                queue.append(pending.pop(0))
+            # retire finished batches
+            for slot, b in list(inflight.items()):
+                if b.event.query():
+                    done = t0_ev.elapsed_time(b.event) / 1e3
+                    for r in b.reqs:
+                        r.done = done
+                        r.batch = b.bid
+                    self.reserved -= b.reserved
+                    del inflight[slot]
+                    free_slots.append(slot)
+            # admit and launch while a slot is free
+            while queue and free_slots:
+                take, need = [], 0
+                while queue and len(take) < self.max_views:
+                    est = self._estimate(queue[0].cam)
+                    if take and self.reserved + need + est > self.budget:
+                        break
+                    if not take and self.reserved + est > self.budget and inflight:
+                        break
+                    take.append(queue.pop(0))
+                    need += est
+                if not take:
+                    break
+                slot = free_slots.pop(0)
+                self.reserved += need
+                inflight[slot] = self._launch(take, slot, bid)
+                bid += 1
+                self.batches_run += 1
+                self.views_run += len(take)
+            if not queue and not inflight and pending:
+                wait = pending[0].arrival - (time.perf_counter() - t0)
+                if wait > 2e-4:
+                    time.sleep(wait - 1e-4)
+        torch.cuda.synchronize()
+        return trace
+
+
+def poisson_trace(n: int, rate: float, seed: int = 3, sizes=None) -> list:
+    """n requests with exponential inter-arrival times (mean 1/rate), poses on
+    a sphere of radius U[3, 6] looking at the origin and resolutions drawn
+    uniformly from `sizes` (fovx 60 degrees)."""
+    from . import scenes
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    return [Request(i, float(t[i]), scenes.sphere_camera(rng, sizes)) for i in range(n)]
+
+
+def latency_stats(reqs: list, skip: int = 0) -> dict:
+    lat = np.array([r.done - r.arrival for r in reqs[skip:]]) * 1e3
+    span = max(r.done for r in reqs[skip:]) - min(r.arrival for r in reqs[skip:])
+    pix = sum(r.pixels for r in reqs[skip:])
+    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "requests": len(lat),
+            "mpix_per_s": pix / span / 1e6}

@@ -1,0 +1,25 @@
+"""Host-side pieces of the server that need no GPU: the Poisson trace and
+the latency statistics."""
+import numpy as np
+
+from paper_2411_12788_gb300 import serve
+
+
+def test_poisson_trace_rate_and_sizes():
+    tr = serve.poisson_trace(4000, rate=200.0, seed=3)
+    t = np.array([r.arrival for r in tr])
+    assert np.all(np.diff(t) > 0)
+    assert abs(len(t) / t[-1] - 200.0) < 12.0
+    sizes = {(r.cam.width, r.cam.height) for r in tr}
+    assert sizes == {(640, 480), (1280, 720), (1920, 1080), (3840, 2160)}
+    radii = np.array([np.linalg.norm(-r.cam.R.T @ r.cam.t) for r in tr])
+    assert radii.min() >= 3.0 and radii.max() <= 6.0
+
+
+def test_latency_stats():
+    tr = serve.poisson_trace(200, rate=100.0, seed=1)
+    for k, r in enumerate(tr):
+        r.done = r.arrival + (0.001 if k % 100 else 0.050)
+    st = serve.latency_stats(tr, skip=0)
+    assert abs(st["p50_ms"] - 1.0) < 1e-6
+    assert st["max_ms"] > 49.9 and st["requests"] == 200
