@@ -28,6 +28,7 @@ PreLayout pre_layout(const gs_plan& p) {
   L.rgb = take(16 * m);
   L.depth_frame = take(48 * m);
   L.rect = take(8 * m);
+  L.bin = take(32 * m);
   L.tiles = take(4 * m);
   L.depth_key = take(4 * m);
   L.sort_keys_alt = take(4 * m);
@@ -77,6 +78,7 @@ ItemState item_state(void* ws, const PreLayout& L) {
   s.rgb = at<float4>(ws, L.rgb);
   s.depth_frame = at<float4>(ws, L.depth_frame);
   s.rect = at<uint2>(ws, L.rect);
+  s.bin = at<float4>(ws, L.bin);
   s.tiles = at<uint32_t>(ws, L.tiles);
   s.depth_key = at<uint32_t>(ws, L.depth_key);
   return s;

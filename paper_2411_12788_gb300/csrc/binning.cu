@@ -2,13 +2,10 @@
 // the depth order of the items (Sec. 3.1), then tile ranges of the list
 // sorted by tile id.  Also the L1 photometric loss of the training step.
 //
-// Duplication is warp-cooperative: a warp takes 32 consecutive items of the
-// depth order, flattens their candidate rectangles into one index space and
-// walks it 32 candidates at a time, so a Gaussian covering hundreds of tiles
-// does not serialise its warp.  Each candidate is tested with the same exact
-// tile predicate as the counting pass in preprocess (identical arithmetic),
-// and its output slot is the item's scanned offset plus the number of hits
-// of the same item before it (ballot + popc).
+// Duplication: one thread per item of the depth order walks the item's tile
+// rows with the same interval form of the support as the counting pass in
+// preprocess (identical arithmetic on the same stored parameters) and writes
+// its entries at its scanned offset, row-major.
 #include "project.cuh"
 
 namespace gs {
@@ -17,12 +14,6 @@ namespace {
 
 constexpr int kDupThreads = 256;
 
-__device__ __forceinline__ uint32_t lanemask_lt_() {
-  uint32_t m;
-  asm volatile("mov.u32 %0, %%lanemask_lt;" : "=r"(m));
-  return m;
-}
-
 __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* __restrict__ views, int64_t n_items,
                                                                 int64_t n, const uint32_t* __restrict__ sorted_items,
                                                                 const uint32_t* __restrict__ offsets, ItemState st,
@@ -30,77 +21,41 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* _
                                                                 uint32_t* __restrict__ vals,
                                                                 uint32_t* __restrict__ status) {
   const int64_t k = (int64_t)blockIdx.x * kDupThreads + threadIdx.x;
-  const int lane = threadIdx.x & 31;
-  uint32_t item = 0, cnt = 0, off = 0;
-  if (k < n_items) {
-    item = sorted_items[k];
-    cnt = st.tiles[item];
-  }
-  float mx = 0.f, my = 0.f, tau = 0.f, A = 0.f, B = 0.f, C = 0.f;
-  uint2 rect = make_uint2(0u, 0u);
-  int area = 0, tbase = 0, tiles_x = 1;
-  if (cnt > 0) {
-    off = offsets[k];
-    rect = st.rect[item];
-    area = rect_area(rect);
-    const float4 a = st.xy_tau_z[item];
-    const float4 c = st.conic_o[item];
-    mx = a.x;
-    my = a.y;
-    tau = a.z;
-    A = c.x;
-    B = c.y;
-    C = c.z;
-    const ViewDev& V = views[item / n];
-    tbase = V.tile_base;
-    tiles_x = V.tiles_x;
-  }
-  uint32_t total;
-  const uint32_t excl = warp_exclusive_sum((uint32_t)area, &total);
+  if (k >= n_items) return;
+  const uint32_t item = sorted_items[k];
+  const uint32_t cnt = st.tiles[item];
+  if (cnt == 0) return;
+  const uint32_t off = offsets[k];
+  const float4 a = st.xy_tau_z[item];
+  const float4 b0 = st.bin[2 * item], b1 = st.bin[2 * item + 1];
+  BinParams b;
+  b.mx = a.x;
+  b.my = a.y;
+  b.tau = a.z;
+  b.k = b0.x;
+  b.sc = b0.y;
+  b.isyy = b0.z;
+  b.h = b0.w;
+  b.rx = b1.x;
+  b.ys = b1.y;
+  const ViewDev& V = views[item / n];
   uint32_t written = 0;
-  const uint32_t lt = lanemask_lt_();
-  for (uint32_t base = 0; base < total; base += 32) {
-    const uint32_t c = base + lane;
-    const int own = warp_owner(excl, min(c, total - 1));
-    const float omx = __shfl_sync(0xffffffffu, mx, own), omy = __shfl_sync(0xffffffffu, my, own);
-    const float oA = __shfl_sync(0xffffffffu, A, own), oB = __shfl_sync(0xffffffffu, B, own);
-    const float oC = __shfl_sync(0xffffffffu, C, own), otau = __shfl_sync(0xffffffffu, tau, own);
-    const uint32_t orx = __shfl_sync(0xffffffffu, rect.x, own), ory = __shfl_sync(0xffffffffu, rect.y, own);
-    const uint32_t oex = __shfl_sync(0xffffffffu, excl, own);
-    const uint32_t ooff = __shfl_sync(0xffffffffu, off, own);
-    const uint32_t owr = __shfl_sync(0xffffffffu, written, own);
-    const uint32_t ocnt = __shfl_sync(0xffffffffu, cnt, own);
-    const uint32_t oitem = __shfl_sync(0xffffffffu, item, own);
-    const int otb = __shfl_sync(0xffffffffu, tbase, own), otx = __shfl_sync(0xffffffffu, tiles_x, own);
-    bool hit = false;
-    int tx = 0, ty = 0;
-    if (c < total) {
-      const int tx0 = orx & 0xffff, ty0 = orx >> 16, nx = (int)(ory & 0xffff) - tx0 + 1;
-      const int kk = (int)(c - oex);
-      tx = tx0 + kk % nx;
-      ty = ty0 + kk / nx;
-      hit = tile_touched(omx, omy, oA, oB, oC, otau, tx, ty);
-    }
-    const uint32_t hits = __ballot_sync(0xffffffffu, hit);
-    if (hit) {
-      const int lo_own = (int)(oex > base ? oex - base : 0u);   // <= lane here
-      const uint32_t below = hits & lt & ~((1u << lo_own) - 1u);
-      const uint32_t r = owr + __popc(below);
-      if (r < ocnt) {
-        keys[ooff + r] = (uint32_t)(otb + ty * otx + tx);
-        vals[ooff + r] = oitem;
-      } else {
-        atomicOr(status, kStatusEntryMismatch);
+  int ty0, ty1;
+  if (tile_rows(b, V.tiles_y, &ty0, &ty1)) {
+    for (int ty = ty0; ty <= ty1; ++ty) {
+      int tx_a, tx_b;
+      if (!row_tiles(b, ty, V.tiles_x, &tx_a, &tx_b)) continue;
+      const uint32_t base = (uint32_t)(V.tile_base + ty * V.tiles_x);
+      for (int tx = tx_a; tx <= tx_b; ++tx) {
+        if (written < cnt) {
+          keys[off + written] = base + (uint32_t)tx;
+          vals[off + written] = item;
+        }
+        ++written;
       }
     }
-    const int lo = (int)min(max((int64_t)excl - (int64_t)base, (int64_t)0), (int64_t)32);
-    const int hi = (int)min(max((int64_t)excl + area - (int64_t)base, (int64_t)0), (int64_t)32);
-    if (hi > lo) {
-      const uint32_t bits = (hi - lo == 32) ? 0xffffffffu : (((1u << (hi - lo)) - 1u) << lo);
-      written += __popc(hits & bits);
-    }
   }
-  if (cnt > 0 && written != cnt) atomicOr(status, kStatusEntryMismatch);
+  if (written != cnt) atomicOr(status, kStatusEntryMismatch);
 }
 
 // [start, end) of every tile in the sorted key list by binary search: thread

@@ -38,7 +38,8 @@ struct ItemState {
   float4* conic_o;           // (A, B, C, opacity); q = A dx^2 + 2B dx dy + C dy^2
   float4* rgb;               // (r, g, b, 0)
   float4* depth_frame;       // 3 x float4 per item: rows of W = diag(1/s) (R Rq)^T, then e = W p_c
-  uint2* rect;               // (tx0 | ty0 << 16, tx1 | ty1 << 16), inclusive
+  uint2* rect;               // (tx0 | ty0 << 16, tx1 | ty1 << 16), inclusive bounding box
+  float4* bin;               // 2 x float4 per item: (k, sc, 1/Syy, h), (rx, ys, 0, 0); see BinParams
   uint32_t* tiles;           // exact touched-tile count (0 = culled)
   uint32_t* depth_key;       // float bits of z, kCulledKey if culled
 };
@@ -46,7 +47,7 @@ struct ItemState {
 // Offsets of the preprocess workspace regions (bytes), host-computed.
 struct PreLayout {
   size_t views, status, n_entries;
-  size_t xy_tau_z, conic_o, rgb, depth_frame, rect, tiles, depth_key;
+  size_t xy_tau_z, conic_o, rgb, depth_frame, rect, bin, tiles, depth_key;
   size_t sort_keys_alt, sort_vals, sort_vals_alt;   // depth sort buffers
   size_t sorted_items, offsets;                      // after the depth sort
   size_t scan_blocks;

@@ -1,14 +1,16 @@
 // Per-(view, Gaussian) projection (Sec. 3.1) and its backward pass.
 //
 // Forward, one thread per Gaussian, looping over the views so that the
-// Gaussian's attributes (236 B at SH degree 3) are read from HBM once:
-//   covariance Sigma = R(q) diag(s^2) R(q)^T, EWA projection
-//   cov2d = J W Sigma W^T J^T + lowpass I, conic = cov2d^{-1}, centre, SH
-//   colour in the viewing direction, the frame for the midpoint depth
-//   (Sec. 4.1), the candidate tile rectangle and, warp-cooperatively, the
-//   exact number of tiles whose pixel-centre rectangle meets the support
-//   q <= 2 ln(o / alpha_min).
-// SH rows are staged through shared memory with coalesced loads.
+// Gaussian's attributes (236 B at SH degree 3) are read from HBM once per
+// batch: covariance Sigma = M M^T with M = R(q) diag(s), EWA projection
+// cov2d = F F^T + lowpass I with F = J W M (2x3), conic = cov2d^{-1}, centre,
+// SH colour in the viewing direction, the frame for the midpoint depth
+// (Sec. 4.1) and the exact number of touched tiles, counted row by row with
+// the interval form of the support (project.cuh, row_tiles).  det(cov2d) is
+// taken from the Lagrange identity |F0|^2 |F1|^2 - (F0.F1)^2 = sum of the
+// squared 2x2 minors of F, which does not cancel for thin Gaussians.
+// SH rows are staged through shared memory with coalesced loads.  Both
+// kernels are instantiated per SH degree so the coefficient loops unroll.
 #include "project.cuh"
 
 namespace gs {
@@ -26,7 +28,7 @@ struct PreParams {
   const float* opac;
   const float* sh;
   int64_t n;
-  int sh_degree, sh_coeffs;
+  int sh_coeffs;
   const ViewDev* views;
   int n_views;
   const uint8_t* mask;
@@ -34,151 +36,127 @@ struct PreParams {
   ItemState st;
 };
 
+// Stage the first K coefficients (3 floats each) of this block's SH rows into
+// shared memory with row stride 3K+1 (odd: conflict-free per-thread reads).
+template <int K>
+__device__ __forceinline__ void stage_sh(const float* __restrict__ sh, int sh_coeffs, int64_t i0, int64_t n,
+                                         float* s_sh) {
+  constexpr int per = 3 * K, row = 3 * K + 1;
+  const int64_t rows = (n - i0 < kPreThreads) ? (n - i0) : (int64_t)kPreThreads;
+  for (int f = threadIdx.x; f < rows * per; f += kPreThreads) {
+    const int g = f / per, c = f - g * per;
+    s_sh[g * row + c] = sh[(i0 + g) * (int64_t)sh_coeffs * 3 + c];
+  }
+}
+
+__device__ __forceinline__ void cull(const ItemState& st, int64_t item) {
+  st.tiles[item] = 0u;
+  st.depth_key[item] = kCulledKey;
+}
+
+template <int DEG>
 __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
-  extern __shared__ float s_sh[];                 // [kPreThreads][used*3 + 1]
-  const int used = (P.sh_degree + 1) * (P.sh_degree + 1);
-  const int row = used * 3 + 1;                   // odd stride: no bank conflicts
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int row = 3 * K + 1;
+  __shared__ float s_sh[kPreThreads * row];
   const int64_t i0 = (int64_t)blockIdx.x * kPreThreads;
   const int64_t i = i0 + threadIdx.x;
-  const bool live = i < P.n;
-  const int lane = threadIdx.x & 31;
-
-  // stage this block's SH rows (first `used` coefficients of each)
-  {
-    const int per = used * 3;
-    const int64_t rows = (P.n - i0 < kPreThreads) ? (P.n - i0) : (int64_t)kPreThreads;
-    for (int f = threadIdx.x; f < rows * per; f += kPreThreads) {
-      int g = f / per, c = f - g * per;
-      s_sh[g * row + c] = P.sh[(i0 + g) * (int64_t)P.sh_coeffs * 3 + c];
-    }
-  }
+  stage_sh<K>(P.sh, P.sh_coeffs, i0, P.n, s_sh);
   __syncthreads();
+  if (i >= P.n) return;
 
-  float3 p = make_float3(0.f, 0.f, 0.f);
-  float sig[6] = {0, 0, 0, 0, 0, 0};                // Sigma_00,01,02,11,12,22
-  float RRq[9];
-  float s0 = 1.f, s1 = 1.f, s2 = 1.f, o = 0.f;
+  const float3 p = make_float3(P.means[3 * i], P.means[3 * i + 1], P.means[3 * i + 2]);
+  const float s0 = P.scales[3 * i], s1 = P.scales[3 * i + 1], s2 = P.scales[3 * i + 2];
+  const float4 q = reinterpret_cast<const float4*>(P.rots)[i];
+  const float qi = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
   float Rq[9];
-  if (live) {
-    p = make_float3(P.means[3 * i], P.means[3 * i + 1], P.means[3 * i + 2]);
-    s0 = P.scales[3 * i];
-    s1 = P.scales[3 * i + 1];
-    s2 = P.scales[3 * i + 2];
-    float4 q = reinterpret_cast<const float4*>(P.rots)[i];
-    float inv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
-    quat_to_rot(q.x * inv, q.y * inv, q.z * inv, q.w * inv, Rq);
-    o = P.opac[i];
-    float M[9] = {Rq[0] * s0, Rq[1] * s1, Rq[2] * s2, Rq[3] * s0, Rq[4] * s1, Rq[5] * s2,
-                  Rq[6] * s0, Rq[7] * s1, Rq[8] * s2};
-    sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
-    sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
-    sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
-    sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
-    sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
-    sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
-  }
+  quat_to_rot(q.x * qi, q.y * qi, q.z * qi, q.w * qi, Rq);
+  const float o = P.opac[i];
+  const float M[9] = {Rq[0] * s0, Rq[1] * s1, Rq[2] * s2, Rq[3] * s0, Rq[4] * s1, Rq[5] * s2,
+                      Rq[6] * s0, Rq[7] * s1, Rq[8] * s2};
   const float tau = 2.f * logf(o / P.alpha_min);
-  const float* my_sh = s_sh + threadIdx.x * row;
+  float shc[K][3];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    shc[k][0] = s_sh[threadIdx.x * row + 3 * k];
+    shc[k][1] = s_sh[threadIdx.x * row + 3 * k + 1];
+    shc[k][2] = s_sh[threadIdx.x * row + 3 * k + 2];
+  }
+  const float lp = P.lowpass;
 
   for (int v = 0; v < P.n_views; ++v) {
     const ViewDev& V = P.views[v];
     const int64_t item = (int64_t)v * P.n + i;
-    bool vis = live && tau > 0.f;
+    bool vis = tau > 0.f;
     if (vis && P.mask) vis = P.mask[item] != 0;
-    float3 pc = make_float3(0.f, 0.f, 1.f);
-    if (vis) {
-      pc.x = V.R[0] * p.x + V.R[1] * p.y + V.R[2] * p.z + V.t[0];
-      pc.y = V.R[3] * p.x + V.R[4] * p.y + V.R[5] * p.z + V.t[1];
-      pc.z = V.R[6] * p.x + V.R[7] * p.y + V.R[8] * p.z + V.t[2];
-      vis = pc.z > P.znear;
+    if (!vis) {
+      cull(P.st, item);
+      continue;
     }
-    float mx = 0.f, my = 0.f, A = 0.f, B = 0.f, C = 0.f, cxx = 0.f, cyy = 0.f;
-    if (vis) {
-      const float iz = 1.f / pc.z;
-      const float txr = fminf(fmaxf(pc.x * iz, -V.limx), V.limx);
-      const float tyr = fminf(fmaxf(pc.y * iz, -V.limy), V.limy);
-      const float J00 = V.fx * iz, J02 = -V.fx * txr * iz;
-      const float J11 = V.fy * iz, J12 = -V.fy * tyr * iz;
-      float T0[3], T1[3];
+    const float3 pc = make_float3(V.R[0] * p.x + V.R[1] * p.y + V.R[2] * p.z + V.t[0],
+                                  V.R[3] * p.x + V.R[4] * p.y + V.R[5] * p.z + V.t[1],
+                                  V.R[6] * p.x + V.R[7] * p.y + V.R[8] * p.z + V.t[2]);
+    if (!(pc.z > P.znear)) {
+      cull(P.st, item);
+      continue;
+    }
+    const float iz = 1.f / pc.z;
+    const float txr = fminf(fmaxf(pc.x * iz, -V.limx), V.limx);
+    const float tyr = fminf(fmaxf(pc.y * iz, -V.limy), V.limy);
+    const float J00 = V.fx * iz, J02 = -V.fx * txr * iz;
+    const float J11 = V.fy * iz, J12 = -V.fy * tyr * iz;
+    float T0[3], T1[3], F0[3], F1[3];
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        T0[k] = J00 * V.R[k] + J02 * V.R[6 + k];
-        T1[k] = J11 * V.R[3 + k] + J12 * V.R[6 + k];
-      }
-      // S T0, S T1 with S = Sigma
-      float ST0[3] = {sig[0] * T0[0] + sig[1] * T0[1] + sig[2] * T0[2],
-                      sig[1] * T0[0] + sig[3] * T0[1] + sig[4] * T0[2],
-                      sig[2] * T0[0] + sig[4] * T0[1] + sig[5] * T0[2]};
-      float ST1[3] = {sig[0] * T1[0] + sig[1] * T1[1] + sig[2] * T1[2],
-                      sig[1] * T1[0] + sig[3] * T1[1] + sig[4] * T1[2],
-                      sig[2] * T1[0] + sig[4] * T1[1] + sig[5] * T1[2]};
-      cxx = T0[0] * ST0[0] + T0[1] * ST0[1] + T0[2] * ST0[2] + P.lowpass;
-      const float cxy = T0[0] * ST1[0] + T0[1] * ST1[1] + T0[2] * ST1[2];
-      cyy = T1[0] * ST1[0] + T1[1] * ST1[1] + T1[2] * ST1[2] + P.lowpass;
-      const float det = cxx * cyy - cxy * cxy;
-      vis = det > 0.f;
-      if (vis) {
-        const float idet = 1.f / det;
-        A = cyy * idet;
-        B = -cxy * idet;
-        C = cxx * idet;
-        mx = V.fx * pc.x * iz + V.cx;
-        my = V.fy * pc.y * iz + V.cy;
+    for (int k = 0; k < 3; ++k) {
+      T0[k] = J00 * V.R[k] + J02 * V.R[6 + k];
+      T1[k] = J11 * V.R[3 + k] + J12 * V.R[6 + k];
+    }
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      F0[k] = T0[0] * M[k] + T0[1] * M[3 + k] + T0[2] * M[6 + k];
+      F1[k] = T1[0] * M[k] + T1[1] * M[3 + k] + T1[2] * M[6 + k];
+    }
+    const float f00 = F0[0] * F0[0] + F0[1] * F0[1] + F0[2] * F0[2];
+    const float f11 = F1[0] * F1[0] + F1[1] * F1[1] + F1[2] * F1[2];
+    const float f01 = F0[0] * F1[0] + F0[1] * F1[1] + F0[2] * F1[2];
+    const float m01 = F0[0] * F1[1] - F0[1] * F1[0];
+    const float m02 = F0[0] * F1[2] - F0[2] * F1[0];
+    const float m12 = F0[1] * F1[2] - F0[2] * F1[1];
+    const float cxx = f00 + lp, cyy = f11 + lp, cxy = f01;
+    const float det = m01 * m01 + m02 * m02 + m12 * m12 + lp * (f00 + f11) + lp * lp;
+    if (!(det > 0.f)) {
+      cull(P.st, item);
+      continue;
+    }
+    const float idet = 1.f / det;
+    const float A = cyy * idet, B = -cxy * idet, C = cxx * idet;
+    BinParams b;
+    b.mx = V.fx * pc.x * iz + V.cx;
+    b.my = V.fy * pc.y * iz + V.cy;
+    b.tau = tau;
+    b.k = cxy / cyy;
+    b.sc = sqrtf(det / cyy);
+    b.isyy = 1.f / cyy;
+    b.h = sqrtf(tau * cyy);
+    b.rx = sqrtf(tau * cxx);
+    b.ys = cxy * sqrtf(tau / cxx);
+    // exact tile count, row by row
+    uint32_t count = 0;
+    int ty0 = 0, ty1 = -1;
+    if (tile_rows(b, V.tiles_y, &ty0, &ty1)) {
+      for (int ty = ty0; ty <= ty1; ++ty) {
+        int a, c;
+        if (row_tiles(b, ty, V.tiles_x, &a, &c)) count += (uint32_t)(c - a + 1);
       }
     }
-    // candidate rectangle of tiles
-    uint2 rect = make_uint2(0u, 0u);
-    int area = 0;
-    if (vis) {
-      const float rx = sqrtf(tau * cxx), ry = sqrtf(tau * cyy);
-      const float fx0 = fmaxf(ceilf((mx - rx - 15.5f) * (1.f / kTile)), 0.f);
-      const float fx1 = fminf(floorf((mx + rx - 0.5f) * (1.f / kTile)), (float)(V.tiles_x - 1));
-      const float fy0 = fmaxf(ceilf((my - ry - 15.5f) * (1.f / kTile)), 0.f);
-      const float fy1 = fminf(floorf((my + ry - 0.5f) * (1.f / kTile)), (float)(V.tiles_y - 1));
-      if (fx0 <= fx1 && fy0 <= fy1) {
-        int tx0 = (int)fx0, tx1 = (int)fx1, ty0 = (int)fy0, ty1 = (int)fy1;
-        rect = make_uint2((uint32_t)tx0 | ((uint32_t)ty0 << 16), (uint32_t)tx1 | ((uint32_t)ty1 << 16));
-        area = (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
-      } else {
-        vis = false;
-      }
-    }
-
-    // exact tile count, warp-cooperatively over the warp's candidate tiles
-    uint32_t total;
-    const uint32_t excl = warp_exclusive_sum((uint32_t)area, &total);
-    uint32_t my_count = 0;
-    for (uint32_t base = 0; base < total; base += 32) {
-      const uint32_t c = base + lane;
-      const int own = warp_owner(excl, min(c, total - 1));
-      const float omx = __shfl_sync(0xffffffffu, mx, own), omy = __shfl_sync(0xffffffffu, my, own);
-      const float oA = __shfl_sync(0xffffffffu, A, own), oB = __shfl_sync(0xffffffffu, B, own);
-      const float oC = __shfl_sync(0xffffffffu, C, own), otau = __shfl_sync(0xffffffffu, tau, own);
-      const uint32_t orx = __shfl_sync(0xffffffffu, rect.x, own), ory = __shfl_sync(0xffffffffu, rect.y, own);
-      const uint32_t oex = __shfl_sync(0xffffffffu, excl, own);
-      bool hit = false;
-      if (c < total) {
-        const int tx0 = orx & 0xffff, ty0 = orx >> 16, nx = (int)(ory & 0xffff) - tx0 + 1;
-        const int k = (int)(c - oex);
-        hit = tile_touched(omx, omy, oA, oB, oC, otau, tx0 + k % nx, ty0 + k / nx);
-      }
-      const uint32_t hits = __ballot_sync(0xffffffffu, hit);
-      // lanes of this chunk that belong to me: [lo, hi)
-      const int lo = (int)min(max((int64_t)excl - (int64_t)base, (int64_t)0), (int64_t)32);
-      const int hi = (int)min(max((int64_t)excl + area - (int64_t)base, (int64_t)0), (int64_t)32);
-      if (hi > lo) {
-        const uint32_t bits = (hi - lo == 32) ? 0xffffffffu : (((1u << (hi - lo)) - 1u) << lo);
-        my_count += __popc(hits & bits);
-      }
-    }
-    if (!live) continue;
-    if (my_count == 0) vis = false;
-    P.st.tiles[item] = vis ? my_count : 0u;
-    P.st.depth_key[item] = vis ? __float_as_uint(pc.z) : kCulledKey;
-    if (!vis) continue;
-    P.st.rect[item] = rect;
-    P.st.xy_tau_z[item] = make_float4(mx, my, tau, pc.z);
+    P.st.tiles[item] = count;
+    P.st.depth_key[item] = count ? __float_as_uint(pc.z) : kCulledKey;
+    if (!count) continue;
+    P.st.rect[item] = make_uint2((uint32_t)ty0 << 16, (uint32_t)(V.tiles_x - 1) | ((uint32_t)ty1 << 16));
+    P.st.xy_tau_z[item] = make_float4(b.mx, b.my, tau, pc.z);
     P.st.conic_o[item] = make_float4(A, B, C, o);
+    P.st.bin[2 * item] = make_float4(b.k, b.sc, b.isyy, b.h);
+    P.st.bin[2 * item + 1] = make_float4(b.rx, b.ys, 0.f, 0.f);
 
     // colour (Sec. 3.1): SH in the direction camera centre -> Gaussian
     float dx = p.x - V.campos[0], dy = p.y - V.campos[1], dz = p.z - V.campos[2];
@@ -187,17 +165,19 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
     dy *= il;
     dz *= il;
     float Y[16];
-    sh_eval(P.sh_degree, dx, dy, dz, Y);
-    float r = 0.5f, g = 0.5f, b = 0.5f;
-    for (int k = 0; k < used; ++k) {
-      r += Y[k] * my_sh[3 * k];
-      g += Y[k] * my_sh[3 * k + 1];
-      b += Y[k] * my_sh[3 * k + 2];
+    sh_eval(DEG, dx, dy, dz, Y);
+    float r = 0.5f, g = 0.5f, bl = 0.5f;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      r += Y[k] * shc[k][0];
+      g += Y[k] * shc[k][1];
+      bl += Y[k] * shc[k][2];
     }
-    P.st.rgb[item] = make_float4(fmaxf(r, 0.f), fmaxf(g, 0.f), fmaxf(b, 0.f), 0.f);
+    P.st.rgb[item] = make_float4(fmaxf(r, 0.f), fmaxf(g, 0.f), fmaxf(bl, 0.f), 0.f);
 
     // midpoint-depth frame: W = diag(1/s) (R Rq)^T maps camera offsets to the
     // unit-sphere frame of the ellipsoid x^2/sx^2 + y^2/sy^2 + z^2/sz^2 = 1
+    float RRq[9];
 #pragma unroll
     for (int r3 = 0; r3 < 3; ++r3)
 #pragma unroll
@@ -230,12 +210,12 @@ struct PreBwdParams {
   const float* opac;
   const float* sh;
   int64_t n;
-  int sh_degree, sh_coeffs;
+  int sh_coeffs;
   const ViewDev* views;
   int n_views;
   float lowpass;
   const uint32_t* tiles;
-  const float4* grad2d;   // 3 x float4 per item: (mx, my, A, B), (C, o, r, g), (b, -, -, -)
+  const float4* grad2d;   // 3 x float4 per item: (mx, my, a2, b2), (c2, log2 o, r, g), (b, -, -, -)
   float* d_means;
   float* d_scales;
   float* d_rots;
@@ -244,34 +224,58 @@ struct PreBwdParams {
   float* d_mean2d_abs;
 };
 
+template <int DEG>
 __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(PreBwdParams P) {
-  const int64_t i = (int64_t)blockIdx.x * kPreThreads + threadIdx.x;
-  if (i >= P.n) return;
-  const int used = (P.sh_degree + 1) * (P.sh_degree + 1);
-  const float3 p = make_float3(P.means[3 * i], P.means[3 * i + 1], P.means[3 * i + 2]);
-  const float s[3] = {P.scales[3 * i], P.scales[3 * i + 1], P.scales[3 * i + 2]};
-  const float4 q = reinterpret_cast<const float4*>(P.rots)[i];
-  const float qn2 = q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w;
-  const float qinv = rsqrtf(qn2);
-  const float qw = q.x * qinv, qx = q.y * qinv, qy = q.z * qinv, qz = q.w * qinv;
-  float Rq[9];
-  quat_to_rot(qw, qx, qy, qz, Rq);
-  const float M[9] = {Rq[0] * s[0], Rq[1] * s[1], Rq[2] * s[2], Rq[3] * s[0], Rq[4] * s[1], Rq[5] * s[2],
-                      Rq[6] * s[0], Rq[7] * s[1], Rq[8] * s[2]};
-  const float sig[6] = {M[0] * M[0] + M[1] * M[1] + M[2] * M[2], M[0] * M[3] + M[1] * M[4] + M[2] * M[5],
-                        M[0] * M[6] + M[1] * M[7] + M[2] * M[8], M[3] * M[3] + M[4] * M[4] + M[5] * M[5],
-                        M[3] * M[6] + M[4] * M[7] + M[5] * M[8], M[6] * M[6] + M[7] * M[7] + M[8] * M[8]};
-  const float* shrow = P.sh + i * (int64_t)P.sh_coeffs * 3;
-  const float opac_i = P.opac[i];
-
+  constexpr int K = (DEG + 1) * (DEG + 1);
+  constexpr int row = 3 * K + 1;
+  __shared__ float s_sh[kPreThreads * row];
+  const int64_t i0 = (int64_t)blockIdx.x * kPreThreads;
+  const int64_t i = i0 + threadIdx.x;
+  stage_sh<K>(P.sh, P.sh_coeffs, i0, P.n, s_sh);
+  __syncthreads();
+  const bool live = i < P.n;
+  float shc[K][3], dsh[K][3];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      shc[k][c] = s_sh[threadIdx.x * row + 3 * k + c];
+      dsh[k][c] = 0.f;
+    }
+  }
+  bool any = false;
   float dp[3] = {0.f, 0.f, 0.f};
   float dSig[6] = {0, 0, 0, 0, 0, 0};       // symmetric dL/dSigma (00,01,02,11,12,22)
   float dop = 0.f, m2abs = 0.f;
-  float dsh[48];
-  for (int k = 0; k < used * 3; ++k) dsh[k] = 0.f;
-  bool any = false;
+  float Rq[9], M[9], sig[6], s[3] = {1.f, 1.f, 1.f};
+  float qw = 1.f, qx = 0.f, qy = 0.f, qz = 0.f, qinv = 1.f, opac_i = 1.f;
+  float3 p = make_float3(0.f, 0.f, 0.f);
+  if (live) {
+    p = make_float3(P.means[3 * i], P.means[3 * i + 1], P.means[3 * i + 2]);
+    s[0] = P.scales[3 * i];
+    s[1] = P.scales[3 * i + 1];
+    s[2] = P.scales[3 * i + 2];
+    const float4 q = reinterpret_cast<const float4*>(P.rots)[i];
+    qinv = rsqrtf(q.x * q.x + q.y * q.y + q.z * q.z + q.w * q.w);
+    qw = q.x * qinv;
+    qx = q.y * qinv;
+    qy = q.z * qinv;
+    qz = q.w * qinv;
+    opac_i = P.opac[i];
+  }
+  quat_to_rot(qw, qx, qy, qz, Rq);
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) M[3 * r + c] = Rq[3 * r + c] * s[c];
+  sig[0] = M[0] * M[0] + M[1] * M[1] + M[2] * M[2];
+  sig[1] = M[0] * M[3] + M[1] * M[4] + M[2] * M[5];
+  sig[2] = M[0] * M[6] + M[1] * M[7] + M[2] * M[8];
+  sig[3] = M[3] * M[3] + M[4] * M[4] + M[5] * M[5];
+  sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
+  sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
 
-  for (int v = 0; v < P.n_views; ++v) {
+  for (int v = 0; v < P.n_views && live; ++v) {
     const int64_t item = (int64_t)v * P.n + i;
     if (P.tiles[item] == 0) continue;
     any = true;
@@ -361,36 +365,56 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(PreBwd
     for (int k = 0; k < 3; ++k) dp[k] += V.R[k] * dpc[0] + V.R[3 + k] * dpc[1] + V.R[6 + k] * dpc[2];
 
     // colour: rgb = max(0, sum sh Y(dir) + 0.5), dir = (p - campos)/|p - campos|
-    float dvx = p.x - V.campos[0], dvy = p.y - V.campos[1], dvz = p.z - V.campos[2];
+    const float dvx = p.x - V.campos[0], dvy = p.y - V.campos[1], dvz = p.z - V.campos[2];
     const float il = rsqrtf(dvx * dvx + dvy * dvy + dvz * dvz);
     const float dx = dvx * il, dy = dvy * il, dz = dvz * il;
     float Y[16];
-    sh_eval(P.sh_degree, dx, dy, dz, Y);
+    sh_eval(DEG, dx, dy, dz, Y);
     float raw[3] = {0.5f, 0.5f, 0.5f};
-    for (int k = 0; k < used; ++k) {
-      raw[0] += Y[k] * shrow[3 * k];
-      raw[1] += Y[k] * shrow[3 * k + 1];
-      raw[2] += Y[k] * shrow[3 * k + 2];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      raw[0] += Y[k] * shc[k][0];
+      raw[1] += Y[k] * shc[k][1];
+      raw[2] += Y[k] * shc[k][2];
     }
     const float dr[3] = {raw[0] >= 0.f ? drgb[0] : 0.f, raw[1] >= 0.f ? drgb[1] : 0.f,
                          raw[2] >= 0.f ? drgb[2] : 0.f};
     float cdot[16];
-    for (int k = 0; k < used; ++k) {
-      dsh[3 * k] += Y[k] * dr[0];
-      dsh[3 * k + 1] += Y[k] * dr[1];
-      dsh[3 * k + 2] += Y[k] * dr[2];
-      cdot[k] = shrow[3 * k] * dr[0] + shrow[3 * k + 1] * dr[1] + shrow[3 * k + 2] * dr[2];
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+      dsh[k][0] += Y[k] * dr[0];
+      dsh[k][1] += Y[k] * dr[1];
+      dsh[k][2] += Y[k] * dr[2];
+      cdot[k] = shc[k][0] * dr[0] + shc[k][1] * dr[1] + shc[k][2] * dr[2];
     }
-    if (P.sh_degree > 0) {
+    if (DEG > 0) {
       float gdir[3] = {0.f, 0.f, 0.f};
-      sh_grad_dot(P.sh_degree, dx, dy, dz, cdot, gdir);
+      sh_grad_dot(DEG, dx, dy, dz, cdot, gdir);
       const float proj = gdir[0] * dx + gdir[1] * dy + gdir[2] * dz;
       dp[0] += (gdir[0] - proj * dx) * il;
       dp[1] += (gdir[1] - proj * dy) * il;
       dp[2] += (gdir[2] - proj * dz) * il;
     }
   }
-  if (!any) return;
+
+  // SH gradients: staged back through shared memory, then added to the
+  // block's rows with coalesced read-modify-writes
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < K; ++k)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s_sh[threadIdx.x * row + 3 * k + c] = dsh[k][c];
+  __syncthreads();
+  {
+    constexpr int per = 3 * K;
+    const int64_t rows = (P.n - i0 < kPreThreads) ? (P.n - i0) : (int64_t)kPreThreads;
+    for (int f = threadIdx.x; f < rows * per; f += kPreThreads) {
+      const int g = f / per, c = f - g * per;
+      const float v = s_sh[g * row + c];
+      if (v != 0.f) P.d_sh[(i0 + g) * (int64_t)P.sh_coeffs * 3 + c] += v;
+    }
+  }
+  if (!live || !any) return;
 
   // Sigma = M M^T, M = Rq diag(s): dM = 2 dSigma M
   const float G[9] = {dSig[0], dSig[1], dSig[2], dSig[1], dSig[3], dSig[4], dSig[2], dSig[4], dSig[5]};
@@ -435,8 +459,6 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(PreBwd
   P.d_rots[4 * i + 2] += dqy;
   P.d_rots[4 * i + 3] += dqz;
   P.d_opac[i] += dop;
-  float* dshrow = P.d_sh + i * (int64_t)P.sh_coeffs * 3;
-  for (int k = 0; k < used * 3; ++k) dshrow[k] += dsh[k];
   if (P.d_mean2d_abs) P.d_mean2d_abs[i] += m2abs;
 }
 
@@ -451,7 +473,6 @@ cudaError_t launch_preprocess(const gs_scene& sc, const ViewDev* views, int n_vi
   P.opac = sc.opacities;
   P.sh = sc.sh;
   P.n = sc.n;
-  P.sh_degree = sc.sh_degree;
   P.sh_coeffs = sc.sh_coeffs;
   P.views = views;
   P.n_views = n_views;
@@ -460,10 +481,14 @@ cudaError_t launch_preprocess(const gs_scene& sc, const ViewDev* views, int n_vi
   P.lowpass = cfg.lowpass;
   P.alpha_min = cfg.alpha_min;
   P.st = st;
-  const int used = (sc.sh_degree + 1) * (sc.sh_degree + 1);
-  const size_t smem = (size_t)kPreThreads * (used * 3 + 1) * sizeof(float);
   const int blocks = ceil_div(sc.n, kPreThreads);
-  if (blocks > 0) GS_TIMED("preprocess", stream, (preprocess_kernel<<<blocks, kPreThreads, smem, stream>>>(P)));
+  if (blocks == 0) return cudaSuccess;
+  switch (sc.sh_degree) {
+    case 0: GS_TIMED("preprocess", stream, (preprocess_kernel<0><<<blocks, kPreThreads, 0, stream>>>(P))); break;
+    case 1: GS_TIMED("preprocess", stream, (preprocess_kernel<1><<<blocks, kPreThreads, 0, stream>>>(P))); break;
+    case 2: GS_TIMED("preprocess", stream, (preprocess_kernel<2><<<blocks, kPreThreads, 0, stream>>>(P))); break;
+    default: GS_TIMED("preprocess", stream, (preprocess_kernel<3><<<blocks, kPreThreads, 0, stream>>>(P))); break;
+  }
   return cudaGetLastError();
 }
 
@@ -477,7 +502,6 @@ cudaError_t launch_preprocess_backward(const gs_scene& sc, const ViewDev* views,
   P.opac = sc.opacities;
   P.sh = sc.sh;
   P.n = sc.n;
-  P.sh_degree = sc.sh_degree;
   P.sh_coeffs = sc.sh_coeffs;
   P.views = views;
   P.n_views = n_views;
@@ -491,8 +515,21 @@ cudaError_t launch_preprocess_backward(const gs_scene& sc, const ViewDev* views,
   P.d_sh = gr.d_sh;
   P.d_mean2d_abs = gr.d_mean2d_abs;
   const int blocks = ceil_div(sc.n, kPreThreads);
-  if (blocks > 0)
-    GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<<<blocks, kPreThreads, 0, stream>>>(P)));
+  if (blocks == 0) return cudaSuccess;
+  switch (sc.sh_degree) {
+    case 0:
+      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<0><<<blocks, kPreThreads, 0, stream>>>(P)));
+      break;
+    case 1:
+      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<1><<<blocks, kPreThreads, 0, stream>>>(P)));
+      break;
+    case 2:
+      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<2><<<blocks, kPreThreads, 0, stream>>>(P)));
+      break;
+    default:
+      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<3><<<blocks, kPreThreads, 0, stream>>>(P)));
+      break;
+  }
   return cudaGetLastError();
 }
 

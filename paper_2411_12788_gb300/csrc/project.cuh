@@ -1,6 +1,6 @@
 // Device helpers for the per-Gaussian projection (Sec. 3.1): quaternion
 // rotation, real spherical harmonics up to degree 3 and the exact
-// tile-touch predicate.  Shared by the preprocess, binning and backward
+// row-by-row tile coverage of a Gaussian's support.  Shared by the preprocess, binning and backward
 // kernels so that every call site evaluates bit-identical arithmetic.
 #pragma once
 
@@ -115,73 +115,52 @@ __device__ __forceinline__ void sh_grad_dot(int degree, float x, float y, float 
   g[2] += gz;
 }
 
-// q(d) = A dx^2 + 2 B dx dy + C dy^2 with explicitly rounded operations, so
-// that every call site (counting, emitting) decides identically.
-__device__ __forceinline__ float conic_q(float A, float B, float C, float dx, float dy) {
-  float t = __fmul_rn(__fmul_rn(C, dy), dy);
-  t = __fmaf_rn(__fmul_rn(__fmul_rn(2.f, B), dx), dy, t);
-  return __fmaf_rn(__fmul_rn(A, dx), dx, t);
+// Exact tile rows of the support q <= tau, one row of tiles at a time.
+//
+// With the 2-D covariance S = [[Sxx, Sxy], [Sxy, Syy]] (S = conic^-1), the
+// support at height dy (offset from the centre) is the x-interval
+//   k dy -+ sc sqrt(tau - dy^2 / Syy),  k = Sxy / Syy,  sc^2 = det(S) / Syy,
+// the x | y decomposition of the Mahalanobis distance.  Over a band of rows
+// dy in [lo, hi] the union of these intervals is [xa, xb]: the right end is
+// concave in dy with its maximum rx = sqrt(tau Sxx) at dy = ys =
+// Sxy sqrt(tau / Sxx) (the ellipse's rightmost point), the left end mirrors
+// it at -ys.  Tile column tx of a tile row is touched iff its pixel-centre
+// range [16 tx + 0.5, 16 tx + 15.5] meets [mx + xa, mx + xb]; that is the
+// same set as "the minimum of q over the tile's pixel-centre rectangle is
+// <= tau".  Counting (preprocess) and emitting (duplicate) call this with
+// the same stored parameters and explicitly rounded arithmetic, so both
+// produce the same tiles.
+struct BinParams {
+  float mx, my, tau;   // centre and support bound
+  float k, sc, isyy;   // x | y decomposition
+  float h, rx, ys;     // half-height sqrt(tau Syy), half-width, y of the rightmost point
+};
+
+__device__ __forceinline__ bool row_tiles(const BinParams& b, int ty, int tiles_x, int* tx_a, int* tx_b) {
+  const float lo = __fsub_rn((float)(ty * kTile) + 0.5f, b.my);
+  const float hi = __fadd_rn(lo, (float)(kTile - 1));
+  const float a = fmaxf(lo, -b.h), c = fminf(hi, b.h);
+  if (a > c) return false;
+  const float ra = __fmul_rn(b.sc, __fsqrt_rn(fmaxf(__fmaf_rn(-__fmul_rn(a, a), b.isyy, b.tau), 0.f)));
+  const float rc = __fmul_rn(b.sc, __fsqrt_rn(fmaxf(__fmaf_rn(-__fmul_rn(c, c), b.isyy, b.tau), 0.f)));
+  const float xb = (b.ys >= a && b.ys <= c) ? b.rx : fmaxf(__fmaf_rn(b.k, a, ra), __fmaf_rn(b.k, c, rc));
+  const float xa = (-b.ys >= a && -b.ys <= c) ? -b.rx : fminf(__fmaf_rn(b.k, a, -ra), __fmaf_rn(b.k, c, -rc));
+  const float fa = ceilf(__fmul_rn(__fsub_rn(__fadd_rn(b.mx, xa), (float)kTile - 0.5f), 1.f / kTile));
+  const float fb = floorf(__fmul_rn(__fsub_rn(__fadd_rn(b.mx, xb), 0.5f), 1.f / kTile));
+  const int ia = (int)fmaxf(fa, 0.f);
+  const int ib = (int)fminf(fb, (float)(tiles_x - 1));
+  *tx_a = ia;
+  *tx_b = ib;
+  return ia <= ib;
 }
 
-// Tile (tx, ty) is touched iff the minimum of q over its pixel-centre
-// rectangle [16tx+0.5, 16tx+15.5] x [16ty+0.5, 16ty+15.5] is <= tau.  The
-// minimum of the convex quadratic is 0 if the centre is inside; otherwise it
-// lies on an edge, where q is a 1-D quadratic minimised at its clamped vertex.
-__device__ __forceinline__ bool tile_touched(float mx, float my, float A, float B, float C, float tau, int tx,
-                                             int ty) {
-  const float x0 = (float)(tx * kTile) + 0.5f, x1 = x0 + (float)(kTile - 1);
-  const float y0 = (float)(ty * kTile) + 0.5f, y1 = y0 + (float)(kTile - 1);
-  if (mx >= x0 && mx <= x1 && my >= y0 && my <= y1) return true;
-  const float lox = __fsub_rn(x0, mx), hix = __fsub_rn(x1, mx);
-  const float loy = __fsub_rn(y0, my), hiy = __fsub_rn(y1, my);
-  float best = INFINITY;
-  // vertical edges (dx fixed): vertex at dy = -B dx / C
-  {
-    float dy = fminf(fmaxf(__fdiv_rn(-__fmul_rn(B, lox), C), loy), hiy);
-    best = fminf(best, conic_q(A, B, C, lox, dy));
-    dy = fminf(fmaxf(__fdiv_rn(-__fmul_rn(B, hix), C), loy), hiy);
-    best = fminf(best, conic_q(A, B, C, hix, dy));
-  }
-  // horizontal edges (dy fixed): vertex at dx = -B dy / A
-  {
-    float dx = fminf(fmaxf(__fdiv_rn(-__fmul_rn(B, loy), A), lox), hix);
-    best = fminf(best, conic_q(A, B, C, dx, loy));
-    dx = fminf(fmaxf(__fdiv_rn(-__fmul_rn(B, hiy), A), lox), hix);
-    best = fminf(best, conic_q(A, B, C, dx, hiy));
-  }
-  return best <= tau;
-}
-
-// Candidate-tile rectangle packed as (tx0 | ty0 << 16, tx1 | ty1 << 16).
-__device__ __forceinline__ int rect_area(uint2 r) {
-  int tx0 = r.x & 0xffff, ty0 = r.x >> 16, tx1 = r.y & 0xffff, ty1 = r.y >> 16;
-  return (tx1 - tx0 + 1) * (ty1 - ty0 + 1);
-}
-
-// Per-lane owner search for warp-cooperative tile enumeration: the lane
-// `owner` with excl[owner] <= c < excl[owner] + area[owner], given each
-// lane's exclusive prefix `excl` of the candidate counts.
-__device__ __forceinline__ int warp_owner(uint32_t excl, uint32_t c) {
-  int lo = 0;
-#pragma unroll
-  for (int step = 16; step >= 1; step >>= 1) {
-    int cand = lo + step;
-    uint32_t e = __shfl_sync(0xffffffffu, excl, cand & 31);
-    if (cand < 32 && e <= c) lo = cand;
-  }
-  return lo;
-}
-
-__device__ __forceinline__ uint32_t warp_exclusive_sum(uint32_t v, uint32_t* total) {
-  const int lane = threadIdx.x & 31;
-  uint32_t x = v;
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1) {
-    uint32_t t = __shfl_up_sync(0xffffffffu, x, off);
-    if (lane >= off) x += t;
-  }
-  *total = __shfl_sync(0xffffffffu, x, 31);
-  return x - v;
+// Rows [ty0, ty1] of tiles whose pixel-centre band meets [my - h, my + h].
+__device__ __forceinline__ bool tile_rows(const BinParams& b, int tiles_y, int* ty0, int* ty1) {
+  const float f0 = ceilf(__fmul_rn(__fsub_rn(__fsub_rn(b.my, b.h), (float)kTile - 0.5f), 1.f / kTile));
+  const float f1 = floorf(__fmul_rn(__fsub_rn(__fadd_rn(b.my, b.h), 0.5f), 1.f / kTile));
+  *ty0 = (int)fmaxf(f0, 0.f);
+  *ty1 = (int)fminf(f1, (float)(tiles_y - 1));
+  return *ty0 <= *ty1;
 }
 
 }  // namespace gs

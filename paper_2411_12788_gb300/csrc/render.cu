@@ -361,25 +361,24 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
         const float e = expo(ex, dx, dy);
         const bool act = pos < nc && e >= P.e_min;
         if (!__any_sync(0xffffffffu, act)) continue;
+        const float T0 = s_T[pt];
+        const float F0 = s_F[pt];
+        const float4 pg = s_pg[pt];
         const float araw = ex2_approx(e);
         const float a = act ? fminf(P.alpha_max, araw) : 0.f;
         // exclusive product of (1 - a) over the lanes, continued from s_T
         const float prod = scan_mul(1.f - a);
         float excl = __shfl_up_sync(0xffffffffu, prod, 1);
         if (lane == 0) excl = 1.f;
-        const float T0 = s_T[pt];
         const float Tl = T0 * excl;
         const float w = a * Tl;
-        const float4 pg = s_pg[pt];
         const float cg = col.x * pg.x + col.y * pg.y + col.z * pg.z;
         const float fs = scan_add(w * cg);
-        const float F0 = s_F[pt];
-        const float total_prod = __shfl_sync(0xffffffffu, prod, 31);
-        const float total_fs = __shfl_sync(0xffffffffu, fs, 31);
+        // lane 31 holds the chunk's totals: carry the pixel's state forward
         __syncwarp();
-        if (lane == 0) {
-          s_T[pt] = T0 * total_prod;
-          s_F[pt] = F0 + total_fs;
+        if (lane == 31) {
+          s_T[pt] = T0 * prod;
+          s_F[pt] = F0 + fs;
         }
         if (act) {
           acc[6] += w * pg.x;
