@@ -89,27 +89,20 @@ __device__ __forceinline__ float rcp_approx(float x) {
   return y;
 }
 
-// Inclusive lane scans (product / sum) in 2 instructions per step.
-__device__ __forceinline__ float scan_mul(float x) {
+// Inclusive lane scan of the affine maps x -> m x + f (applied front to back):
+// (m1, f1) then (m2, f2) composes to (m1 m2, f1 + m1 f2).  After the scan lane
+// l holds (prod_{k<=l} m_k, sum_{k<=l} f_k prod_{j<k} m_j): the transmittance
+// product and the transmittance-weighted sum in one 5-step chain.
+__device__ __forceinline__ void scan_affine(float& m, float& f) {
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1)
-    asm("{\n\t.reg .f32 t;\n\t.reg .pred p;\n\t"
-        "shfl.sync.up.b32 t|p, %0, %1, 0, 0xffffffff;\n\t"
-        "@p mul.f32 %0, %0, t;\n\t}"
-        : "+f"(x)
+    asm("{\n\t.reg .f32 tm, tf;\n\t.reg .pred p;\n\t"
+        "shfl.sync.up.b32 tm|p, %0, %2, 0, 0xffffffff;\n\t"
+        "shfl.sync.up.b32 tf, %1, %2, 0, 0xffffffff;\n\t"
+        "@p fma.rn.f32 %1, tm, %1, tf;\n\t"
+        "@p mul.f32 %0, %0, tm;\n\t}"
+        : "+f"(m), "+f"(f)
         : "r"(off));
-  return x;
-}
-
-__device__ __forceinline__ float scan_add(float x) {
-#pragma unroll
-  for (int off = 1; off < 32; off <<= 1)
-    asm("{\n\t.reg .f32 t;\n\t.reg .pred p;\n\t"
-        "shfl.sync.up.b32 t|p, %0, %1, 0, 0xffffffff;\n\t"
-        "@p add.f32 %0, %0, t;\n\t}"
-        : "+f"(x)
-        : "r"(off));
-  return x;
 }
 
 __device__ __forceinline__ int find_view(const ViewDev* views, int n_views, int tile) {
@@ -352,11 +345,13 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
       const uint32_t pos = c0 + lane;
       const float dx0 = bxf - m.x, dy0 = byf - m.y;
       float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-#pragma unroll 8
-      for (int p = 0; p < 32; ++p) {
+      // pixels of this warp that are still blending at this chunk
+      uint32_t pmask = __ballot_sync(0xffffffffu, s_nc[warp * 32 + lane] > c0);
+      while (pmask) {
+        const int p = __ffs(pmask) - 1;
+        pmask &= pmask - 1;
         const int pt = warp * 32 + p;                 // the pixel's thread id
         const uint32_t nc = s_nc[pt];
-        if (c0 >= nc) continue;                       // pixel stopped before this chunk
         const float dx = dx0 + (float)(p & 7), dy = dy0 + (float)(p >> 3);
         const float e = expo(ex, dx, dy);
         const bool act = pos < nc && e >= P.e_min;
@@ -366,26 +361,27 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
         const float4 pg = s_pg[pt];
         const float araw = ex2_approx(e);
         const float a = act ? fminf(P.alpha_max, araw) : 0.f;
-        // exclusive product of (1 - a) over the lanes, continued from s_T
-        const float prod = scan_mul(1.f - a);
-        float excl = __shfl_up_sync(0xffffffffu, prod, 1);
-        if (lane == 0) excl = 1.f;
-        const float Tl = T0 * excl;
-        const float w = a * Tl;
         const float cg = col.x * pg.x + col.y * pg.y + col.z * pg.z;
-        const float fs = scan_add(w * cg);
+        // one scan gives the product of (1 - a) and sum a_k cg_k prod_{j<k} (1 - a_j)
+        float m = 1.f - a, f = a * cg;
+        scan_affine(m, f);
+        float mex = __shfl_up_sync(0xffffffffu, m, 1);     // exclusive product
+        if (lane == 0) mex = 1.f;
+        const float Tl = T0 * mex;
+        const float w = a * Tl;
+        const float Fl = F0 + T0 * f;                      // sum_{k<=l} w_k cg_k
         // lane 31 holds the chunk's totals: carry the pixel's state forward
         __syncwarp();
         if (lane == 31) {
-          s_T[pt] = T0 * prod;
-          s_F[pt] = F0 + fs;
+          s_T[pt] = T0 * m;
+          s_F[pt] = Fl;
         }
         if (act) {
           acc[6] += w * pg.x;
           acc[7] += w * pg.y;
           acc[8] += w * pg.z;
           if (araw <= P.alpha_max) {
-            const float dal = Tl * cg - (pg.w - (F0 + fs)) * rcp_approx(1.f - a);
+            const float dal = Tl * cg - (pg.w - Fl) * rcp_approx(1.f - a);
             const float de = dal * a * kLn2;          // dL/de
             acc[5] += de;                             // d log2 o
             acc[2] += de * dx * dx;                   // d a2

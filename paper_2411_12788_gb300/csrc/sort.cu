@@ -7,7 +7,8 @@
 //   * one histogram kernel counts every pass's digits in a single read;
 //   * each CTA of the pass kernel takes the next tile of 3840 keys (dynamic
 //     tile id, so every predecessor tile is already running), ranks its keys
-//     stably by digit with warp-level match_any, publishes its per-digit
+//     stably by digit inside each warp (the lanes sharing a digit found by
+//     one ballot per digit bit), publishes its per-digit
 //     counts, and looks back over its predecessors' published counts
 //     (decoupled look-back) to find its global offset per digit; keys are
 //     then staged in shared memory in output order and written out so that
@@ -114,49 +115,85 @@ __global__ void __launch_bounds__(kRadix) radix_scan_hist_kernel(uint32_t* hist)
   h[threadIdx.x] = s[threadIdx.x] - v;
 }
 
-__global__ void __launch_bounds__(kSortThreads) radix_onesweep_kernel(
+// Dynamic shared memory of the pass kernel: the CTA's keys (original order,
+// then reused for the keys in output order), its values (original order) and
+// its values in output order.
+constexpr size_t kOnesweepDynSmem = 3 * (size_t)kSortTile * sizeof(uint32_t);
+constexpr long kCopyWaitLimit = 1L << 22;
+
+__global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift, int digit_bits,
     const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ counter,
     uint32_t* __restrict__ lookback, uint32_t* __restrict__ status) {
-  __shared__ uint32_t s_keys[kSortTile];
-  __shared__ uint32_t s_vals[kSortTile];
+  extern __shared__ __align__(16) uint32_t s_dyn[];
+  uint32_t* s_keys = s_dyn;                       // keys: loaded, then in output order
+  uint32_t* s_vin = s_dyn + kSortTile;            // values as loaded
+  uint32_t* s_vals = s_dyn + 2 * kSortTile;       // values in output order
   __shared__ uint32_t s_warp_hist[kWarps][kRadix];
   __shared__ uint32_t s_cta_start[kRadix];
-  __shared__ int64_t s_out_base[kRadix];
+  __shared__ uint32_t s_out_base[kRadix];         // output index of the CTA's first key of each digit, minus its start
   __shared__ uint32_t s_tile;
+  __shared__ __align__(8) uint64_t s_bar;
 
   const int tid = threadIdx.x;
   const int lane = tid & 31;
   const int warp = tid >> 5;
-  if (tid == 0) s_tile = atomicAdd(counter, 1u);
+  if (tid == 0) {
+    s_tile = atomicAdd(counter, 1u);
+    mbar_init(&s_bar, 1);
+  }
   for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&s_warp_hist[0][0])[i] = 0;
   __syncthreads();
   const int64_t tile = s_tile;
   const int64_t tile_start = tile * kSortTile;
+  const int count = (int)((n - tile_start < kSortTile) ? (n - tile_start) : (int64_t)kSortTile);
 
-  // 1. load keys (warp-striped: each warp owns a contiguous segment) and rank
-  //    them stably by digit inside the warp.
+  // 0. stage the tile's keys and values in shared memory: two bulk copies of
+  //    the 16-byte-aligned part, plain loads for a ragged tail of < 4 keys
+  const int bulk = count & ~3;
+  if (tid == 0) {
+    if (bulk > 0) {
+      mbar_arrive_expect_tx(&s_bar, 2u * (uint32_t)bulk * 4u);
+      bulk_copy_g2s(s_keys, keys_in + tile_start, (uint32_t)bulk * 4u, &s_bar);
+      bulk_copy_g2s(s_vin, vals_in + tile_start, (uint32_t)bulk * 4u, &s_bar);
+    }
+  }
+  if (tid < count - bulk) {
+    s_keys[bulk + tid] = keys_in[tile_start + bulk + tid];
+    s_vin[bulk + tid] = vals_in[tile_start + bulk + tid];
+  }
+  if (bulk > 0 && !mbar_wait(&s_bar, 0, kCopyWaitLimit)) {
+    atomicOr(status, kStatusTimeout);
+    mbar_wait(&s_bar, 0, kCopyWaitLimit);        // let the copy land before the CTA exits
+  }
+  __syncthreads();
+
+  // 1. rank the keys stably by digit inside each warp (warp-striped: warp w
+  //    owns keys [480 w, 480 w + 480) of the tile)
   uint32_t key[kSortItemsPerThread];
   uint32_t rank[kSortItemsPerThread];
   const uint32_t lt = lanemask_lt();
-  const int64_t warp_start = tile_start + warp * kWarpKeys;
-  // issue every load of this thread before ranking (the ranking steps below
-  // are ordered by __syncwarp, which would otherwise serialise the loads)
+  const int warp_start = warp * kWarpKeys;
 #pragma unroll
   for (int k = 0; k < kSortItemsPerThread; ++k) {
-    const int64_t i = warp_start + k * 32 + lane;
-    key[k] = i < n ? keys_in[i] : 0u;
+    const int i = warp_start + k * 32 + lane;
+    key[k] = i < count ? s_keys[i] : 0u;
   }
 #pragma unroll
   for (int k = 0; k < kSortItemsPerThread; ++k) {
-    int64_t i = warp_start + k * 32 + lane;
-    bool valid = i < n;
-    uint32_t vmask = __ballot_sync(0xffffffffu, valid);
+    const int i = warp_start + k * 32 + lane;
+    const bool valid = i < count;
+    const uint32_t d = (key[k] >> shift) & (kRadix - 1);
+    // lanes holding the same digit: AND over the digit's bits of the ballot
+    // of that bit (or of its complement)
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    for (int b = 0; b < digit_bits; ++b) {
+      const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+      peers &= ((d >> b) & 1u) ? bal : ~bal;
+    }
     rank[k] = 0;
     if (valid) {
-      uint32_t d = (key[k] >> shift) & (kRadix - 1);
-      uint32_t peers = __match_any_sync(vmask, d);
       int leader = __ffs(peers) - 1;
       uint32_t before = 0;
       if (lane == leader) {
@@ -189,25 +226,41 @@ __global__ void __launch_bounds__(kSortThreads) radix_onesweep_kernel(
     }
   }
 
-  // 3. decoupled look-back for this digit
+  // 3. decoupled look-back for this digit, 8 predecessors per round: the
+  //    loads of a window are independent, so a round costs one L2 latency
   uint32_t exclusive = 0;
   if (tile > 0) {
     const int d = tid;
     int64_t j = tile - 1;
     long spins = 0;
+    constexpr int kWin = 8;
     while (j >= 0) {
-      uint32_t s = *(volatile uint32_t*)(lookback + j * kRadix + d);
-      uint32_t flag = s & ~kValueMask;
-      if (flag == 0) {
-        if (++spins > kSpinLimit) {
-          atomicOr(status, kStatusTimeout);
-          break;
+      uint32_t st[kWin];
+#pragma unroll
+      for (int w = 0; w < kWin; ++w)
+        st[w] = (j - w >= 0) ? *(volatile uint32_t*)(lookback + (j - w) * kRadix + d) : (uint32_t)kFlagPrefix;
+      uint32_t add = 0;
+      int used = 0;
+      bool found = false, stalled = false;
+#pragma unroll
+      for (int w = 0; w < kWin; ++w) {
+        if (found || stalled) continue;
+        const uint32_t flag = st[w] & ~kValueMask;
+        if (flag == 0) {
+          stalled = true;
+          continue;
         }
-        continue;
+        add += st[w] & kValueMask;
+        ++used;
+        if (flag == kFlagPrefix) found = true;
       }
-      exclusive += s & kValueMask;
-      if (flag == kFlagPrefix) break;
-      --j;
+      exclusive += add;
+      j -= used;
+      if (found) break;
+      if (stalled && ++spins > kSpinLimit) {
+        atomicOr(status, kStatusTimeout);
+        break;
+      }
     }
     *(volatile uint32_t*)(lookback + tile * kRadix + d) = kFlagPrefix | (exclusive + cta_count);
   }
@@ -229,29 +282,28 @@ __global__ void __launch_bounds__(kSortThreads) radix_onesweep_kernel(
     for (int w = 0; w < warp; ++w) add += s_warp_tot[w];
     uint32_t start = v - cta_count + add;
     s_cta_start[d] = start;
-    s_out_base[d] = (int64_t)digit_base[d] + exclusive - start;
+    s_out_base[d] = digit_base[d] + exclusive - start;
   }
   __syncthreads();
 
   // 5. stage keys and values in output order
 #pragma unroll
   for (int k = 0; k < kSortItemsPerThread; ++k) {
-    int64_t i = tile_start + warp * kWarpKeys + k * 32 + lane;
-    if (i < n) {
-      uint32_t d = (key[k] >> shift) & (kRadix - 1);
-      uint32_t pos = s_cta_start[d] + s_warp_hist[warp][d] + rank[k];
+    const int i = warp_start + k * 32 + lane;
+    if (i < count) {
+      const uint32_t d = (key[k] >> shift) & (kRadix - 1);
+      const uint32_t pos = s_cta_start[d] + s_warp_hist[warp][d] + rank[k];
       s_keys[pos] = key[k];
-      s_vals[pos] = vals_in[i];
+      s_vals[pos] = s_vin[i];
     }
   }
   __syncthreads();
 
-  // 6. write out
-  const int count = (int)((n - tile_start < kSortTile) ? (n - tile_start) : (int64_t)kSortTile);
+  // 6. write out: runs of equal digits are contiguous in the output
   for (int i = tid; i < count; i += kSortThreads) {
-    uint32_t k = s_keys[i];
-    uint32_t d = (k >> shift) & (kRadix - 1);
-    int64_t out = s_out_base[d] + i;
+    const uint32_t k = s_keys[i];
+    const uint32_t d = (k >> shift) & (kRadix - 1);
+    const uint32_t out = s_out_base[d] + (uint32_t)i;
     keys_out[out] = k;
     vals_out[out] = s_vals[i];
   }
@@ -355,6 +407,16 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
                              int64_t n, int bits, void* scratch, uint32_t* status, cudaStream_t stream,
                              const char* tag) {
   if (n <= 0 || bits <= 0) return cudaSuccess;
+  if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(keys_alt) | reinterpret_cast<uintptr_t>(vals) |
+       reinterpret_cast<uintptr_t>(vals_alt)) & 15)
+    return cudaErrorMisalignedAddress;     // the bulk copies need 16-byte aligned rows
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t ea = cudaFuncSetAttribute(radix_onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                          (int)kOnesweepDynSmem);
+    if (ea != cudaSuccess) return ea;
+    attr_set = true;
+  }
   const int passes = (bits + kRadixBits - 1) / kRadixBits;
   RadixScratch s = carve(scratch, n);
   const int64_t tiles = sort_tiles(n);
@@ -369,8 +431,9 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
   uint32_t *kin = keys, *kout = keys_alt, *vin = vals, *vout = vals_alt;
   for (int p = 0; p < passes; ++p) {
     GS_TIMED(depth ? "depth_sort_onesweep" : "tile_sort_onesweep", stream,
-             (radix_onesweep_kernel<<<(unsigned)tiles, kSortThreads, 0, stream>>>(
-                 kin, vin, kout, vout, n, p * kRadixBits, s.hist + p * kRadix, s.counters + p,
+             (radix_onesweep_kernel<<<(unsigned)tiles, kSortThreads, kOnesweepDynSmem, stream>>>(
+                 kin, vin, kout, vout, n, p * kRadixBits, std::min(kRadixBits, bits - p * kRadixBits),
+                 s.hist + p * kRadix, s.counters + p,
                  s.lookback + (size_t)p * tiles * kRadix, status)));
     std::swap(kin, kout);
     std::swap(vin, vout);
