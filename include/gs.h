@@ -210,8 +210,8 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
  * application that owns all GPU memory and hands out fixed buffers, code
  * where an allocation could block or fail mid-frame).  It computes exactly
  * what gs_bin_sort computes, but the caller passes the outputs directly
- * (tile_ids and items: device [n_entries] uint32; ranges: device
- * [total_tiles][2] uint32, [start, end) per tile) and the sort's scratch comes
+ * (tile_ids and items: device [n_entries] uint32, 16-byte aligned; ranges:
+ * device [total_tiles][2] uint32, [start, end) per tile) and the sort's scratch comes
  * from a fixed file-scope device array of GS_NOALLOC_SCRATCH_BYTES that every
  * GPU loading the library keeps until exit; nothing is allocated.
  *  - plan->n_entries above GS_NOALLOC_MAX_ENTRIES: GS_ERR_CAPACITY, nothing

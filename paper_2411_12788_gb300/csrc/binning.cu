@@ -39,6 +39,13 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* _
   b.rx = b1.x;
   b.ys = b1.y;
   const ViewDev& V = views[item / n];
+  // this item's entries are the contiguous run [off, off + cnt): write it as
+  // scalars up to a 16-byte boundary, then in groups of four (uint4), then
+  // the scalar tail
+  const uint32_t head = min((4u - (off & 3u)) & 3u, cnt);
+  const uint32_t groups_end = head + ((cnt - head) & ~3u);
+  const uint4 vals4 = make_uint4(item, item, item, item);
+  uint32_t buf[4];
   uint32_t written = 0;
   int ty0, ty1;
   if (tile_rows(b, V.tiles_y, &ty0, &ty1)) {
@@ -47,9 +54,18 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* _
       if (!row_tiles(b, ty, V.tiles_x, &tx_a, &tx_b)) continue;
       const uint32_t base = (uint32_t)(V.tile_base + ty * V.tiles_x);
       for (int tx = tx_a; tx <= tx_b; ++tx) {
-        if (written < cnt) {
-          keys[off + written] = base + (uint32_t)tx;
+        const uint32_t key = base + (uint32_t)tx;
+        if (written < head || (written >= groups_end && written < cnt)) {
+          keys[off + written] = key;
           vals[off + written] = item;
+        } else if (written < groups_end) {
+          const uint32_t g = (written - head) & 3u;
+          buf[g] = key;
+          if (g == 3u) {
+            const uint32_t at = off + written - 3u;     // 4-aligned
+            *reinterpret_cast<uint4*>(keys + at) = make_uint4(buf[0], buf[1], buf[2], buf[3]);
+            *reinterpret_cast<uint4*>(vals + at) = vals4;
+          }
         }
         ++written;
       }

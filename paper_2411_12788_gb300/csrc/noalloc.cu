@@ -72,6 +72,7 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_plan* plan, void* pre_ws, uint
   if (!plan || plan->n_views < 1 || plan->n_views > GS_MAX_VIEWS || plan->n_entries < 0 || !pre_ws || !ranges)
     return GS_ERR_INVALID_ARG;
   if (plan->n_entries > 0 && (!tile_ids || !items)) return GS_ERR_INVALID_ARG;
+  if ((reinterpret_cast<uintptr_t>(tile_ids) | reinterpret_cast<uintptr_t>(items)) & 15) return GS_ERR_INVALID_ARG;
   if (plan->n_entries > kMaxEntries) return GS_ERR_CAPACITY;
   if (plan->sort_bits < 1 || plan->sort_bits > 32) return GS_ERR_INVALID_ARG;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
