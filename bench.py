@@ -30,7 +30,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "fwd+bwd Mpix/s and steps/s at 1M Gaussians; serving p50/p99 ms vs one-at-a-time"
 WORKLOAD = ("batched fwd+bwd, 1M Gaussians SH3 (64-cluster + shell scene), 8 views "
-            "2x800x800 + 3x1280x720 + 2x1600x1063 + 1x1920x1080, L1 loss")
+            "2x800x800 + 3x1280x720 + 2x1600x1063 + 1x1920x1080, L1 loss; emits colour, d^mid depth, "
+            "i_max and per-Gaussian accumulated blending weight")
 
 
 def parse():
@@ -149,11 +150,15 @@ class Step:
         self.cfg = raster.make_config(flags=raster._lib.GS_FLAG_ZERO_ACCUM)
         self.pre_ws = torch.empty(raster.preprocess_workspace_size(self.plan), dtype=torch.uint8, device="cuda")
         self.sort_ws = torch.empty(0, dtype=torch.uint8, device="cuda")
+        # the step emits colour, depth, i_max (forward) and the accumulated
+        # blending weight I_i, which the backward pass collects as it replays
+        # every blended entry
         self.outs = raster.alloc_outputs(self.plan, "cuda", want=("image", "final_T", "n_contrib", "depth",
-                                                                  "imax", "weight_sum"))
+                                                                  "imax"))
         self.loss = torch.zeros(1, device="cuda")
         self.dL = torch.empty_like(self.outs["image"])
         self.grads = raster.alloc_grads(self.g)
+        self.grads["weight_sum"] = torch.zeros(int(self.plan.n_items), device="cuda")
         self.pixels = int(self.plan.total_pixels)
 
     def run(self):

@@ -131,7 +131,10 @@ typedef struct gs_fwd_outputs {
 /* Gradients, device, ACCUMULATED (+=) over views, same layouts as gs_scene;
  * d_sh has sh_coeffs columns (unused ones are left untouched).
  * d_mean2d_abs (nullable, [n]) += |dL/d mean2d| per view (3DGS densification
- * statistic). */
+ * statistic).  weight_sum (nullable, [n_items]) += the accumulated blending
+ * weight I_i of Sec. 3.2, the same quantity as gs_fwd_outputs.weight_sum,
+ * collected during the backward pass: a training step can take I_i from here
+ * and skip it in the forward pass. */
 typedef struct gs_grads {
   float* d_means;
   float* d_scales;
@@ -139,6 +142,7 @@ typedef struct gs_grads {
   float* d_opacities;
   float* d_sh;
   float* d_mean2d_abs;
+  float* weight_sum;
 } gs_grads;
 
 /* ---- plan and sizes (host only) ------------------------------------- */

@@ -65,7 +65,8 @@ class FwdOutputs(C.Structure):
 
 class Grads(C.Structure):
     _fields_ = [("d_means", C.c_void_p), ("d_scales", C.c_void_p), ("d_rotations", C.c_void_p),
-                ("d_opacities", C.c_void_p), ("d_sh", C.c_void_p), ("d_mean2d_abs", C.c_void_p)]
+                ("d_opacities", C.c_void_p), ("d_sh", C.c_void_p), ("d_mean2d_abs", C.c_void_p),
+                ("weight_sum", C.c_void_p)]
 
 
 class PreprocessView(C.Structure):

@@ -304,13 +304,14 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_opacities, 0, 4 * (size_t)n, stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(g->d_sh, 0, 12 * (size_t)n * scene->sh_coeffs, stream);
     if (e == cudaSuccess && g->d_mean2d_abs) e = cudaMemsetAsync(g->d_mean2d_abs, 0, 4 * (size_t)n, stream);
+    if (e == cudaSuccess && g->weight_sum) e = cudaMemsetAsync(g->weight_sum, 0, 4 * (size_t)plan->n_items, stream);
   }
   if (e != cudaSuccess) return GS_ERR_CUDA;
   const ItemState st = item_state(pre_ws, L);
   float4* grad2d = at<float4>(pre_ws, L.grad2d);
   e = launch_render_bwd(at<ViewDev>(pre_ws, L.views), plan->n_views, n, plan->total_tiles,
                         at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals), st, *cfg, dL_dimage, image,
-                        n_contrib, grad2d, stream);
+                        n_contrib, grad2d, g->weight_sum, stream);
   if (e == cudaSuccess)
     e = launch_preprocess_backward(*scene, at<ViewDev>(pre_ws, L.views), plan->n_views, *cfg, st.tiles, grad2d, *g,
                                    stream);

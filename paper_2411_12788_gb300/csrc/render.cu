@@ -246,6 +246,7 @@ struct BwdIn {
   const float* image;           // forward output c(x) + T_final bg
   const uint32_t* n_contrib;
   float4* grad2d;               // 3 x float4 per item
+  float* weight_sum;            // optional: += I_i per item
 };
 
 // Backward of Eq. 1, one lane per entry.  For pixel x with blended entries
@@ -271,6 +272,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
   __shared__ float4 s_rgb[kRenderThreads];
   __shared__ uint32_t s_item[kRenderThreads];
   __shared__ float s_g[9][kRenderThreads];
+  __shared__ float s_wsum[kRenderThreads];     // I_i of the batch's entries (optional output)
   // per-pixel state, indexed by the pixel's thread id (warp w owns 32w..32w+31)
   __shared__ float4 s_pg[kRenderThreads];     // dL/dI (r, g, b) and I . dL/dI
   __shared__ float s_T[kRenderThreads];       // transmittance before the next chunk
@@ -315,6 +317,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
   }
 #pragma unroll
   for (int k = 0; k < 9; ++k) s_g[k][tid] = 0.f;
+  s_wsum[tid] = 0.f;
   __syncthreads();
   const uint32_t max_nc = s_max_nc;
   const uint32_t warp_nc = s_warp_nc[warp];
@@ -345,11 +348,13 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
       const uint32_t pos = c0 + lane;
       const float dx0 = bxf - m.x, dy0 = byf - m.y;
       float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+      float wsum = 0.f;                             // this entry's blending weight over the warp's pixels
       // pixels of this warp that are still blending at this chunk
-      uint32_t pmask = __ballot_sync(0xffffffffu, s_nc[warp * 32 + lane] > c0);
-      while (pmask) {
-        const int p = __ffs(pmask) - 1;
-        pmask &= pmask - 1;
+      const uint32_t pmask = __ballot_sync(0xffffffffu, s_nc[warp * 32 + lane] > c0);
+      const float a2x2 = 2.f * ex.x, c2x2 = 2.f * ex.z;
+#pragma unroll
+      for (int p = 0; p < 32; ++p) {
+        if (!(pmask & (1u << p))) continue;
         const int pt = warp * 32 + p;                 // the pixel's thread id
         const uint32_t nc = s_nc[pt];
         const float dx = dx0 + (float)(p & 7), dy = dy0 + (float)(p >> 3);
@@ -369,7 +374,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
         if (lane == 0) mex = 1.f;
         const float Tl = T0 * mex;
         const float w = a * Tl;
-        const float Fl = F0 + T0 * f;                      // sum_{k<=l} w_k cg_k
+        const float Fl = fmaf(T0, f, F0);                  // sum_{k<=l} w_k cg_k
         // lane 31 holds the chunk's totals: carry the pixel's state forward
         __syncwarp();
         if (lane == 31) {
@@ -377,19 +382,21 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
           s_F[pt] = Fl;
         }
         if (act) {
-          acc[6] += w * pg.x;
-          acc[7] += w * pg.y;
-          acc[8] += w * pg.z;
+          wsum += w;
+          acc[6] = fmaf(w, pg.x, acc[6]);
+          acc[7] = fmaf(w, pg.y, acc[7]);
+          acc[8] = fmaf(w, pg.z, acc[8]);
           if (araw <= P.alpha_max) {
-            const float dal = Tl * cg - (pg.w - Fl) * rcp_approx(1.f - a);
+            const float dal = fmaf(Tl, cg, -(pg.w - Fl) * rcp_approx(1.f - a));
             const float de = dal * a * kLn2;          // dL/de
+            const float dedx = de * dx, dedy = de * dy;
             acc[5] += de;                             // d log2 o
-            acc[2] += de * dx * dx;                   // d a2
-            acc[3] += de * dx * dy;                   // d b2
-            acc[4] += de * dy * dy;                   // d c2
+            acc[2] = fmaf(dedx, dx, acc[2]);          // d a2
+            acc[3] = fmaf(dedx, dy, acc[3]);          // d b2
+            acc[4] = fmaf(dedy, dy, acc[4]);          // d c2
             // d = pixel - centre: de/dcentre = -(2 a2 dx + b2 dy, b2 dx + 2 c2 dy)
-            acc[0] -= de * (2.f * ex.x * dx + ex.y * dy);
-            acc[1] -= de * (ex.y * dx + 2.f * ex.z * dy);
+            acc[0] = fmaf(-a2x2, dedx, fmaf(-ex.y, dedy, acc[0]));
+            acc[1] = fmaf(-ex.y, dedx, fmaf(-c2x2, dedy, acc[1]));
           }
         }
       }
@@ -397,6 +404,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
 #pragma unroll
         for (int k = 0; k < 9; ++k)
           if (acc[k] != 0.f) atomicAdd(&s_g[k][e_idx], acc[k]);
+        if (B.weight_sum && wsum != 0.f) atomicAdd(&s_wsum[e_idx], wsum);
       }
     }
     __syncthreads();
@@ -414,6 +422,11 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
       if (v[4] != 0.f || v[5] != 0.f || v[6] != 0.f || v[7] != 0.f)
         atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
       if (v[8] != 0.f) atomicAdd(&dst[2].x, v[8]);
+      if (B.weight_sum) {
+        const float ws = s_wsum[tid];
+        s_wsum[tid] = 0.f;
+        if (ws != 0.f) atomicAdd(&B.weight_sum[item], ws);
+      }
     }
     __syncthreads();
   }
@@ -456,9 +469,9 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
 cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
                               const uint32_t* vals, const ItemState& st, const gs_config& cfg,
                               const float* dL_dimage, const float* image, const uint32_t* n_contrib,
-                              float4* grad2d, cudaStream_t stream) {
+                              float4* grad2d, float* weight_sum, cudaStream_t stream) {
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
-  BwdIn B{dL_dimage, image, n_contrib, grad2d};
+  BwdIn B{dL_dimage, image, n_contrib, grad2d, weight_sum};
   if (total_tiles > 0)
     GS_TIMED("render_bwd", stream, (render_bwd_kernel<<<total_tiles, kRenderThreads, 0, stream>>>(P, B)));
   return cudaGetLastError();

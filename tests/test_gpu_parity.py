@@ -270,6 +270,23 @@ def test_backward_matches_oracle(deg, seed):
         _assert_grad_close(name, gg, r, keep)
 
 
+def test_backward_collects_the_forward_weight_sums():
+    """I_i collected by the backward pass equals the forward's I_i."""
+    _need_gpu()
+    sc, cams = SCENES["box512_deg3_multiview"]()
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, cams)
+    grads = raster.alloc_grads(g)
+    grads["weight_sum"] = torch.zeros(int(fr.plan.n_items), device="cuda")
+    dL = torch.rand_like(fr.outs["image"]) - 0.5
+    raster.render_bwd(fr.plan, g.struct(), fr.cfg, fr.pre_ws, fr.sort_ws, dL, fr.outs["image"],
+                      fr.outs["n_contrib"], grads)
+    a = grads["weight_sum"].double().cpu()
+    b = fr.outs["weight_sum"].double().cpu()
+    assert b.max() > 1.0
+    assert torch.all((a - b).abs() <= 1e-4 + 1e-5 * b.abs())
+
+
 def test_autograd_function_and_recompute():
     """The torch.autograd.Function gives the same gradients whether the sorted
     lists are kept or rebuilt in backward."""
