@@ -296,119 +296,78 @@ def run_ours(args, rank, world):
 
 
 def run_e2e(st: Step, args, world) -> dict:
-    """Same step with host buffers: H2D of the scene and targets from pinned
-    memory, the step, D2H of the loss and the gradients, every step."""
+    """The same step with host buffers: every step copies its scene and target
+    images in from pinned host memory and its loss and gradients (and I_i)
+    back out.  The copies run on a second stream with two device buffer sets,
+    so step k+1's upload and step k's download overlap step k's compute; all
+    of them are inside the timed region."""
     import torch
+    from paper_2411_12788_gb300 import raster
     names = ("means", "scales", "rotations", "opacities", "sh")
     host_in = {k: getattr(st.g, k).cpu().pin_memory() for k in names}
     host_tg = st.target.cpu().pin_memory()
-    host_out = {k: v.cpu().pin_memory() for k, v in st.grads.items()}
-    host_loss = torch.zeros(1).pin_memory()
+    sets = []
+    for b in range(2):
+        g = st.g if b == 0 else raster.GaussianTensors(*(getattr(st.g, k).clone() for k in names), st.g.sh_degree)
+        tg = st.target if b == 0 else st.target.clone()
+        gr = st.grads if b == 0 else {k: v.clone() for k, v in st.grads.items()}
+        loss = st.loss if b == 0 else st.loss.clone()
+        out = {k: v.cpu().pin_memory() for k, v in gr.items()}
+        sets.append({"g": g, "target": tg, "grads": gr, "loss": loss, "host_out": out,
+                     "host_loss": torch.zeros(1).pin_memory()})
     h2d = sum(t.numel() * 4 for t in host_in.values()) + host_tg.numel() * 4
-    d2h = sum(t.numel() * 4 for t in host_out.values()) + 4
+    d2h = sum(t.numel() * 4 for t in sets[0]["host_out"].values()) + 4
+    compute = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
+    ready = [torch.cuda.Event(), torch.cuda.Event()]
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+    orig = (st.g, st.target, st.grads, st.loss)
 
-    def step():
-        for k in names:
-            getattr(st.g, k).copy_(host_in[k], non_blocking=True)
-        st.target.copy_(host_tg, non_blocking=True)
+    def upload(b):
+        with torch.cuda.stream(copy):
+            copy.wait_event(done[b])                 # the step that last read set b is finished
+            for k in names:
+                getattr(sets[b]["g"], k).copy_(host_in[k], non_blocking=True)
+            sets[b]["target"].copy_(host_tg, non_blocking=True)
+            ready[b].record(copy)
+
+    def run(k):
+        b = k % 2
+        compute.wait_event(ready[b])
+        st.g, st.target, st.grads, st.loss = sets[b]["g"], sets[b]["target"], sets[b]["grads"], sets[b]["loss"]
         st.run()
-        for k, v in st.grads.items():
-            host_out[k].copy_(v, non_blocking=True)
-        host_loss.copy_(st.loss, non_blocking=True)
+        done[b].record(compute)
+        with torch.cuda.stream(copy):
+            copy.wait_event(done[b])
+            for key, v in sets[b]["grads"].items():
+                sets[b]["host_out"][key].copy_(v, non_blocking=True)
+            sets[b]["host_loss"].copy_(sets[b]["loss"], non_blocking=True)
 
-    for _ in range(2):
-        step()
+    def steps(n):
+        upload(0)
+        upload(1)
+        for k in range(n):
+            run(k)
+            if k + 2 < n:
+                upload(k % 2)                       # inputs of step k+2 go into the set step k used
+        compute.wait_stream(copy)                   # the last downloads are part of the run
+
+    steps(3)
     torch.cuda.synchronize()
     barrier(world)
-    stream = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        step()
-    e1.record(stream)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(compute)
+    steps(args.steps)
+    t1.record(compute)
     torch.cuda.synchronize()
     barrier(world)
-    sec = e0.elapsed_time(e1) / 1e3
+    st.g, st.target, st.grads, st.loss = orig
+    sec = t0.elapsed_time(t1) / 1e3
     units, sec_max = aggregate(st.pixels * args.steps, sec, world)
     return {"value": units / sec_max / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "ms_per_step": sec_max * 1e3 / args.steps}
-
-
-def run_serving(st: Step, args) -> dict:
-    """Serving loop on the resident 1M scene: Poisson arrivals at 200 req/s
-    (seed 3), poses on a sphere of radius U[3, 6], resolutions uniform over
-    640x480 / 1280x720 / 1920x1080 / 3840x2160, 24 GB admission budget; the
-    first 10 % of requests are warm-up.  Batched (3 stream slots, up to 16
-    views per batch) against the same trace served one request at a time."""
-    import torch
-    from paper_2411_12788_gb300 import serve
-    n = args.serve_requests
-    skip = n // 11
-    out = {"rate_per_s": 200.0, "requests_timed": n - skip, "warmup_requests": skip, "budget_gb": 24,
-           "scene_gaussians": st.g.n}
-    for name, streams, views in (("batched", 3, 16), ("one_at_a_time", 1, 1)):
-        trace = serve.poisson_trace(n, rate=200.0, seed=3)
-        srv = serve.RenderServer(st.g, budget_bytes=24 << 30, streams=streams, max_views=views)
-        srv.serve(trace)
-        stats = serve.latency_stats(trace, skip=skip)
-        stats.update({"streams": streams, "max_views": views, "batches": srv.batches_run,
-                      "mean_views_per_batch": srv.views_run / max(1, srv.batches_run),
-                      "peak_reserved_gb": srv.peak_reserved / 2**30})
-        out[name] = stats
-        torch.cuda.synchronize()
-    out["p99_speedup"] = out["one_at_a_time"]["p99_ms"] / out["batched"]["p99_ms"]
-    return out
-
-
-def run_dense(args, iters: int = 3) -> dict:
-    """Dense-phase step (MSv2-D): 3M Gaussians (256 clusters, SH 3), one
-    1920x1080 view: fwd+bwd with L1, keep the top 25 % by accumulated weight,
-    gather them and re-render the sparse set."""
-    import torch
-    from paper_2411_12788_gb300 import raster, scenes
-    sc = scenes.cluster_scene(3_000_000, 256, seed=0, sh_degree=3)
-    cam = scenes.ring_camera(0.3, 1920, 1080)
-    g = raster.GaussianTensors.from_scene(sc, "cuda")
-    target = torch.as_tensor(scenes.target_images([cam], seed=1)[0].reshape(-1)).cuda()
-    cfg = raster.make_config(flags=raster._lib.GS_FLAG_ZERO_ACCUM)
-    k = math.ceil(0.25 * sc.n)
-    loss = torch.zeros(1, device="cuda")
-    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
-    times = {"fwd_bwd": 0.0, "prune_gather": 0.0, "rerender": 0.0}
-
-    def once(record):
-        s = torch.cuda.current_stream()
-        if record:
-            ev[0].record(s)
-        fr = raster.forward(g, [cam], cfg)
-        dL = torch.empty_like(fr.outs["image"])
-        raster.loss_l1(fr.outs["image"], target, loss, dL)
-        raster.backward(g, fr, dL)
-        if record:
-            ev[1].record(s)
-        keep = raster.prune_select(fr.outs["weight_sum"], k)
-        h = raster.gather_scene(g, keep)
-        if record:
-            ev[2].record(s)
-        fr2 = raster.forward(h, [cam], cfg)
-        if record:
-            ev[3].record(s)
-            torch.cuda.synchronize()
-            times["fwd_bwd"] += ev[0].elapsed_time(ev[1])
-            times["prune_gather"] += ev[1].elapsed_time(ev[2])
-            times["rerender"] += ev[2].elapsed_time(ev[3])
-        return fr, fr2
-    once(False)
-    torch.cuda.synchronize()
-    for _ in range(iters):
-        fr, fr2 = once(True)
-    ms = {k2: v / iters for k2, v in times.items()}
-    total = sum(ms.values())
-    pix = cam.width * cam.height
-    return {"workload": "3M Gaussians SH3 (256 clusters), 1920x1080: fwd+bwd, top-25% prune, re-render",
-            "ms": ms, "ms_total": total, "kept": k, "entries": int(fr.plan.n_entries),
-            "entries_after_prune": int(fr2.plan.n_entries), "mpix_per_s": 2 * pix / total / 1e3,
-            "note": "each phase allocates its workspaces from the torch caching allocator"}
+            "d2h_bytes_per_step": d2h, "ms_per_step": sec_max * 1e3 / args.steps,
+            "overlap": "double-buffered: uploads and downloads on a copy stream overlap the previous/next step"}
 
 
 # ---------------------------------------------------------------- oracle arm

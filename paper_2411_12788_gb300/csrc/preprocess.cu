@@ -38,12 +38,12 @@ struct PreParams {
 
 // Stage the first K coefficients (3 floats each) of this block's SH rows into
 // shared memory with row stride 3K+1 (odd: conflict-free per-thread reads).
-template <int K>
+template <int K, int THREADS>
 __device__ __forceinline__ void stage_sh(const float* __restrict__ sh, int sh_coeffs, int64_t i0, int64_t n,
                                          float* s_sh) {
   constexpr int per = 3 * K, row = 3 * K + 1;
-  const int64_t rows = (n - i0 < kPreThreads) ? (n - i0) : (int64_t)kPreThreads;
-  for (int f = threadIdx.x; f < rows * per; f += kPreThreads) {
+  const int64_t rows = (n - i0 < THREADS) ? (n - i0) : (int64_t)THREADS;
+  for (int f = threadIdx.x; f < rows * per; f += THREADS) {
     const int g = f / per, c = f - g * per;
     s_sh[g * row + c] = sh[(i0 + g) * (int64_t)sh_coeffs * 3 + c];
   }
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
   __shared__ float s_sh[kPreThreads * row];
   const int64_t i0 = (int64_t)blockIdx.x * kPreThreads;
   const int64_t i = i0 + threadIdx.x;
-  stage_sh<K>(P.sh, P.sh_coeffs, i0, P.n, s_sh);
+  stage_sh<K, kPreThreads>(P.sh, P.sh_coeffs, i0, P.n, s_sh);
   __syncthreads();
   if (i >= P.n) return;
 
@@ -75,13 +75,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
   const float M[9] = {Rq[0] * s0, Rq[1] * s1, Rq[2] * s2, Rq[3] * s0, Rq[4] * s1, Rq[5] * s2,
                       Rq[6] * s0, Rq[7] * s1, Rq[8] * s2};
   const float tau = 2.f * logf(o / P.alpha_min);
-  float shc[K][3];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-    shc[k][0] = s_sh[threadIdx.x * row + 3 * k];
-    shc[k][1] = s_sh[threadIdx.x * row + 3 * k + 1];
-    shc[k][2] = s_sh[threadIdx.x * row + 3 * k + 2];
-  }
+  const float* shc = s_sh + threadIdx.x * row;     // coefficient k, channel c at [3k + c]
   const float lp = P.lowpass;
 
   for (int v = 0; v < P.n_views; ++v) {
@@ -169,9 +163,9 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
     float r = 0.5f, g = 0.5f, bl = 0.5f;
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      r += Y[k] * shc[k][0];
-      g += Y[k] * shc[k][1];
-      bl += Y[k] * shc[k][2];
+      r += Y[k] * shc[3 * k];
+      g += Y[k] * shc[3 * k + 1];
+      bl += Y[k] * shc[3 * k + 2];
     }
     P.st.rgb[item] = make_float4(fmaxf(r, 0.f), fmaxf(g, 0.f), fmaxf(bl, 0.f), 0.f);
 
@@ -224,25 +218,25 @@ struct PreBwdParams {
   float* d_mean2d_abs;
 };
 
+constexpr int kPreBwdThreads = 64;
+
+// One thread per Gaussian; its SH row and the row's gradient live in shared
+// memory (per-thread rows, odd stride) rather than in registers, which keeps
+// the kernel near 90 registers and several blocks per SM.
 template <int DEG>
-__global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(PreBwdParams P) {
+__global__ void __launch_bounds__(kPreBwdThreads) preprocess_backward_kernel(PreBwdParams P) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int row = 3 * K + 1;
-  __shared__ float s_sh[kPreThreads * row];
-  const int64_t i0 = (int64_t)blockIdx.x * kPreThreads;
+  __shared__ float s_sh[kPreBwdThreads * row];
+  __shared__ float s_dsh[kPreBwdThreads * row];
+  const int64_t i0 = (int64_t)blockIdx.x * kPreBwdThreads;
   const int64_t i = i0 + threadIdx.x;
-  stage_sh<K>(P.sh, P.sh_coeffs, i0, P.n, s_sh);
+  stage_sh<K, kPreBwdThreads>(P.sh, P.sh_coeffs, i0, P.n, s_sh);
+  for (int f = threadIdx.x; f < kPreBwdThreads * row; f += kPreBwdThreads) s_dsh[f] = 0.f;
   __syncthreads();
   const bool live = i < P.n;
-  float shc[K][3], dsh[K][3];
-#pragma unroll
-  for (int k = 0; k < K; ++k) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      shc[k][c] = s_sh[threadIdx.x * row + 3 * k + c];
-      dsh[k][c] = 0.f;
-    }
-  }
+  const float* shc = s_sh + threadIdx.x * row;      // coefficient k, channel c at [3k + c]
+  float* dsh = s_dsh + threadIdx.x * row;
   bool any = false;
   float dp[3] = {0.f, 0.f, 0.f};
   float dSig[6] = {0, 0, 0, 0, 0, 0};       // symmetric dL/dSigma (00,01,02,11,12,22)
@@ -373,19 +367,19 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(PreBwd
     float raw[3] = {0.5f, 0.5f, 0.5f};
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      raw[0] += Y[k] * shc[k][0];
-      raw[1] += Y[k] * shc[k][1];
-      raw[2] += Y[k] * shc[k][2];
+      raw[0] += Y[k] * shc[3 * k];
+      raw[1] += Y[k] * shc[3 * k + 1];
+      raw[2] += Y[k] * shc[3 * k + 2];
     }
     const float dr[3] = {raw[0] >= 0.f ? drgb[0] : 0.f, raw[1] >= 0.f ? drgb[1] : 0.f,
                          raw[2] >= 0.f ? drgb[2] : 0.f};
     float cdot[16];
 #pragma unroll
     for (int k = 0; k < K; ++k) {
-      dsh[k][0] += Y[k] * dr[0];
-      dsh[k][1] += Y[k] * dr[1];
-      dsh[k][2] += Y[k] * dr[2];
-      cdot[k] = shc[k][0] * dr[0] + shc[k][1] * dr[1] + shc[k][2] * dr[2];
+      dsh[3 * k] += Y[k] * dr[0];
+      dsh[3 * k + 1] += Y[k] * dr[1];
+      dsh[3 * k + 2] += Y[k] * dr[2];
+      cdot[k] = shc[3 * k] * dr[0] + shc[3 * k + 1] * dr[1] + shc[3 * k + 2] * dr[2];
     }
     if (DEG > 0) {
       float gdir[3] = {0.f, 0.f, 0.f};
@@ -397,20 +391,14 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_backward_kernel(PreBwd
     }
   }
 
-  // SH gradients: staged back through shared memory, then added to the
-  // block's rows with coalesced read-modify-writes
-  __syncthreads();
-#pragma unroll
-  for (int k = 0; k < K; ++k)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) s_sh[threadIdx.x * row + 3 * k + c] = dsh[k][c];
+  // SH gradients: added to the block's rows with coalesced read-modify-writes
   __syncthreads();
   {
     constexpr int per = 3 * K;
-    const int64_t rows = (P.n - i0 < kPreThreads) ? (P.n - i0) : (int64_t)kPreThreads;
-    for (int f = threadIdx.x; f < rows * per; f += kPreThreads) {
+    const int64_t rows = (P.n - i0 < kPreBwdThreads) ? (P.n - i0) : (int64_t)kPreBwdThreads;
+    for (int f = threadIdx.x; f < rows * per; f += kPreBwdThreads) {
       const int g = f / per, c = f - g * per;
-      const float v = s_sh[g * row + c];
+      const float v = s_dsh[g * row + c];
       if (v != 0.f) P.d_sh[(i0 + g) * (int64_t)P.sh_coeffs * 3 + c] += v;
     }
   }
@@ -514,20 +502,20 @@ cudaError_t launch_preprocess_backward(const gs_scene& sc, const ViewDev* views,
   P.d_opac = gr.d_opacities;
   P.d_sh = gr.d_sh;
   P.d_mean2d_abs = gr.d_mean2d_abs;
-  const int blocks = ceil_div(sc.n, kPreThreads);
+  const int blocks = ceil_div(sc.n, kPreBwdThreads);
   if (blocks == 0) return cudaSuccess;
   switch (sc.sh_degree) {
     case 0:
-      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<0><<<blocks, kPreThreads, 0, stream>>>(P)));
+      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<0><<<blocks, kPreBwdThreads, 0, stream>>>(P)));
       break;
     case 1:
-      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<1><<<blocks, kPreThreads, 0, stream>>>(P)));
+      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<1><<<blocks, kPreBwdThreads, 0, stream>>>(P)));
       break;
     case 2:
-      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<2><<<blocks, kPreThreads, 0, stream>>>(P)));
+      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<2><<<blocks, kPreBwdThreads, 0, stream>>>(P)));
       break;
     default:
-      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<3><<<blocks, kPreThreads, 0, stream>>>(P)));
+      GS_TIMED("preprocess_backward", stream, (preprocess_backward_kernel<3><<<blocks, kPreBwdThreads, 0, stream>>>(P)));
       break;
   }
   return cudaGetLastError();
