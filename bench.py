@@ -225,12 +225,14 @@ def roofline(kt: dict, st: "Step", steps: int, peaks: dict, clocks: dict) -> dic
 
 
 FP32_LANES = 152 * 128
-# FP32 operations per (pixel, entry) evaluation, counted from the inner loops
-# (an FMA counts 2): forward ~ q (5 FMA) + exp (2) + alpha (2) + T (2) +
-# blend of colour, depth, weight (10) + compares;  backward adds the reverse
-# transmittance, the colour recursion and the nine gradient terms.
-FWD_FLOPS_PER_EVAL = 30
-BWD_FLOPS_PER_EVAL = 80
+# FP32 floating-point operations (an FMA counts 2) per (pixel, entry)
+# evaluation of a blended entry, counted from the arithmetic the kernels do:
+# forward: offsets 2, exponent 8, alpha 2, transmittance 2, weight 1,
+# colour 6, depth 2, argmax 1 = 24; backward: offsets 2, exponent 8, alpha 2,
+# c.g 5, affine scan 15, T/w/F 5, colour gradient 6, dL/dalpha 6, dL/de 2,
+# conic and centre terms 15 = 66.  MUFU work (ex2, rcp) is not counted.
+FWD_FLOPS_PER_EVAL = 24
+BWD_FLOPS_PER_EVAL = 66
 
 
 def run_ours(args, rank, world):
