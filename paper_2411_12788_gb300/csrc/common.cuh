@@ -36,7 +36,7 @@ struct ViewDev {
 struct ItemState {
   float4* xy_tau_z;          // (mean2d.x, mean2d.y, tau, z)
   float4* conic_o;           // (A, B, C, opacity); q = A dx^2 + 2B dx dy + C dy^2
-  float4* rgb;               // (r, g, b, 0)
+  float4* rgb;               // (r, g, b, support half-extents as two halves; see pack_extent)
   float4* depth_frame;       // 3 x float4 per item: rows of W = diag(1/s) (R Rq)^T, then e = W p_c
   uint2* rect;               // (tx0 | ty0 << 16, tx1 | ty1 << 16), inclusive bounding box
   float4* bin;               // 2 x float4 per item: (k, sc, 1/Syy, h), (rx, ys, 0, 0); see BinParams

@@ -143,6 +143,10 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
         if (row_tiles(b, ty, V.tiles_x, &a, &c)) count += (uint32_t)(c - a + 1);
       }
     }
+    // condition number of the 2-D covariance (for the culling boxes)
+    const float hd = 0.5f * (cxx - cyy);
+    const float lmax = 0.5f * (cxx + cyy) + sqrtf(hd * hd + cxy * cxy);
+    const float kappa = lmax * lmax / det;
     P.st.tiles[item] = count;
     P.st.depth_key[item] = count ? __float_as_uint(pc.z) : kCulledKey;
     if (!count) continue;
@@ -167,7 +171,8 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
       g += Y[k] * shc[3 * k + 1];
       bl += Y[k] * shc[3 * k + 2];
     }
-    P.st.rgb[item] = make_float4(fmaxf(r, 0.f), fmaxf(g, 0.f), fmaxf(bl, 0.f), 0.f);
+    P.st.rgb[item] = make_float4(fmaxf(r, 0.f), fmaxf(g, 0.f), fmaxf(bl, 0.f), 
+                                 pack_extent(support_extent(b.rx, cxx, kappa), support_extent(b.h, cyy, kappa)));
 
     // midpoint-depth frame: W = diag(1/s) (R Rq)^T maps camera offsets to the
     // unit-sphere frame of the ellipsoid x^2/sx^2 + y^2/sy^2 + z^2/sz^2 = 1

@@ -4,6 +4,8 @@
 // kernels so that every call site evaluates bit-identical arithmetic.
 #pragma once
 
+#include <cuda_fp16.h>
+
 #include "common.cuh"
 
 namespace gs {
@@ -161,6 +163,37 @@ __device__ __forceinline__ bool tile_rows(const BinParams& b, int tiles_y, int* 
   *ty0 = (int)fmaxf(f0, 0.f);
   *ty1 = (int)fminf(f1, (float)(tiles_y - 1));
   return *ty0 <= *ty1;
+}
+
+// Support half-extents of an item for the backward kernel's per-block
+// culling, packed as two halves in the colour's fourth component.
+//
+// The render kernels decide membership pixel by pixel with the FP32 exponent
+// e = log2 o + a2 dx^2 + b2 dx dy + c2 dy^2 >= log2(alpha_min), whose rounding
+// error is bounded by a few ulp times S = |A| dx^2 + 2|B||dx dy| + |C| dy^2,
+// plus an absolute part from log2 o and the threshold.  For the 2-D
+// covariance S2 with eigenvalues l_max >= l_min and kappa = l_max / l_min,
+// S <= 4 kappa q, while outside the box [-f rx, f rx] (rx = sqrt(tau Sxx))
+// q >= f^2 tau.  The relative error of q is at most about 3e-6 kappa (a few
+// roundings of the evaluation and of the conic), so with f = 1.02 + 4e-6 kappa
+// no pixel outside the box passes while f^2 (1 - 3e-6 kappa) > 1, which holds
+// up to kappa = 2e5 (an axis ratio of about 450, where the FP32 exponent has
+// lost most of its digits near the support edge anyway).  The term
+// 2e-3 sqrt(Sxx) covers the absolute part (q error up to 4e-6) and 0.5 px more
+// the rounding of the box ends.  The result is rounded up to half precision,
+// so the box contains every pixel whose exponent test can pass.
+__device__ __forceinline__ float support_extent(float r, float s_diag, float kappa) {
+  return fmaf(fmaf(4e-6f, kappa, 1.02f), r, fmaf(2e-3f, sqrtf(s_diag), 0.5f));
+}
+
+__device__ __forceinline__ float pack_extent(float ex, float ey) {
+  const __half2 h = __halves2half2(__float2half_ru(ex), __float2half_ru(ey));
+  return __uint_as_float(*reinterpret_cast<const uint32_t*>(&h));
+}
+
+__device__ __forceinline__ float2 unpack_extent(float packed) {
+  const uint32_t u = __float_as_uint(packed);
+  return __half22float2(*reinterpret_cast<const __half2*>(&u));
 }
 
 }  // namespace gs

@@ -1,8 +1,9 @@
 // Per-tile front-to-back alpha blending (Eq. 1) and its derivative.
 //
-// One CTA of 256 threads per 16x16 tile; each warp owns an 8x4 block of the
-// tile.  The tile's depth-ordered list is streamed through shared memory in
-// batches of 256 entries, gathered by item id.  Per entry the batch holds its
+// One CTA per 16x16 tile (128 threads forward, 256 backward); pixels are
+// grouped in 8x4 blocks, one per warp.  The tile's depth-ordered list is
+// streamed through shared memory in batches of 256 entries, gathered by item
+// id.  Per entry the batch holds its
 // centre, colour, depth and the 2-D Gaussian in exponent form:
 //   alpha_raw(x) = o exp(-q/2) = 2^e,  e = log2 o + a2 dx^2 + b2 dx dy + c2 dy^2
 // with (a2, b2, c2) = -log2(e) (A/2, B, C/2) for the conic (A, B, C).  An entry
@@ -10,7 +11,7 @@
 // then alpha = min(alpha_max, 2^e).  Forward and backward evaluate e with the
 // same explicitly rounded operations, so they make identical decisions.
 //
-// Forward (one thread per pixel): front-to-back blending with a per-pixel
+// Forward (one thread per two pixels): front-to-back blending with a per-pixel
 // stop before T (1 - alpha) < t_min, the CTA leaving the list once all its
 // pixels stopped.  Side outputs (what the paper's reorganisation reads):
 // i_max = argmax_i w_i and w_max, the midpoint depth d^mid_{i_max} (Eq. 2,
@@ -21,8 +22,9 @@
 // (tile, entry)) and the maximum-contribution area S_i (Sec. 4.1;
 // warp-aggregated atomics).
 //
-// Backward: one lane per entry, a warp walking its pixels with lane scans
-// for the transmittance and the colour in front (see render_bwd_kernel);
+// Backward: two entries per lane, a warp walking its pixels with lane scans
+// for the transmittance and the colour in front, over the entries whose
+// support box meets its 8x4 block (see render_bwd_kernel);
 // gradients accumulate in registers, are combined across the CTA's warps in
 // shared memory and added to the per-item buffer with one vector atomic per
 // (tile, entry).  They are taken with respect to (centre, a2, b2, c2,
@@ -122,108 +124,66 @@ __device__ __forceinline__ void pixel_of(const ViewDev& V, int tile, int t, int*
   *py = ty * kTile + (warp >> 1) * 4 + (lane >> 3);
 }
 
-__global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(RenderParams P, FwdOut O) {
-  __shared__ int s_view;
-  __shared__ float2 s_xy[kRenderThreads];
-  __shared__ float4 s_ex[kRenderThreads];
-  __shared__ float4 s_rgbz[kRenderThreads];
-  __shared__ uint32_t s_item[kRenderThreads];
-  __shared__ uint32_t s_wsum[kRenderThreads];    // 2^-24 fixed point
+// Forward state of one pixel.
+struct FwdPix {
+  float fx, fy;                 // pixel centre
+  float T, cr, cg, cb, dblend, wmax;
+  int imax_pos;                 // list position of the argmax, -1 if none
+  uint32_t last;                // one past the last blended position
+  bool done;
+};
 
-  const int tile = blockIdx.x;
-  const int tid = threadIdx.x, lane = tid & 31;
-  if (tid == 0) s_view = find_view(P.views, P.n_views, tile);
-  s_wsum[tid] = 0u;
-  __syncthreads();
-  const ViewDev& V = P.views[s_view];
-  int px, py;
-  pixel_of(V, tile, tid, &px, &py);
-  const bool inside = px < V.width && py < V.height;
-  const float fxp = (float)px + 0.5f, fyp = (float)py + 0.5f;
-  const uint2 range = P.ranges[tile];
-  const bool want_w = O.weight_sum != nullptr;
+__device__ __forceinline__ void fwd_pix_init(FwdPix& q, int px, int py, bool inside) {
+  q.fx = (float)px + 0.5f;
+  q.fy = (float)py + 0.5f;
+  q.T = 1.f;
+  q.cr = q.cg = q.cb = q.dblend = q.wmax = 0.f;
+  q.imax_pos = -1;
+  q.last = 0;
+  q.done = !inside;
+}
 
-  float T = 1.f, cr = 0.f, cg = 0.f, cb = 0.f, dblend = 0.f, wmax = 0.f;
-  int imax_pos = -1;
-  uint32_t last = 0;
-  bool done = !inside;
-
-  for (uint32_t bstart = range.x; bstart < range.y; bstart += kRenderThreads) {
-    if (__syncthreads_count(done) == kRenderThreads) break;
-    const uint32_t idx = bstart + tid;
-    if (idx < range.y) {
-      const uint32_t item = P.vals[idx];
-      s_item[tid] = item;
-      const float4 a = P.xy_tau_z[item];
-      s_xy[tid] = make_float2(a.x, a.y);
-      s_ex[tid] = exponent_form(P.conic_o[item]);
-      const float4 c = P.rgb[item];
-      s_rgbz[tid] = make_float4(c.x, c.y, c.z, a.w);
-    }
-    __syncthreads();
-    const int nb = (int)min(range.y - bstart, (uint32_t)kRenderThreads);
-    for (int j = 0; j < nb; ++j) {
-      if (__all_sync(0xffffffffu, done)) break;
-      float w = 0.f;
-      if (!done) {
-        const float2 m = s_xy[j];
-        const float e = expo(s_ex[j], fxp - m.x, fyp - m.y);
-        if (e >= P.e_min) {
-          const float alpha = fminf(P.alpha_max, ex2_approx(e));
-          const float Tn = T * (1.f - alpha);
-          if (Tn < P.t_min) {
-            done = true;
-          } else {
-            w = alpha * T;
-            const float4 c = s_rgbz[j];
-            cr += w * c.x;
-            cg += w * c.y;
-            cb += w * c.z;
-            dblend += w * c.w;
-            if (w > wmax) {
-              wmax = w;
-              imax_pos = (int)(bstart - range.x) + j;
-            }
-            T = Tn;
-            last = bstart - range.x + j + 1;
-          }
-        }
-      }
-      if (want_w && __any_sync(0xffffffffu, w > 0.f)) {
-        const uint32_t s = __reduce_add_sync(0xffffffffu, __float2uint_rn(w * 16777216.f));
-        if (lane == 0) atomicAdd(&s_wsum[j], s);
-      }
-    }
-    __syncthreads();
-    if (want_w && tid < nb) {
-      const uint32_t s = s_wsum[tid];
-      if (s) atomicAdd(&O.weight_sum[s_item[tid]], (float)s * (1.f / 16777216.f));
-      s_wsum[tid] = 0u;
-    }
+// Blends the entry at list position `pos` into the pixel; returns its weight.
+__device__ __forceinline__ float fwd_pix_blend(FwdPix& q, float2 m, float4 ex, const float4* s_rgbz, int j,
+                                               int pos, float alpha_max, float e_min, float t_min) {
+  if (q.done) return 0.f;
+  const float e = expo(ex, q.fx - m.x, q.fy - m.y);
+  if (e < e_min) return 0.f;
+  const float alpha = fminf(alpha_max, ex2_approx(e));
+  const float Tn = q.T * (1.f - alpha);
+  if (Tn < t_min) {
+    q.done = true;
+    return 0.f;
   }
-
-  const int64_t imax_item = imax_pos >= 0 ? (int64_t)P.vals[range.x + imax_pos] : -1;
-  // S_i: pixels whose i_max is i (warp-aggregated)
-  if (O.max_area) {
-    const bool has = inside && imax_item >= 0;
-    const uint32_t m = __ballot_sync(0xffffffffu, has);
-    if (has) {
-      const uint32_t peers = __match_any_sync(m, (unsigned long long)imax_item);
-      if (lane == __ffs(peers) - 1) atomicAdd(&O.max_area[imax_item], (uint32_t)__popc(peers));
-    }
+  const float w = alpha * q.T;
+  const float4 c = s_rgbz[j];
+  q.cr += w * c.x;
+  q.cg += w * c.y;
+  q.cb += w * c.z;
+  q.dblend += w * c.w;
+  if (w > q.wmax) {
+    q.wmax = w;
+    q.imax_pos = pos;
   }
-  if (!inside) return;
+  q.T = Tn;
+  q.last = pos + 1;
+  return w;
+}
+
+// Writes one pixel's outputs; S_i is added warp-aggregated by the caller.
+__device__ __forceinline__ void fwd_pix_store(const FwdPix& q, const RenderParams& P, const FwdOut& O, const ViewDev& V,
+                                              int view, int px, int py, int64_t imax_item) {
   const int64_t pix = V.pixel_base + (int64_t)py * V.width + px;
   const int64_t hw = (int64_t)V.width * V.height;
   float* img = O.image + 3 * V.pixel_base + (int64_t)py * V.width + px;
-  img[0] = cr + T * P.bg[0];
-  img[hw] = cg + T * P.bg[1];
-  img[2 * hw] = cb + T * P.bg[2];
-  O.final_T[pix] = T;
-  O.n_contrib[pix] = last;
-  if (O.imax) O.imax[pix] = imax_item >= 0 ? (int32_t)(imax_item - (int64_t)s_view * P.n) : -1;
-  if (O.wmax) O.wmax[pix] = wmax;
-  if (O.depth_blend) O.depth_blend[pix] = dblend;
+  img[0] = q.cr + q.T * P.bg[0];
+  img[hw] = q.cg + q.T * P.bg[1];
+  img[2 * hw] = q.cb + q.T * P.bg[2];
+  O.final_T[pix] = q.T;
+  O.n_contrib[pix] = q.last;
+  if (O.imax) O.imax[pix] = imax_item >= 0 ? (int32_t)(imax_item - (int64_t)view * P.n) : -1;
+  if (O.wmax) O.wmax[pix] = q.wmax;
+  if (O.depth_blend) O.depth_blend[pix] = q.dblend;
   if (O.depth) {
     float d = 0.f;
     if (imax_item >= 0) {
@@ -231,7 +191,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(RenderParams
       // is t Wd - e, and the chord midpoint is t = (e . Wd) / (Wd . Wd)
       const float4* df = P.depth_frame + 3 * imax_item;
       const float4 r0 = df[0], r1 = df[1], r2 = df[2];
-      const float rx = (fxp - V.cx) / V.fx, ry = (fyp - V.cy) / V.fy;
+      const float rx = (q.fx - V.cx) / V.fx, ry = (q.fy - V.cy) / V.fy;
       const float w0 = r0.x * rx + r0.y * ry + r0.z;
       const float w1 = r1.x * rx + r1.y * ry + r1.z;
       const float w2 = r2.x * rx + r2.y * ry + r2.z;
@@ -239,6 +199,118 @@ __global__ void __launch_bounds__(kRenderThreads) render_fwd_kernel(RenderParams
     }
     O.depth[pix] = d;
   }
+}
+
+// S_i: pixels whose i_max is i (warp-aggregated).
+__device__ __forceinline__ void add_max_area(uint32_t* max_area, bool has, int64_t imax_item, int lane) {
+  const uint32_t m = __ballot_sync(0xffffffffu, has);
+  if (has) {
+    const uint32_t peers = __match_any_sync(m, (unsigned long long)imax_item);
+    if (lane == __ffs(peers) - 1) atomicAdd(&max_area[imax_item], (uint32_t)__popc(peers));
+  }
+}
+
+// Support box (x0, x1, y0, y1) of an entry from its centre and the packed
+// half-extents (see pack_extent).
+__device__ __forceinline__ float4 support_box(float mx, float my, float packed) {
+  const float2 e = unpack_extent(packed);
+  return make_float4(mx - e.x, mx + e.x, my - e.y, my + e.y);
+}
+
+// Whether the box meets the pixel-centre rectangle [x0, x0 + 7] x [y0, y0 + 3]
+// of an 8x4 block.  The box contains every pixel whose exponent test can
+// pass (see pack_extent), so an entry whose box misses a block was blended
+// at none of its pixels.
+__device__ __forceinline__ bool box_meets_block(float4 b, float x0, float y0) {
+  return b.x <= x0 + 7.f && b.y >= x0 && b.z <= y0 + 3.f && b.w >= y0;
+}
+
+// One thread per two pixels: rows y and y + 8 of the tile (warp w < 4 owns
+// the 8x4 blocks at ((w & 1) 8, (w >> 1) 4) and 8 rows below), so the
+// shared-memory reads of an entry and the loop control serve both.
+constexpr int kFwdThreads = kTilePixels / 2;
+
+__global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P, FwdOut O) {
+  constexpr int kBatch = kTilePixels;
+  __shared__ int s_view;
+  __shared__ float2 s_xy[kBatch];
+  __shared__ float4 s_ex[kBatch];
+  __shared__ float4 s_rgbz[kBatch];
+  __shared__ uint32_t s_item[kBatch];
+  __shared__ uint32_t s_wsum[kBatch];    // 2^-24 fixed point
+
+  const int tile = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31;
+  if (tid == 0) s_view = find_view(P.views, P.n_views, tile);
+  s_wsum[tid] = 0u;
+  s_wsum[tid + kFwdThreads] = 0u;
+  __syncthreads();
+  const int view = s_view;
+  const ViewDev& V = P.views[view];
+  int px, py;
+  pixel_of(V, tile, tid, &px, &py);
+  const int py2 = py + kTile / 2;
+  const bool in0 = px < V.width && py < V.height;
+  const bool in1 = px < V.width && py2 < V.height;
+  FwdPix q0, q1;
+  fwd_pix_init(q0, px, py, in0);
+  fwd_pix_init(q1, px, py2, in1);
+  const uint2 range = P.ranges[tile];
+  const bool want_w = O.weight_sum != nullptr;
+
+  for (uint32_t bstart = range.x; bstart < range.y; bstart += kBatch) {
+    if (__syncthreads_count(q0.done && q1.done) == kFwdThreads) break;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = tid + h * kFwdThreads;
+      const uint32_t idx = bstart + k;
+      if (idx < range.y) {
+        const uint32_t item = P.vals[idx];
+        s_item[k] = item;
+        const float4 a = P.xy_tau_z[item];
+        s_xy[k] = make_float2(a.x, a.y);
+        s_ex[k] = exponent_form(P.conic_o[item]);
+        const float4 c = P.rgb[item];
+        s_rgbz[k] = make_float4(c.x, c.y, c.z, a.w);
+      }
+    }
+    __syncthreads();
+    const int nb = (int)min(range.y - bstart, (uint32_t)kBatch);
+    const int pos0 = (int)(bstart - range.x);
+    for (int j = 0; j < nb; ++j) {
+      if (__all_sync(0xffffffffu, q0.done && q1.done)) break;
+      const float2 m = s_xy[j];
+      const float4 ex = s_ex[j];
+      const float w0 = fwd_pix_blend(q0, m, ex, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
+      const float w1 = fwd_pix_blend(q1, m, ex, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
+      if (want_w && __any_sync(0xffffffffu, w0 > 0.f || w1 > 0.f)) {
+        const uint32_t s = __reduce_add_sync(0xffffffffu, __float2uint_rn(w0 * 16777216.f) +
+                                                              __float2uint_rn(w1 * 16777216.f));
+        if (lane == 0) atomicAdd(&s_wsum[j], s);
+      }
+    }
+    __syncthreads();
+    if (want_w) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = tid + h * kFwdThreads;
+        if (k < nb) {
+          const uint32_t s = s_wsum[k];
+          if (s) atomicAdd(&O.weight_sum[s_item[k]], (float)s * (1.f / 16777216.f));
+          s_wsum[k] = 0u;
+        }
+      }
+    }
+  }
+
+  const int64_t item0 = q0.imax_pos >= 0 ? (int64_t)P.vals[range.x + q0.imax_pos] : -1;
+  const int64_t item1 = q1.imax_pos >= 0 ? (int64_t)P.vals[range.x + q1.imax_pos] : -1;
+  if (O.max_area) {
+    add_max_area(O.max_area, in0 && item0 >= 0, item0, lane);
+    add_max_area(O.max_area, in1 && item1 >= 0, item1, lane);
+  }
+  if (in0) fwd_pix_store(q0, P, O, V, view, px, py, item0);
+  if (in1) fwd_pix_store(q1, P, O, V, view, px, py2, item1);
 }
 
 struct BwdIn {
@@ -249,35 +321,94 @@ struct BwdIn {
   float* weight_sum;            // optional: += I_i per item
 };
 
-// Backward of Eq. 1, one lane per entry.  For pixel x with blended entries
+// Backward of Eq. 1, two entries per lane.  For pixel x with blended entries
 // k (alpha_k, colour c_k, w_k = alpha_k T_k) and image I = sum w_k c_k + T bg:
 //   dI/dc_l     = w_l
 //   dI/dalpha_l = T_l c_l - (I - F_l) / (1 - alpha_l),  F_l = sum_{k<=l} w_k c_k
-// so with g = dL/dI the only per-pixel quantities a lane needs are the
+// so with g = dL/dI the only per-pixel quantities an entry needs are the
 // exclusive product T_l of (1 - alpha) and the inclusive sum of
-// w_k (c_k . g) over the entries in front of it.  A warp takes 32 consecutive
-// entries of the tile's list (one per lane) and walks its 32 pixels; both
-// prefix quantities are 5-step shuffle scans across the lanes, continued from
-// chunk to chunk through per-pixel state in shared memory.  Each lane sums
-// its entry's gradients over the pixels in registers, so no per-entry
-// reduction across pixels is needed.  Entries at or after a pixel's
-// n_contrib and entries with e < log2(alpha_min) do not take part, exactly as
-// in the forward pass.  With alpha_raw = 2^e unclamped, dalpha/de = alpha ln 2.
-__global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams P, BwdIn B) {
+// w_k (c_k . g) over the entries in front of it.  After a batch is staged,
+// each warp lists the batch entries whose support box meets its 8x4 block
+// (an entry outside the box was blended at none of the block's pixels), then
+// takes 64 consecutive listed entries at a time (lane l holds the 2l-th and
+// (2l + 1)-th) and walks its 32 pixels.  Each lane composes the affine maps x -> (1 - a) x + a (c.g)
+// of its two entries, one 5-step shuffle scan over the lanes gives both
+// prefix quantities for the lane's first entry, and the second follows from
+// the first in registers; the pixel's state is continued from chunk to chunk
+// through shared memory.  Each lane sums its entries' gradients over the
+// pixels in registers, so no per-entry reduction across pixels is needed.
+// Entries at or after a pixel's n_contrib and entries with
+// e < log2(alpha_min) do not take part, exactly as in the forward pass.  With
+// alpha_raw = 2^e unclamped, dalpha/de = alpha ln 2.
+struct BwdEntry {
+  float mx, my;        // centre
+  float4 ex;           // exponent form
+  float3 col;
+  float acc[9];        // d(centre x, y), d(a2, b2, c2), d log2 o, d colour
+  float wsum;          // blending weight over the warp's pixels (I_i)
+};
+
+__device__ __forceinline__ void bwd_entry_load(BwdEntry& E, bool valid, const float2* s_xy, const float4* s_ex,
+                                               const float4* s_rgb, int idx) {
+  const float2 m = valid ? s_xy[idx] : make_float2(0.f, 0.f);
+  E.mx = m.x;
+  E.my = m.y;
+  // an invalid entry gets an exponent that never passes the e_min test
+  E.ex = valid ? s_ex[idx] : make_float4(0.f, 0.f, 0.f, -1e30f);
+  const float4 c = valid ? s_rgb[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
+  E.col = make_float3(c.x, c.y, c.z);
+#pragma unroll
+  for (int k = 0; k < 9; ++k) E.acc[k] = 0.f;
+  E.wsum = 0.f;
+}
+
+// Adds one pixel's contribution to an active entry's gradient sums.
+__device__ __forceinline__ void bwd_entry_accumulate(BwdEntry& E, const float4& pg, float dx, float dy, float a,
+                                                     float araw, float Tl, float Fl, float cg, float alpha_max) {
+  const float w = a * Tl;
+  E.wsum += w;
+  E.acc[6] = fmaf(w, pg.x, E.acc[6]);
+  E.acc[7] = fmaf(w, pg.y, E.acc[7]);
+  E.acc[8] = fmaf(w, pg.z, E.acc[8]);
+  if (araw <= alpha_max) {
+    const float dal = fmaf(Tl, cg, -(pg.w - Fl) * rcp_approx(1.f - a));
+    const float de = dal * a * kLn2;          // dL/de
+    const float dedx = de * dx, dedy = de * dy;
+    E.acc[5] += de;                           // d log2 o
+    E.acc[2] = fmaf(dedx, dx, E.acc[2]);      // d a2
+    E.acc[3] = fmaf(dedx, dy, E.acc[3]);      // d b2
+    E.acc[4] = fmaf(dedy, dy, E.acc[4]);      // d c2
+    // d = pixel - centre: de/dcentre = -(2 a2 dx + b2 dy, b2 dx + 2 c2 dy)
+    E.acc[0] = fmaf(-2.f * E.ex.x, dedx, fmaf(-E.ex.y, dedy, E.acc[0]));
+    E.acc[1] = fmaf(-E.ex.y, dedx, fmaf(-2.f * E.ex.z, dedy, E.acc[1]));
+  }
+}
+
+__device__ __forceinline__ void bwd_entry_flush(const BwdEntry& E, float (*s_g)[kRenderThreads], float* s_wsum,
+                                                int idx, bool want_w) {
+#pragma unroll
+  for (int k = 0; k < 9; ++k)
+    if (E.acc[k] != 0.f) atomicAdd(&s_g[k][idx], E.acc[k]);
+  if (want_w && E.wsum != 0.f) atomicAdd(&s_wsum[idx], E.wsum);
+}
+
+__global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderParams P, BwdIn B) {
   constexpr int kWarps = kRenderThreads / 32;
+  constexpr int kChunk = 64;                   // entries per warp step
   __shared__ int s_view;
   __shared__ uint32_t s_max_nc;
   __shared__ float2 s_xy[kRenderThreads];
   __shared__ float4 s_ex[kRenderThreads];
   __shared__ float4 s_rgb[kRenderThreads];
+  __shared__ float4 s_box[kRenderThreads];
   __shared__ uint32_t s_item[kRenderThreads];
   __shared__ float s_g[9][kRenderThreads];
   __shared__ float s_wsum[kRenderThreads];     // I_i of the batch's entries (optional output)
+  __shared__ uint8_t s_list[kWarps][kRenderThreads];   // the batch entries each warp walks
   // per-pixel state, indexed by the pixel's thread id (warp w owns 32w..32w+31)
   __shared__ float4 s_pg[kRenderThreads];     // dL/dI (r, g, b) and I . dL/dI
-  __shared__ float s_T[kRenderThreads];       // transmittance before the next chunk
-  __shared__ float s_F[kRenderThreads];       // sum of w (c . g) so far
-  __shared__ uint32_t s_nc[kRenderThreads];
+  // transmittance before the next chunk, sum of w (c . g) so far, n_contrib
+  __shared__ float4 s_st[kRenderThreads];
   __shared__ uint32_t s_warp_nc[kWarps];
 
   const int tile = blockIdx.x;
@@ -289,12 +420,13 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
   __syncthreads();
   const ViewDev& V = P.views[s_view];
   const uint2 range = P.ranges[tile];
+  const bool want_w = B.weight_sum != nullptr;
+  uint32_t my_nc = 0;
   {
     int px, py;
     pixel_of(V, tile, tid, &px, &py);
     const bool inside = px < V.width && py < V.height;
     float4 pg = make_float4(0.f, 0.f, 0.f, 0.f);
-    uint32_t nc = 0;
     if (inside) {
       const int64_t pix = V.pixel_base + (int64_t)py * V.width + px;
       const int64_t hw = (int64_t)V.width * V.height;
@@ -303,13 +435,11 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
       pg.y = B.dL_dimage[o3 + hw];
       pg.z = B.dL_dimage[o3 + 2 * hw];
       pg.w = B.image[o3] * pg.x + B.image[o3 + hw] * pg.y + B.image[o3 + 2 * hw] * pg.z;
-      nc = B.n_contrib[pix];
+      my_nc = B.n_contrib[pix];
     }
     s_pg[tid] = pg;
-    s_T[tid] = 1.f;
-    s_F[tid] = 0.f;
-    s_nc[tid] = nc;
-    const uint32_t wm = __reduce_max_sync(0xffffffffu, nc);
+    s_st[tid] = make_float4(1.f, 0.f, __uint_as_float(my_nc), 0.f);
+    const uint32_t wm = __reduce_max_sync(0xffffffffu, my_nc);
     if (lane == 0) {
       s_warp_nc[warp] = wm;
       atomicMax(&s_max_nc, wm);
@@ -324,6 +454,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
   int bx, by;
   pixel_of(V, tile, warp * 32, &bx, &by);        // this warp's first pixel
   const float bxf = (float)bx + 0.5f, byf = (float)by + 0.5f;
+  const uint32_t lt_mask = (1u << lane) - 1u;
 
   for (uint32_t bstart = 0; bstart < max_nc; bstart += kRenderThreads) {
     const int nb = (int)min(max_nc - bstart, (uint32_t)kRenderThreads);
@@ -333,79 +464,82 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
       const float4 a = P.xy_tau_z[item];
       s_xy[tid] = make_float2(a.x, a.y);
       s_ex[tid] = exponent_form(P.conic_o[item]);
-      s_rgb[tid] = P.rgb[item];
+      const float4 c = P.rgb[item];
+      s_rgb[tid] = c;
+      s_box[tid] = support_box(a.x, a.y, c.w);
     }
     __syncthreads();
-    for (int c = 0; c < nb; c += 32) {
-      const uint32_t c0 = bstart + c;
-      if (c0 >= warp_nc) break;
-      const int e_idx = c + lane;                   // my entry in the batch
-      const bool valid = e_idx < nb;
-      const float2 m = valid ? s_xy[e_idx] : make_float2(0.f, 0.f);
-      // an invalid lane gets an exponent that never passes the e_min test
-      const float4 ex = valid ? s_ex[e_idx] : make_float4(0.f, 0.f, 0.f, -1e30f);
-      const float4 col = valid ? s_rgb[e_idx] : make_float4(0.f, 0.f, 0.f, 0.f);
-      const uint32_t pos = c0 + lane;
-      const float dx0 = bxf - m.x, dy0 = byf - m.y;
-      float acc[9] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-      float wsum = 0.f;                             // this entry's blending weight over the warp's pixels
-      // pixels of this warp that are still blending at this chunk
-      const uint32_t pmask = __ballot_sync(0xffffffffu, s_nc[warp * 32 + lane] > c0);
-      const float a2x2 = 2.f * ex.x, c2x2 = 2.f * ex.z;
-#pragma unroll
+    // the batch entries this warp walks: support box meets its 8x4 block and
+    // list position before the last blended position of its pixels (the
+    // forward pass culls with the same boxes and blocks)
+    int cnt = 0;
+    for (int k0 = 0; k0 < nb; k0 += 32) {
+      const int k = k0 + lane;
+      const bool hit = k < nb && bstart + (uint32_t)k < warp_nc && box_meets_block(s_box[k], bxf, byf);
+      const uint32_t bal = __ballot_sync(0xffffffffu, hit);
+      if (hit) s_list[warp][cnt + __popc(bal & lt_mask)] = (uint8_t)k;
+      cnt += __popc(bal);
+    }
+    for (int c = 0; c < cnt; c += kChunk) {
+      __syncwarp();                                 // list stores; lane 31's state stores of the last chunk
+      const int ta = c + 2 * lane, tb = ta + 1;     // my entries in the list
+      const bool va = ta < cnt, vb = tb < cnt;
+      const int ia = va ? s_list[warp][ta] : 0, ib = vb ? s_list[warp][tb] : 0;
+      BwdEntry A, Bn;
+      bwd_entry_load(A, va, s_xy, s_ex, s_rgb, ia);
+      bwd_entry_load(Bn, vb, s_xy, s_ex, s_rgb, ib);
+      const uint32_t posa = bstart + ia, posb = bstart + ib;   // list positions
+      // pixels of this warp still blending at the chunk's first entry
+      const uint32_t pmask = __ballot_sync(0xffffffffu, my_nc > bstart + s_list[warp][c]);
+#pragma unroll 4
       for (int p = 0; p < 32; ++p) {
         if (!(pmask & (1u << p))) continue;
         const int pt = warp * 32 + p;                 // the pixel's thread id
-        const uint32_t nc = s_nc[pt];
-        const float dx = dx0 + (float)(p & 7), dy = dy0 + (float)(p >> 3);
-        const float e = expo(ex, dx, dy);
-        const bool act = pos < nc && e >= P.e_min;
-        if (!__any_sync(0xffffffffu, act)) continue;
-        const float T0 = s_T[pt];
-        const float F0 = s_F[pt];
+        const float4 st = s_st[pt];
+        const uint32_t nc = __float_as_uint(st.z);
+        // pixel centre minus entry centre, rounded exactly as in the forward
+        const float fx = bxf + (float)(p & 7), fy = byf + (float)(p >> 3);
+        const float dxa = fx - A.mx, dya = fy - A.my;
+        const float dxb = fx - Bn.mx, dyb = fy - Bn.my;
+        const float ea = expo(A.ex, dxa, dya);
+        const float eb = expo(Bn.ex, dxb, dyb);
+        const bool acta = posa < nc && ea >= P.e_min;
+        const bool actb = posb < nc && eb >= P.e_min;
+        if (!__any_sync(0xffffffffu, acta || actb)) continue;
         const float4 pg = s_pg[pt];
-        const float araw = ex2_approx(e);
-        const float a = act ? fminf(P.alpha_max, araw) : 0.f;
-        const float cg = col.x * pg.x + col.y * pg.y + col.z * pg.z;
-        // one scan gives the product of (1 - a) and sum a_k cg_k prod_{j<k} (1 - a_j)
-        float m = 1.f - a, f = a * cg;
+        const float arawa = ex2_approx(ea), arawb = ex2_approx(eb);
+        const float aa = acta ? fminf(P.alpha_max, arawa) : 0.f;
+        const float ab = actb ? fminf(P.alpha_max, arawb) : 0.f;
+        const float cga = A.col.x * pg.x + A.col.y * pg.y + A.col.z * pg.z;
+        const float cgb = Bn.col.x * pg.x + Bn.col.y * pg.y + Bn.col.z * pg.z;
+        // the lane's two maps composed, then one scan over the lanes: the
+        // product of (1 - a) and sum a_k cg_k prod_{j<k} (1 - a_j)
+        const float ma = 1.f - aa, mb = 1.f - ab;
+        const float fa = aa * cga;
+        float m = ma * mb, f = fmaf(ma, ab * cgb, fa);
         scan_affine(m, f);
-        float mex = __shfl_up_sync(0xffffffffu, m, 1);     // exclusive product
-        if (lane == 0) mex = 1.f;
-        const float Tl = T0 * mex;
-        const float w = a * Tl;
-        const float Fl = fmaf(T0, f, F0);                  // sum_{k<=l} w_k cg_k
+        float mex = __shfl_up_sync(0xffffffffu, m, 1);     // exclusive over lanes
+        float fex = __shfl_up_sync(0xffffffffu, f, 1);
+        if (lane == 0) {
+          mex = 1.f;
+          fex = 0.f;
+        }
+        const float T0 = st.x, F0 = st.y;
+        const float Ta = T0 * mex;                          // T in front of entry A
+        const float Fa = fmaf(Ta, fa, fmaf(T0, fex, F0));   // sum_{k<=A} w_k cg_k
+        const float Tb = Ta * ma;
+        const float Fb = fmaf(Tb * ab, cgb, Fa);
         // lane 31 holds the chunk's totals: carry the pixel's state forward
         __syncwarp();
         if (lane == 31) {
-          s_T[pt] = T0 * m;
-          s_F[pt] = Fl;
+          float2* stp = reinterpret_cast<float2*>(&s_st[pt]);
+          *stp = make_float2(T0 * m, fmaf(T0, f, F0));
         }
-        if (act) {
-          wsum += w;
-          acc[6] = fmaf(w, pg.x, acc[6]);
-          acc[7] = fmaf(w, pg.y, acc[7]);
-          acc[8] = fmaf(w, pg.z, acc[8]);
-          if (araw <= P.alpha_max) {
-            const float dal = fmaf(Tl, cg, -(pg.w - Fl) * rcp_approx(1.f - a));
-            const float de = dal * a * kLn2;          // dL/de
-            const float dedx = de * dx, dedy = de * dy;
-            acc[5] += de;                             // d log2 o
-            acc[2] = fmaf(dedx, dx, acc[2]);          // d a2
-            acc[3] = fmaf(dedx, dy, acc[3]);          // d b2
-            acc[4] = fmaf(dedy, dy, acc[4]);          // d c2
-            // d = pixel - centre: de/dcentre = -(2 a2 dx + b2 dy, b2 dx + 2 c2 dy)
-            acc[0] = fmaf(-a2x2, dedx, fmaf(-ex.y, dedy, acc[0]));
-            acc[1] = fmaf(-ex.y, dedx, fmaf(-c2x2, dedy, acc[1]));
-          }
-        }
+        if (acta) bwd_entry_accumulate(A, pg, dxa, dya, aa, arawa, Ta, Fa, cga, P.alpha_max);
+        if (actb) bwd_entry_accumulate(Bn, pg, dxb, dyb, ab, arawb, Tb, Fb, cgb, P.alpha_max);
       }
-      if (valid) {
-#pragma unroll
-        for (int k = 0; k < 9; ++k)
-          if (acc[k] != 0.f) atomicAdd(&s_g[k][e_idx], acc[k]);
-        if (B.weight_sum && wsum != 0.f) atomicAdd(&s_wsum[e_idx], wsum);
-      }
+      if (va) bwd_entry_flush(A, s_g, s_wsum, ia, want_w);
+      if (vb) bwd_entry_flush(Bn, s_g, s_wsum, ib, want_w);
     }
     __syncthreads();
     if (tid < nb) {
@@ -422,7 +556,7 @@ __global__ void __launch_bounds__(kRenderThreads) render_bwd_kernel(RenderParams
       if (v[4] != 0.f || v[5] != 0.f || v[6] != 0.f || v[7] != 0.f)
         atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
       if (v[8] != 0.f) atomicAdd(&dst[2].x, v[8]);
-      if (B.weight_sum) {
+      if (want_w) {
         const float ws = s_wsum[tid];
         s_wsum[tid] = 0.f;
         if (ws != 0.f) atomicAdd(&B.weight_sum[item], ws);
@@ -462,7 +596,7 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
   FwdOut O{out.image, out.final_T, out.n_contrib, out.imax, out.wmax, out.depth, out.depth_blend,
            out.weight_sum, out.max_area};
   if (total_tiles > 0)
-    GS_TIMED("render_fwd", stream, (render_fwd_kernel<<<total_tiles, kRenderThreads, 0, stream>>>(P, O)));
+    GS_TIMED("render_fwd", stream, (render_fwd_kernel<<<total_tiles, kFwdThreads, 0, stream>>>(P, O)));
   return cudaGetLastError();
 }
 

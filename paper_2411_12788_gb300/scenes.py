@@ -112,6 +112,25 @@ def box_scene(n: int = 1024, seed: int = 0, sh_degree: int = 0) -> Scene:
                    {"kind": "box", "seed": seed})
 
 
+def needle_scene(n: int = 4000, seed: int = 0) -> Scene:
+    """Adversarial scene for the support-box margins: means uniform in
+    [-1.5,1.5]^2 x [2,8], long axis log-uniform in [0.02, 0.5], the other two
+    shorter by a log-uniform ratio in [1, 1000] (x U[0.5, 2] for the third),
+    uniform unit quaternions, half the opacities just above 1/255
+    ((1 + U[1e-4, 1e-2]) / 255) and half U[0.05, 0.99], DC colour U[0,1]."""
+    rng = np.random.default_rng(seed)
+    means = np.stack([rng.uniform(-1.5, 1.5, n), rng.uniform(-1.5, 1.5, n),
+                      rng.uniform(2, 8, n)], axis=1)
+    long = np.exp(rng.uniform(np.log(0.02), np.log(0.5), n))
+    short = long / np.exp(rng.uniform(0.0, np.log(1e3), n))
+    scales = np.stack([long, short, short * rng.uniform(0.5, 2.0, n)], axis=1)
+    quats = _unit_quaternions(rng, n)
+    faint = rng.uniform(size=n) < 0.5
+    opac = np.where(faint, (1.0 + rng.uniform(1e-4, 1e-2, n)) / 255.0, rng.uniform(0.05, 0.99, n))
+    sh = _sh_from_colour(rng, n, 0, 0.05)
+    return _finish(means, scales, quats, opac, sh, 0, {"kind": "needles", "seed": seed})
+
+
 def cluster_scene(n: int, n_clusters: int = 64, seed: int = 0,
                   sh_degree: int = 3) -> Scene:
     """Training-shaped scene: 80 % of the means from a mixture of anisotropic

@@ -1,0 +1,65 @@
+"""Per-block culling of the backward pass.
+
+The backward kernel walks, per 8x4 pixel block, only the entries whose packed
+support box meets the block; the forward pass decides membership pixel by
+pixel.  The two agree only if every pixel the forward pass blended an entry at
+lies inside that entry's box.  Every pixel's i_max is such a (pixel, entry)
+pair, so on a scene where most blended pairs are an argmax (sparse needles)
+this checks the boxes directly, on the inputs where the FP32 exponent's
+rounding is largest next to the support: axis ratios up to 1e3 and opacities
+just above the alpha threshold.
+"""
+import numpy as np
+import pytest
+import torch
+
+from paper_2411_12788_gb300 import raster, scenes
+
+pytestmark = pytest.mark.gpu
+
+
+def _need_gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _unpack_extents(packed: np.ndarray):
+    u = packed.astype(np.float32).view(np.uint32)
+    ex = (u & 0xFFFF).astype(np.uint16).view(np.float16).astype(np.float32)
+    ey = (u >> 16).astype(np.uint16).view(np.float16).astype(np.float32)
+    return ex, ey
+
+
+@pytest.mark.parametrize("seed", [7, 8])
+def test_support_boxes_hold_every_blended_pixel(seed):
+    _need_gpu()
+    W = H = 512
+    sc = scenes.needle_scene(4000, seed=seed)
+    cam = scenes.origin_camera(W, H, 512.0)
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, [cam])
+    st = raster.inspect_preprocess(fr)
+    imax = fr.outs["imax"][: W * H].cpu().numpy()
+    pix = np.nonzero(imax >= 0)[0]
+    assert pix.size > 10000
+    i = imax[pix]
+    xyz = st["xy_tau_z"].numpy()
+    mx, my = xyz[i, 0], xyz[i, 1]
+    ex, ey = _unpack_extents(st["rgb"].numpy()[i, 3])
+    px = (pix % W).astype(np.float32) + np.float32(0.5)
+    py = (pix // W).astype(np.float32) + np.float32(0.5)
+    inside = (mx - ex <= px) & (mx + ex >= px) & (my - ey <= py) & (my + ey >= py)
+    assert inside.all(), f"{(~inside).sum()} blended pixels outside their entry's box"
+
+    # the scene does reach thin, faint supports
+    co = st["conic_o"].numpy()
+    vis = st["tiles"].numpy() > 0
+    A, B, C = co[vis, 0].astype(np.float64), co[vis, 1].astype(np.float64), co[vis, 2].astype(np.float64)
+    disc = np.sqrt(((A - C) / 2) ** 2 + B ** 2)
+    kappa = ((A + C) / 2 + disc) / ((A + C) / 2 - disc)
+    assert kappa.max() > 1e4
+    assert (co[vis, 3] < 1.02 / 255).sum() > 100
+    # and blended pixels reach the outer part of their boxes (thin supports get
+    # wider margins, so the ratio stays below 1 / (1.02 + 4e-6 kappa))
+    rel = np.maximum(np.abs(px - mx) / ex, np.abs(py - my) / ey)
+    assert (rel > 0.75).sum() > 0
