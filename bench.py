@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-serve", action="store_true")
     ap.add_argument("--no-dense", action="store_true")
+    ap.add_argument("--no-culling", action="store_true")
     ap.add_argument("--serve-requests", type=int, default=2200)
     return ap.parse_args()
 
@@ -161,9 +162,9 @@ class Step:
         self.grads["weight_sum"] = torch.zeros(int(self.plan.n_items), device="cuda")
         self.pixels = int(self.plan.total_pixels)
 
-    def run(self):
+    def run(self, mask=None):
         r = self.raster
-        r.preprocess(self.plan, self.g.struct(), self.cfg, self.pre_ws)
+        r.preprocess(self.plan, self.g.struct(), self.cfg, self.pre_ws, mask)
         need = r.bin_sort_workspace_size(self.plan)
         if self.sort_ws.numel() < need:
             self.sort_ws = self.torch.empty(int(need * 1.1), dtype=self.torch.uint8, device="cuda")
@@ -225,14 +226,16 @@ def roofline(kt: dict, st: "Step", steps: int, peaks: dict, clocks: dict) -> dic
 
 
 FP32_LANES = 152 * 128
-# FP32 floating-point operations (an FMA counts 2) per (pixel, entry)
-# evaluation of a blended entry, counted from the arithmetic the kernels do:
-# forward: offsets 2, exponent 8, alpha 2, transmittance 2, weight 1,
-# colour 6, depth 2, argmax 1 = 24; backward: offsets 2, exponent 8, alpha 2,
-# c.g 5, affine scan 15, T/w/F 5, colour gradient 6, dL/dalpha 6, dL/de 2,
-# conic and centre terms 15 = 66.  MUFU work (ex2, rcp) is not counted.
+# Algorithmic FP32 operations (an FMA counts 2) per (pixel, entry)
+# evaluation of a blended entry, counted for the plain sequential per-pixel
+# algorithm (no scan or other parallelisation overhead): forward: offsets 2,
+# exponent 8, alpha 2, transmittance 2, weight 1, colour 6, blended depth 2,
+# argmax 1 = 24; backward: offsets 2, exponent 8, alpha 2, transmittance 2,
+# weight 1, c.g 5, running colour sum 2, colour gradient 6, dL/dalpha 4,
+# dL/de 2, conic and centre terms 17, I_i 1 = 52.  MUFU work (ex2, rcp) is not
+# counted.
 FWD_FLOPS_PER_EVAL = 24
-BWD_FLOPS_PER_EVAL = 66
+BWD_FLOPS_PER_EVAL = 52
 
 
 def run_ours(args, rank, world):
@@ -275,6 +278,7 @@ def run_ours(args, rank, world):
         peaks = {"hbm_gbs": 6800.0, "note": "fallback"}
     rl = roofline(kt, st, args.steps, peaks, ck)
 
+    culling = None if args.no_culling else run_culling(st, args, sec_max * 1e3 / args.steps)
     e2e = None
     if not args.no_e2e:
         e2e = run_e2e(st, args, world)
@@ -292,9 +296,51 @@ def run_ours(args, rank, world):
                        "l2": "inputs larger than L2 (236 MB scene, 1.5 GB workspace)",
                        "parallelism": f"replicas x{world}"},
             "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
-            "serving": serving, "dense_phase": dense,
+            "serving": serving, "dense_phase": dense, "culling": culling,
             "clocks": ck, "kernels": kt}
     return line
+
+
+def run_culling(st: Step, args, ms_unculled: float) -> dict:
+    """Occluded-Gaussian culling (Sec. 5.2): the per-view visibility V_i of
+    the step's scene and views from one forward pass (I_i, S_i, i_max, w_max
+    -> gs_identify), then the same training step with the invisible (view,
+    Gaussian) items masked out in the preprocess.  Reports both step times,
+    like the paper's comparison of training with and without culling."""
+    import torch
+    r = st.raster
+    outs = r.alloc_outputs(st.plan, "cuda", want=("image", "final_T", "n_contrib", "imax", "wmax", "weight_sum",
+                                                  "max_area"))
+    r.preprocess(st.plan, st.g.struct(), st.cfg, st.pre_ws)
+    r.bin_sort(st.plan, st.pre_ws, st.sort_ws)
+    r.render_fwd(st.plan, st.cfg, st.pre_ws, st.sort_ws, outs)
+    entries = int(st.plan.n_entries)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    idr = r.identify(st.plan, outs["weight_sum"], outs["max_area"], outs["imax"], outs["wmax"])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    identify_ms = e0.elapsed_time(e1)
+    mask = idr["visible_mask"]
+    for _ in range(3):
+        st.run(mask)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(args.steps):
+        st.run(mask)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    culled_entries = int(st.plan.n_entries)
+    counts = idr["counts"].cpu().tolist()
+    return {"visible_items": int(mask.to(torch.int64).sum().item()), "items": int(st.plan.n_items),
+            "per_view_blur_intersect_visible_critical": counts, "identify_ms": identify_ms,
+            "ms_per_step_unculled": ms_unculled, "ms_per_step_culled": ms,
+            "mpix_per_s_culled": st.pixels / ms / 1e3, "entries_unculled": entries, "entries_culled": culled_entries,
+            "note": "visibility: keep quantile 0.99 of the positive I_i per view; the masked step renders only "
+                    "the visible (view, Gaussian) items"}
 
 
 def run_e2e(st: Step, args, world) -> dict:

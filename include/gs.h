@@ -262,6 +262,46 @@ gs_status gs_prune_select(const float* importance, int64_t n, int64_t k, uint32_
 gs_status gs_gather_scene(const gs_scene* src, const uint32_t* idx, int64_t k,
                           const gs_scene_buf* dst, void* stream);
 
+/* ---- identification of Gaussians (Sec. 4-5) ------------------------------ */
+
+/* Flag bits written by gs_identify, per (view, Gaussian) item. */
+#define GS_ID_BLUR 1u       /* G^blur (Sec. 4.1): S_i > theta_blur * H * W, blur-split candidate */
+#define GS_ID_INTERSECT 2u  /* G^int (Sec. 4.3): S_i > 0, the i_max of at least one pixel */
+#define GS_ID_VISIBLE 4u    /* V_i (Sec. 5.2): I_i above the view's keep-quantile threshold */
+#define GS_ID_CRITICAL 8u   /* G^crit (Sec. 5.1): i_max of a pixel whose w_max is above the
+                               view's keep-quantile threshold */
+
+typedef struct gs_config_identify {
+  float theta_blur;         /* 2e-4 (Sec. 4.1) */
+  float keep_visible;       /* 0.99 keep quantile of the visibility threshold (Sec. 5.2) */
+  float keep_critical;      /* 0.99 keep quantile of the critical threshold (Sec. 5.1) */
+} gs_config_identify;
+
+void gs_config_identify_default(gs_config_identify* out);
+
+/* Bytes of the workspace gs_identify needs (256-byte aligned). */
+size_t gs_identify_workspace_size(const gs_plan* plan);
+
+/* Per-view selections of Gaussians from one forward pass over the plan's
+ * views.  A keep quantile q over the M positive values of a view keeps the
+ * ceil(q M) largest of them (q M formed in double), ties to the lower index;
+ * the paper states the quantile only as "0.99" (Sec. 5.1, 5.2).
+ *   weight_sum  device [n_items] I_i of each item (Sec. 3.2), non-negative
+ *   max_area    device [n_items] S_i of each item (Sec. 4.1)
+ *   imax, wmax  device [total_pixels] forward outputs of the same plan
+ *   flags       device, n_items rounded up to a multiple of 4 bytes, 4-byte
+ *               aligned; OVERWRITTEN with GS_ID_* bits per item
+ *   visible_mask  device [n_items] or NULL: 1 where GS_ID_VISIBLE, else 0 (a
+ *               mask for gs_preprocess: view-dependent culling, Sec. 5.2)
+ *   counts      device [n_views][4] or NULL: per view, how many items carry
+ *               BLUR, INTERSECT, VISIBLE, CRITICAL (overwritten)
+ * Asynchronous; GS_ERR_INVALID_ARG for bad sizes, pointers, alignment or
+ * configuration (quantiles outside [0, 1], negative theta). */
+gs_status gs_identify(const gs_plan* plan, const gs_config_identify* cfg, const float* weight_sum,
+                      const uint32_t* max_area, const int32_t* imax, const float* wmax,
+                      uint8_t* flags, uint8_t* visible_mask, uint32_t* counts,
+                      void* ws, size_t ws_bytes, void* stream);
+
 /* ---- training-step helpers ------------------------------------------- */
 
 /* Mean absolute error over `count` elements and its gradient (the L1 term
@@ -279,7 +319,7 @@ gs_status gs_loss_l1(const float* image, const float* target, int64_t count,
 typedef struct gs_preprocess_view {
   const float* xy_tau_z;        /* [n_items][4] centre x, y, tau = 2 ln(o/alpha_min), z */
   const float* conic_o;         /* [n_items][4] A, B, C, opacity */
-  const float* rgb;             /* [n_items][4] r, g, b, 0 */
+  const float* rgb;             /* [n_items][4] r, g, b, support half-extents (x, y) as two halves */
   const uint32_t* tiles;        /* [n_items] touched-tile count, 0 if culled */
   const uint32_t* rect;         /* [n_items][2] (tx0 | ty0 << 16, tx1 | ty1 << 16) */
   const uint32_t* sorted_items; /* [n_items] items in (float32 z, item) order, culled last */

@@ -13,7 +13,8 @@ definitions:
   * Sec. 3.3, Eq. 2 and Sec. 4.1: the rendered index i_max = argmax_i w_i and
     the midpoint depth of the ray-ellipsoid chord d^mid_{i_max}; the blended
     depth sum_i w_i d_i; the maximum-contribution area S_i.
-  * Sec. 5.2: per-view visibility from summed blending weights.
+  * Sec. 4.1, 4.3, 5.1, 5.2: blur-split candidates, intersected, visible and
+    critical Gaussians of a rendered view.
 Gradients are the exact derivatives of this forward, taken by torch.autograd.
 
 Module map:
@@ -21,9 +22,10 @@ Module map:
   oracle.render    step R: per-pixel compositing and its side outputs
   oracle.binning   step B: tile lists, sort order and tile ranges
   oracle.prune     top-fraction selection by blending weight
+  oracle.identify  per-view selections of Gaussians (Sec. 4-5)
   oracle.loss      photometric losses used by the training step
 """
 from .config import OracleConfig
-from . import project, render, binning, prune, loss
+from . import project, render, binning, prune, loss, identify
 
-__all__ = ["OracleConfig", "project", "render", "binning", "prune", "loss"]
+__all__ = ["OracleConfig", "project", "render", "binning", "prune", "loss", "identify"]

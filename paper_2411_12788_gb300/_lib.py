@@ -79,6 +79,10 @@ class SortView(C.Structure):
     _fields_ = [("tile_ids", C.c_void_p), ("items", C.c_void_p), ("ranges", C.c_void_p)]
 
 
+class ConfigIdentify(C.Structure):
+    _fields_ = [("theta_blur", C.c_float), ("keep_visible", C.c_float), ("keep_critical", C.c_float)]
+
+
 class KernelTime(C.Structure):
     _fields_ = [("name", C.c_char_p), ("ms", C.c_double), ("launches", C.c_int64)]
 
@@ -103,6 +107,11 @@ SIGNATURES = {
     "gs_prune_select": (C.c_int, [C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t,
                                   C.c_void_p]),
     "gs_gather_scene": (C.c_int, [C.POINTER(Scene), C.c_void_p, C.c_int64, C.POINTER(SceneBuf), C.c_void_p]),
+    "gs_config_identify_default": (None, [C.POINTER(ConfigIdentify)]),
+    "gs_identify_workspace_size": (C.c_size_t, [C.POINTER(Plan)]),
+    "gs_identify": (C.c_int, [C.POINTER(Plan), C.POINTER(ConfigIdentify), C.c_void_p, C.c_void_p, C.c_void_p,
+                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
+                              C.c_void_p]),
     "gs_loss_l1": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_device_status": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.c_void_p]),
     "gs_inspect_preprocess": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.POINTER(PreprocessView)]),

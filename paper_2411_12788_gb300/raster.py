@@ -151,6 +151,35 @@ def prune_select(importance: torch.Tensor, k: int, stream=None) -> torch.Tensor:
     return keep[:k]
 
 
+ID_BLUR, ID_INTERSECT, ID_VISIBLE, ID_CRITICAL = 1, 2, 4, 8
+
+
+def make_identify_config(**kw) -> _lib.ConfigIdentify:
+    c = _lib.ConfigIdentify()
+    lib().gs_config_identify_default(C.byref(c))
+    for k, v in kw.items():
+        setattr(c, k, v)
+    return c
+
+
+def identify(plan, weight_sum: torch.Tensor, max_area: torch.Tensor, imax: torch.Tensor, wmax: torch.Tensor,
+             cfg=None, stream=None) -> dict:
+    """Per-view selections of Gaussians (gs_identify): flags [n_items] uint8
+    (ID_* bits), visible_mask [n_items] uint8 (a gs_preprocess mask) and
+    counts [n_views, 4] (BLUR, INTERSECT, VISIBLE, CRITICAL per view)."""
+    cfg = cfg or make_identify_config()
+    dev = weight_sum.device
+    I = int(plan.n_items)
+    flags = torch.empty(((I + 3) // 4) * 4 or 4, dtype=torch.uint8, device=dev)
+    vis = torch.empty(max(I, 1), dtype=torch.uint8, device=dev)
+    counts = torch.empty((int(plan.n_views), 4), dtype=torch.int32, device=dev)
+    ws = torch.empty(max(int(lib().gs_identify_workspace_size(C.byref(plan))), 1), dtype=torch.uint8, device=dev)
+    check("gs_identify", lib().gs_identify(C.byref(plan), C.byref(cfg), _ptr(weight_sum), _ptr(max_area), _ptr(imax),
+                                           _ptr(wmax), _ptr(flags), _ptr(vis), _ptr(counts), _ptr(ws), ws.numel(),
+                                           _stream(stream)))
+    return {"flags": flags[:I], "visible_mask": vis[:I], "counts": counts}
+
+
 def gather_scene(g: "GaussianTensors", idx: torch.Tensor, stream=None) -> "GaussianTensors":
     """A compact copy of the rows idx of every attribute (gs_gather_scene)."""
     k = int(idx.numel())

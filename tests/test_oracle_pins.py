@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from oracle import OracleConfig
-from oracle import binning, project as P, render as R, prune, loss
+from oracle import binning, identify, project as P, render as R, prune, loss
 from paper_2411_12788_gb300 import scenes
 
 CFG = OracleConfig()
@@ -388,6 +388,71 @@ def test_keep_top_ties_by_index():
     w = np.array([0.5, 2.0, 0.5, 1.0, 0.5, 3.0])
     assert prune.keep_top(w, 0.5).tolist() == [1, 3, 5]
     assert prune.keep_top(w, 0.6).tolist() == [0, 1, 3, 5]      # ceil(3.6) = 4
+
+
+def test_keep_quantile_by_hand():
+    # M = 5 positive values, q = 0.5 -> ceil(2.5) = 3 kept: the 3, 3 and 2
+    v = np.array([0.0, 3.0, 1.0, 3.0, 2.0, 0.5])
+    assert identify.keep_quantile(v, 0.5).tolist() == [False, True, False, True, True, False]
+    # ties at the boundary go to the lower index; zeros are never kept
+    t = np.array([1.0, 2.0, 2.0, 2.0, 0.0, 1.0])
+    # (q in single precision: 0.3f * 5 = 1.50000006 -> 2; 0.4f * 5 = 2.00000003 -> 3)
+    assert np.nonzero(identify.keep_quantile(t, 0.3))[0].tolist() == [1, 2]
+    assert np.nonzero(identify.keep_quantile(t, 0.4))[0].tolist() == [1, 2, 3]
+    assert np.nonzero(identify.keep_quantile(t, 0.61))[0].tolist() == [0, 1, 2, 3]  # 4th: the lower-index 1
+    assert not identify.keep_quantile(np.zeros(7), 0.99).any()
+    assert identify.keep_quantile(t, 1.0).sum() == 5 and not identify.keep_quantile(t, 0.0).any()
+    # q is the single-precision 0.99 (0.99000000953...): 1000 values keep 991, 100 keep all 100
+    assert identify.keep_count(1000, 0.99) == 991 and identify.keep_count(100, 0.99) == 100
+    assert identify.keep_quantile(np.arange(1.0, 1001.0), 0.99).sum() == 991
+    assert not identify.keep_quantile(np.arange(1.0, 1001.0), 0.99)[:9].any()
+
+
+def test_blur_split_threshold_by_hand():
+    # theta = 2e-4 in single precision is 1.99999995e-4: 100 x 100 -> S > 1.99999995,
+    # 400 x 250 -> S > 19.9999995
+    assert identify.blur_split([0, 1, 2, 3, 10], 100, 100).tolist() == [False, False, True, True, True]
+    assert identify.blur_split([19, 20], 250, 400).tolist() == [False, True]
+    assert identify.intersected([0, 1, 5]).tolist() == [False, True, True]
+
+
+def test_critical_by_hand():
+    imax = np.array([0, 0, 1, -1, 2, 2])
+    wmax = np.array([0.9, 0.2, 0.5, 0.0, 0.1, 0.05])
+    # 5 pixels with a contributor, q = 0.5 keeps 3: w 0.9 (G0), 0.5 (G1), 0.2 (G0)
+    assert identify.critical(imax, wmax, 0.5, 4).tolist() == [True, True, False, False]
+    assert identify.critical(imax, wmax, 1.0, 4).tolist() == [True, True, True, False]
+
+
+def test_identify_on_rendered_separated_gaussians():
+    # Disjoint isotropic Gaussians: every touched pixel has one contributor, so
+    # S_i is the number of pixels with o exp(-q/2) >= 1/255 (counted by brute
+    # force here) and I_i the sum of those alphas.
+    W = H = 256
+    cam = scenes.origin_camera(W, H, 256.0)
+    cx = np.array([-0.6, 0.0, 0.6])
+    sig = np.array([0.004, 0.02, 0.06])          # world std at z = 4 -> 0.26, 1.3, 3.8 px
+    o = np.array([0.1, 0.5, 0.8])
+    means = np.stack([cx * 4 / 4, np.zeros(3), np.full(3, 4.0)], 1)
+    sc = scenes.Scene(means.astype(np.float32), np.repeat(sig[:, None], 3, 1).astype(np.float32),
+                      np.tile(np.array([1.0, 0, 0, 0], np.float32), (3, 1)), o.astype(np.float32),
+                      (np.full((3, 1, 3), 0.3, np.float32)), 0)
+    with torch.no_grad():
+        pr = P.project(sc.means, sc.scales, sc.rotations, sc.opacities, sc.sh, 0, cam)
+        out = R.render_view(pr, cam)
+    S = out["max_area"].numpy()
+    u, v = np.meshgrid(np.arange(W) + 0.5, np.arange(H) + 0.5)
+    for i in range(3):
+        m = pr["mean2d"][i].numpy()
+        A, B, C = pr["conic"][i].numpy()
+        dx, dy = u - m[0], v - m[1]
+        a = o[i] * np.exp(-0.5 * (A * dx * dx + 2 * B * dx * dy + C * dy * dy))
+        assert S[i] == np.sum(a >= 1 / 255)
+    # threshold 2e-4 * 256^2 = 13.1 px: the two larger ones are blur-split candidates
+    assert identify.blur_split(S, H, W).tolist() == [False, True, True]
+    I = out["weight_sum"].numpy()
+    vis = identify.visible(I, 0.5)                 # ceil(1.5) = 2 of 3
+    assert vis.tolist() == (I >= np.sort(I)[1]).tolist()
 
 
 def test_l1_loss_closed_form():
