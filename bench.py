@@ -278,6 +278,7 @@ def run_ours(args, rank, world):
         peaks = {"hbm_gbs": 6800.0, "note": "fallback"}
     rl = roofline(kt, st, args.steps, peaks, ck)
 
+    strategies = None if args.no_culling else run_strategies(st)
     culling = None if args.no_culling else run_culling(st, args, sec_max * 1e3 / args.steps)
     e2e = None
     if not args.no_e2e:
@@ -296,7 +297,7 @@ def run_ours(args, rank, world):
                        "l2": "inputs larger than L2 (236 MB scene, 1.5 GB workspace)",
                        "parallelism": f"replicas x{world}"},
             "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
-            "serving": serving, "dense_phase": dense, "culling": culling,
+            "serving": serving, "dense_phase": dense, "culling": culling, "strategies": strategies,
             "clocks": ck, "kernels": kt}
     return line
 
@@ -341,6 +342,47 @@ def run_culling(st: Step, args, ms_unculled: float) -> dict:
             "mpix_per_s_culled": st.pixels / ms / 1e3, "entries_unculled": entries, "entries_culled": culled_entries,
             "note": "visibility: keep quantile 0.99 of the positive I_i per view; the masked step renders only "
                     "the visible (view, Gaussian) items"}
+
+
+def run_strategies(st: Step, reps: int = 5) -> dict:
+    """The sampling kernels of the reorganisation on the step's own outputs:
+    primitive sampling of half of the Gaussians with I_i > 0 by P_i ~ I_i
+    (Sec. 4.3; I_i summed over the 8 views) and depth-reinitialization seeds
+    of 10 % of each view's pixels (Sec. 4.2).  Mean of `reps` calls each,
+    CUDA events."""
+    import torch
+    r = st.raster
+    n = st.g.n
+    I = st.grads["weight_sum"].view(len(st.cams), n).sum(0)
+    g = torch.Generator(device="cuda").manual_seed(7)
+    E = -torch.log(1.0 - torch.rand(n, device="cuda", generator=g))      # Exp(1) draws
+    k = int((I > 0).sum().item()) // 2
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    r.sample_gaussians(I, E, k)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        kept = r.sample_gaussians(I, E, k)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    sample_ms = e0.elapsed_time(e1) / reps
+    us = [1.0 - torch.rand(int(c.width) * int(c.height), device="cuda", generator=g) for c in st.cams]
+    ks = [int(c.width) * int(c.height) // 10 for c in st.cams]
+    e0.record(stream)
+    drawn = 0
+    for _ in range(reps):
+        for v in range(len(st.cams)):
+            off = int(st.plan.pixel_base[v])
+            tgt = st.target[3 * off: 3 * int(st.plan.pixel_base[v + 1])]
+            drawn += int(r.depth_points(st.plan, v, st.outs["depth"], st.outs["imax"], tgt, us[v],
+                                        ks[v])["points"].shape[0])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return {"sample_gaussians_ms": sample_ms, "sampled": int(kept.numel()), "of_positive": 2 * k,
+            "depth_points_ms_8_views": e0.elapsed_time(e1) / reps, "depth_points_per_call": drawn // reps,
+            "note": "depth_points includes one host read of the drawn count per view (the Python binding "
+                    "slices its outputs)"}
 
 
 def run_e2e(st: Step, args, world) -> dict:

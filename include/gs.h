@@ -302,6 +302,44 @@ gs_status gs_identify(const gs_plan* plan, const gs_config_identify* cfg, const 
                       uint8_t* flags, uint8_t* visible_mask, uint32_t* counts,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* ---- sampling (Sec. 4.2, 4.3) ------------------------------------------ */
+
+/* Bytes of the workspace gs_sample_gaussians needs for n Gaussians. */
+size_t gs_sample_workspace_size(int64_t n);
+
+/* Primitive sampling (Sec. 4.3): k Gaussians drawn without replacement with
+ * probability proportional to the importance I_i (P_i = I_i / sum I), by
+ * exponential clocks (Efraimidis and Spirakis): the caller draws
+ * expo_i ~ Exp(1) (> 0), and the k largest keys I_i / expo_i (IEEE FP32
+ * division) are kept, ties to the lower index.  Gaussians with I_i = 0 are
+ * never drawn: K = min(k, #(I_i > 0)) indices are written to keep_idx
+ * (device [k], ascending) and K to *k_out (device, nullable).
+ *   importance, expo: device [n]; 0 <= n < 2^32; workspace 256-byte aligned.
+ * Asynchronous. */
+gs_status gs_sample_gaussians(const float* importance, const float* expo, int64_t n, int64_t k,
+                              uint32_t* keep_idx, uint32_t* k_out, void* ws, size_t ws_bytes,
+                              void* stream);
+
+/* Bytes of the workspace gs_depth_points needs for the plan's largest view. */
+size_t gs_depth_points_workspace_size(const gs_plan* plan);
+
+/* Depth reinitialization seeds (Sec. 4.2): of the pixels of `view` that have
+ * a maximum contributor (imax >= 0) and d^mid > 0, K = min(k, #such) are drawn
+ * uniformly without replacement -- the K largest of the caller's uniform
+ * draws u (device [H W] of that view, values in (0, 1]), ties to the lower
+ * pixel index -- and reprojected: p_c = d ((x + 0.5 - cx) / fx,
+ * (y + 0.5 - cy) / fy, 1), world point R^T (p_c - t), colour from the
+ * target image.
+ *   depth, imax: device [total_pixels], outputs of gs_render_fwd for the plan
+ *   target: device planar [3][H][W] image of that view
+ *   points, colours: device [k][3]; pixel_idx: device [k] (view-local pixel
+ *   index y W + x, ascending); rows >= K are not written; K -> *k_out
+ *   (device, nullable).
+ * Asynchronous. */
+gs_status gs_depth_points(const gs_plan* plan, int32_t view, const float* depth, const int32_t* imax,
+                          const float* target, const float* u, int64_t k, float* points, float* colours,
+                          uint32_t* pixel_idx, uint32_t* k_out, void* ws, size_t ws_bytes, void* stream);
+
 /* ---- training-step helpers ------------------------------------------- */
 
 /* Mean absolute error over `count` elements and its gradient (the L1 term

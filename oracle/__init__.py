@@ -15,6 +15,7 @@ definitions:
     depth sum_i w_i d_i; the maximum-contribution area S_i.
   * Sec. 4.1, 4.3, 5.1, 5.2: blur-split candidates, intersected, visible and
     critical Gaussians of a rendered view.
+  * Sec. 4.2, 4.3: depth-reinitialization seeds and importance sampling.
 Gradients are the exact derivatives of this forward, taken by torch.autograd.
 
 Module map:
@@ -23,9 +24,10 @@ Module map:
   oracle.binning   step B: tile lists, sort order and tile ranges
   oracle.prune     top-fraction selection by blending weight
   oracle.identify  per-view selections of Gaussians (Sec. 4-5)
+  oracle.sampling  primitive sampling and depth-reinitialization seeds
   oracle.loss      photometric losses used by the training step
 """
 from .config import OracleConfig
-from . import project, render, binning, prune, loss, identify
+from . import project, render, binning, prune, loss, identify, sampling
 
-__all__ = ["OracleConfig", "project", "render", "binning", "prune", "loss", "identify"]
+__all__ = ["OracleConfig", "project", "render", "binning", "prune", "loss", "identify", "sampling"]

@@ -12,6 +12,15 @@
 //   the M positive values keeps the ceil(q M) largest, ties to the lower
 //   index (the same rule as the pruning); K is computed on the device.
 //
+// * Primitive sampling (Sec. 4.3): k Gaussians drawn without replacement
+//   with probabilities proportional to I_i, by exponential clocks (the
+//   method of Efraimidis and Spirakis): with E_i ~ Exp(1) supplied by the
+//   caller, keep the k largest I_i / E_i.
+// * Depth reinitialization (Sec. 4.2): k pixels of a view drawn uniformly
+//   without replacement among those with a maximum contributor and a
+//   positive d^mid (the k largest of the caller's uniform draws), their
+//   depth reprojected to world points and coloured from the target image.
+//
 // Selection is an MSD radix select on the bit patterns of the (non-negative)
 // values, which order like the values: four passes each histogram the next
 // 8 bits of the keys that still match the prefix found so far, and a single
@@ -91,7 +100,7 @@ __global__ void keep_flags_kernel(const uint32_t* __restrict__ keys, int64_t n, 
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
   const uint32_t k = keys[i], t = st->prefix;
-  flag[i] = (k > t || (k == t && tie_rank[i] < st->k_rem)) ? 1u : 0u;
+  flag[i] = (st->k_rem > 0 && (k > t || (k == t && tie_rank[i] < st->k_rem))) ? 1u : 0u;
 }
 
 __global__ void scatter_kept_kernel(const uint32_t* __restrict__ flag, const uint32_t* __restrict__ pos, int64_t n,
@@ -217,8 +226,59 @@ __global__ void __launch_bounds__(256) identify_critical_kernel(const uint32_t* 
   if (count && !(old & bit)) atomicAdd(count, 1u);
 }
 
+// key_i = I_i / E_i (IEEE division), 0 where I_i is 0
+__global__ void sampling_keys_kernel(const float* __restrict__ importance, const float* __restrict__ expo, int64_t n,
+                                     float* __restrict__ keys) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) keys[i] = __fdiv_rn(importance[i], expo[i]);
+}
+
+// key = u for pixels with a maximum contributor and d^mid > 0, else 0
+__global__ void depth_point_keys_kernel(const float* __restrict__ depth, const int32_t* __restrict__ imax,
+                                        const float* __restrict__ u, int64_t n, float* __restrict__ keys) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) keys[i] = (imax[i] >= 0 && depth[i] > 0.f) ? u[i] : 0.f;
+}
+
+// K = min(k, #positive keys)
+__global__ void select_init_count_kernel(SelectState* st, const uint32_t* __restrict__ count, int64_t k,
+                                         uint32_t* __restrict__ k_out) {
+  const uint32_t m = *count;
+  const uint32_t kk = (uint32_t)((int64_t)m < k ? (int64_t)m : k);
+  *st = SelectState{0u, 0u, kk, 0u};
+  if (k_out) *k_out = kk;
+}
+
+// Reprojection of the kept pixels: p_c = d ((x + 0.5 - cx) / fx,
+// (y + 0.5 - cy) / fy, 1), world point R^T (p_c - t); colour from the
+// view's planar target image.
+struct CamDev {
+  float R[9], t[3], fx, fy, cx, cy;
+  int width, height;
+};
+
+__global__ void depth_points_kernel(const uint32_t* __restrict__ idx, const uint32_t* __restrict__ k_dev,
+                                    const float* __restrict__ depth, const float* __restrict__ image, CamDev cam,
+                                    float* __restrict__ points, float* __restrict__ colours) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= (int64_t)*k_dev) return;
+  const uint32_t p = idx[r];
+  const int x = (int)(p % (uint32_t)cam.width), y = (int)(p / (uint32_t)cam.width);
+  const float d = depth[p];
+  const float cx = d * (((float)x + 0.5f - cam.cx) / cam.fx);
+  const float cy = d * (((float)y + 0.5f - cam.cy) / cam.fy);
+  const float a = cx - cam.t[0], b = cy - cam.t[1], c = d - cam.t[2];
+  points[3 * r + 0] = cam.R[0] * a + cam.R[3] * b + cam.R[6] * c;
+  points[3 * r + 1] = cam.R[1] * a + cam.R[4] * b + cam.R[7] * c;
+  points[3 * r + 2] = cam.R[2] * a + cam.R[5] * b + cam.R[8] * c;
+  const int64_t hw = (int64_t)cam.width * cam.height;
+  colours[3 * r + 0] = image[p];
+  colours[3 * r + 1] = image[hw + p];
+  colours[3 * r + 2] = image[2 * hw + p];
+}
+
 struct SelectLayout {
-  size_t state, hist, count, flag, rank, pos, scan_blocks, total_dev, total;
+  size_t state, hist, count, k_dev, flag, rank, pos, keys, scan_blocks, total_dev, total;
 };
 
 SelectLayout select_layout(int64_t n) {
@@ -233,10 +293,12 @@ SelectLayout select_layout(int64_t n) {
   L.state = take(sizeof(SelectState));
   L.hist = take(256 * 4);
   L.count = take(4);
+  L.k_dev = take(4);
   L.total_dev = take(8);
   L.flag = take(4 * m);
   L.rank = take(4 * m);
   L.pos = take(4 * m);
+  L.keys = take(4 * m);
   L.scan_blocks = take(scan_block_bytes((int64_t)m));
   L.total = o;
   return L;
@@ -246,6 +308,8 @@ struct SelectBufs {
   SelectState* st;
   uint32_t* hist;
   uint32_t* count;
+  uint32_t* k_dev;
+  float* keys;
   uint32_t* flag;
   uint32_t* rank;
   uint32_t* pos;
@@ -256,7 +320,8 @@ struct SelectBufs {
 SelectBufs select_bufs(void* ws, const SelectLayout& L) {
   char* base = static_cast<char*>(ws);
   return SelectBufs{reinterpret_cast<SelectState*>(base + L.state), reinterpret_cast<uint32_t*>(base + L.hist),
-                    reinterpret_cast<uint32_t*>(base + L.count),     reinterpret_cast<uint32_t*>(base + L.flag),
+                    reinterpret_cast<uint32_t*>(base + L.count),     reinterpret_cast<uint32_t*>(base + L.k_dev),
+                    reinterpret_cast<float*>(base + L.keys),         reinterpret_cast<uint32_t*>(base + L.flag),
                     reinterpret_cast<uint32_t*>(base + L.rank),      reinterpret_cast<uint32_t*>(base + L.pos),
                     reinterpret_cast<uint64_t*>(base + L.scan_blocks),
                     reinterpret_cast<unsigned long long*>(base + L.total_dev)};
@@ -278,6 +343,29 @@ cudaError_t select_threshold(const uint32_t* keys, int64_t n, const SelectBufs& 
   e = cudaGetLastError();
   if (e == cudaSuccess) e = gather_exclusive_scan(B.flag, nullptr, B.rank, n, B.sb, B.tot, stream);
   return e;
+}
+
+// keep_idx[0..K) <- the kept indices in ascending order (after select_threshold).
+cudaError_t select_compact(const uint32_t* keys, int64_t n, const SelectBufs& B, uint32_t* keep_idx,
+                           cudaStream_t stream) {
+  const int blocks = ceil_div(n, 256);
+  GS_TIMED("select_keep", stream, (keep_flags_kernel<<<blocks, 256, 0, stream>>>(keys, n, B.st, B.rank, B.flag)));
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = gather_exclusive_scan(B.flag, nullptr, B.pos, n, B.sb, B.tot, stream);
+  if (e == cudaSuccess)
+    GS_TIMED("select_scatter", stream, (scatter_kept_kernel<<<blocks, 256, 0, stream>>>(B.flag, B.pos, n, keep_idx)));
+  return cudaGetLastError();
+}
+
+// B.st <- K = min(k, #(keys > 0)), also written to B.k_dev.
+cudaError_t select_init_count(const uint32_t* keys, int64_t n, int64_t k, const SelectBufs& B, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(B.count, 0, 4, stream);
+  if (e != cudaSuccess) return e;
+  GS_TIMED("select_count", stream,
+           (count_positive_kernel<<<std::max(1, std::min(ceil_div(n, 256), 4 * 152)), 256, 0, stream>>>(keys, n,
+                                                                                                        B.count)));
+  GS_TIMED("select_init", stream, (select_init_count_kernel<<<1, 1, 0, stream>>>(B.st, B.count, k, B.k_dev)));
+  return cudaGetLastError();
 }
 
 // B.st <- k = ceil(q * #(keys > 0)).
@@ -426,4 +514,84 @@ extern "C" gs_status gs_gather_scene(const gs_scene* src, const uint32_t* idx, i
              (gather_rows_kernel<<<ceil_div(total, 256), 256, 0, stream>>>(p.s, idx, k, p.w, p.d)));
   }
   return cudaGetLastError() == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+extern "C" size_t gs_sample_workspace_size(int64_t n) { return n < 0 ? 0 : select_layout(n).total; }
+
+extern "C" gs_status gs_sample_gaussians(const float* importance, const float* expo, int64_t n, int64_t k,
+                                         uint32_t* keep_idx, uint32_t* k_out, void* ws, size_t ws_bytes,
+                                         void* stream_) {
+  if (n < 0 || k < 0 || n >= ((int64_t)1 << 32) || (n > 0 && (!importance || !expo)) || (k > 0 && !keep_idx) ||
+      !ws || (reinterpret_cast<uintptr_t>(ws) & 255))
+    return GS_ERR_INVALID_ARG;
+  const SelectLayout L = select_layout(n);
+  if (ws_bytes < L.total) return GS_ERR_CAPACITY;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const SelectBufs B = select_bufs(ws, L);
+  cudaError_t e = cudaSuccess;
+  if (n == 0 || k == 0) {
+    if (k_out) e = cudaMemsetAsync(k_out, 0, 4, stream);
+    return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+  }
+  GS_TIMED("sample_keys", stream,
+           (sampling_keys_kernel<<<ceil_div(n, 256), 256, 0, stream>>>(importance, expo, n, B.keys)));
+  const uint32_t* keys = reinterpret_cast<const uint32_t*>(B.keys);
+  e = select_init_count(keys, n, k, B, stream);
+  if (e == cudaSuccess) e = select_threshold(keys, n, B, stream);
+  if (e == cudaSuccess) e = select_compact(keys, n, B, keep_idx, stream);
+  if (e == cudaSuccess && k_out) e = cudaMemcpyAsync(k_out, B.k_dev, 4, cudaMemcpyDeviceToDevice, stream);
+  return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+extern "C" size_t gs_depth_points_workspace_size(const gs_plan* plan) {
+  if (!plan || plan->n_views < 1 || plan->n_views > GS_MAX_VIEWS) return 0;
+  int64_t m = 1;
+  for (int v = 0; v < plan->n_views; ++v) m = std::max(m, plan->pixel_base[v + 1] - plan->pixel_base[v]);
+  return select_layout(m).total;
+}
+
+extern "C" gs_status gs_depth_points(const gs_plan* plan, int32_t view, const float* depth, const int32_t* imax,
+                                     const float* target, const float* u, int64_t k, float* points, float* colours,
+                                     uint32_t* pixel_idx, uint32_t* k_out, void* ws, size_t ws_bytes,
+                                     void* stream_) {
+  if (!plan || view < 0 || view >= plan->n_views || plan->n_views > GS_MAX_VIEWS || k < 0 || !ws ||
+      (reinterpret_cast<uintptr_t>(ws) & 255))
+    return GS_ERR_INVALID_ARG;
+  const int64_t p0 = plan->pixel_base[view], np = plan->pixel_base[view + 1] - p0;
+  if (np >= ((int64_t)1 << 32)) return GS_ERR_INVALID_ARG;
+  if (np > 0 && (!depth || !imax || !target || !u)) return GS_ERR_INVALID_ARG;
+  if (k > 0 && (!points || !colours || !pixel_idx)) return GS_ERR_INVALID_ARG;
+  const SelectLayout L = select_layout(std::max<int64_t>(np, 1));
+  if (ws_bytes < L.total) return GS_ERR_CAPACITY;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  cudaError_t e = cudaSuccess;
+  if (np == 0 || k == 0) {
+    if (k_out) e = cudaMemsetAsync(k_out, 0, 4, stream);
+    return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+  }
+  const SelectBufs B = select_bufs(ws, L);
+  GS_TIMED("depth_point_keys", stream,
+           (depth_point_keys_kernel<<<ceil_div(np, 256), 256, 0, stream>>>(depth + p0, imax + p0, u, np, B.keys)));
+  const uint32_t* keys = reinterpret_cast<const uint32_t*>(B.keys);
+  e = select_init_count(keys, np, k, B, stream);
+  if (e == cudaSuccess) e = select_threshold(keys, np, B, stream);
+  if (e == cudaSuccess) e = select_compact(keys, np, B, pixel_idx, stream);
+  if (e == cudaSuccess) {
+    const gs_camera& c = plan->cams[view];
+    CamDev cam;
+    for (int i = 0; i < 9; ++i) cam.R[i] = c.R[i];
+    for (int i = 0; i < 3; ++i) cam.t[i] = c.t[i];
+    cam.fx = c.fx;
+    cam.fy = c.fy;
+    cam.cx = c.cx;
+    cam.cy = c.cy;
+    cam.width = c.width;
+    cam.height = c.height;
+    GS_TIMED("depth_points", stream,
+             (depth_points_kernel<<<ceil_div(std::min<int64_t>(k, np), 256), 256, 0, stream>>>(
+                 pixel_idx, B.k_dev, depth + p0, target, cam, points, colours)));
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && k_out) e = cudaMemcpyAsync(k_out, B.k_dev, 4, cudaMemcpyDeviceToDevice, stream);
+  return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

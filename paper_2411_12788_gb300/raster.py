@@ -180,6 +180,39 @@ def identify(plan, weight_sum: torch.Tensor, max_area: torch.Tensor, imax: torch
     return {"flags": flags[:I], "visible_mask": vis[:I], "counts": counts}
 
 
+def sample_gaussians(importance: torch.Tensor, expo: torch.Tensor, k: int, stream=None) -> torch.Tensor:
+    """Primitive sampling (gs_sample_gaussians): ascending indices of k
+    Gaussians drawn without replacement with P_i proportional to I_i, given
+    expo ~ Exp(1); fewer if fewer have I_i > 0."""
+    n = importance.numel()
+    dev = importance.device
+    ws = torch.empty(max(int(lib().gs_sample_workspace_size(n)), 1), dtype=torch.uint8, device=dev)
+    keep = torch.empty(max(k, 1), dtype=torch.int32, device=dev)
+    kk = torch.zeros(1, dtype=torch.int32, device=dev)
+    check("gs_sample_gaussians", lib().gs_sample_gaussians(_ptr(importance), _ptr(expo), n, int(k), _ptr(keep),
+                                                           _ptr(kk), _ptr(ws), ws.numel(), _stream(stream)))
+    return keep[: int(kk.item())]
+
+
+def depth_points(plan, view: int, depth: torch.Tensor, imax: torch.Tensor, target: torch.Tensor, u: torch.Tensor,
+                 k: int, stream=None) -> dict:
+    """Depth reinitialization seeds of one view (gs_depth_points): world
+    points, colours and view-local pixel indices of k pixels drawn uniformly
+    (by the largest u) among those with a contributor and d^mid > 0."""
+    dev = depth.device
+    ws = torch.empty(max(int(lib().gs_depth_points_workspace_size(C.byref(plan))), 1), dtype=torch.uint8,
+                     device=dev)
+    pts = torch.empty((max(k, 1), 3), device=dev)
+    col = torch.empty((max(k, 1), 3), device=dev)
+    idx = torch.empty(max(k, 1), dtype=torch.int32, device=dev)
+    kk = torch.zeros(1, dtype=torch.int32, device=dev)
+    check("gs_depth_points", lib().gs_depth_points(C.byref(plan), int(view), _ptr(depth), _ptr(imax),
+                                                   _ptr(target), _ptr(u), int(k), _ptr(pts), _ptr(col), _ptr(idx),
+                                                   _ptr(kk), _ptr(ws), ws.numel(), _stream(stream)))
+    K = int(kk.item())
+    return {"points": pts[:K], "colours": col[:K], "pixel_idx": idx[:K]}
+
+
 def gather_scene(g: "GaussianTensors", idx: torch.Tensor, stream=None) -> "GaussianTensors":
     """A compact copy of the rows idx of every attribute (gs_gather_scene)."""
     k = int(idx.numel())

@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from oracle import OracleConfig
-from oracle import binning, identify, project as P, render as R, prune, loss
+from oracle import binning, identify, project as P, render as R, prune, loss, sampling
 from paper_2411_12788_gb300 import scenes
 
 CFG = OracleConfig()
@@ -453,6 +453,76 @@ def test_identify_on_rendered_separated_gaussians():
     I = out["weight_sum"].numpy()
     vis = identify.visible(I, 0.5)                 # ceil(1.5) = 2 of 3
     assert vis.tolist() == (I >= np.sort(I)[1]).tolist()
+
+
+def test_weighted_sample_first_draw_is_proportional():
+    # exponential clocks: the first to ring is i with probability I_i / sum I
+    rng = np.random.default_rng(3)
+    I = np.array([1.0, 2.0, 3.0, 4.0, 0.0])
+    T = 200000
+    E = rng.exponential(size=(T, 5)).astype(np.float32)
+    first = np.argmax((I.astype(np.float32) / E), axis=1)
+    freq = np.bincount(first, minlength=5) / T
+    assert np.allclose(freq, I / I.sum(), atol=4e-3)
+    # and the oracle's draw of one is that Gaussian
+    for t in range(50):
+        assert sampling.weighted_sample(I, E[t], 1).tolist() == [first[t]]
+
+
+def test_weighted_sample_two_draws_match_sequential_law():
+    # inclusion probability of i in two successive proportional draws without
+    # replacement: p_i + sum_{j != i} p_j p_i / (1 - p_j)
+    rng = np.random.default_rng(4)
+    I = np.array([5.0, 1.0, 3.0, 1.0])
+    p = I / I.sum()
+    incl = np.array([p[i] + sum(p[j] * p[i] / (1 - p[j]) for j in range(4) if j != i) for i in range(4)])
+    T = 60000
+    counts = np.zeros(4)
+    E = rng.exponential(size=(T, 4)).astype(np.float32)
+    for t in range(T):
+        counts[sampling.weighted_sample(I, E[t], 2)] += 1
+    assert np.allclose(counts / T, incl, atol=6e-3)
+
+
+def test_weighted_sample_edges():
+    I = np.array([0.0, 2.0, 0.0, 1.0, 3.0])
+    E = np.ones(5, np.float32)
+    assert sampling.weighted_sample(I, E, 10).tolist() == [1, 3, 4]      # zeros never drawn
+    assert sampling.weighted_sample(I, E, 2).tolist() == [1, 4]
+    assert sampling.weighted_sample(I, E, 0).tolist() == []
+    # equal keys: the lower index first
+    assert sampling.weighted_sample([1.0, 1.0, 1.0], np.ones(3, np.float32), 2).tolist() == [0, 1]
+
+
+def test_reprojection_inverts_the_pinhole_projection():
+    R, t = scenes.look_at((0.7, -0.4, 0.2), (0.0, 0.0, 4.0))
+    cam = scenes.fov_camera(R, t, 64, 48, 55.0)
+    rng = np.random.default_rng(5)
+    pix = rng.integers(0, 64 * 48, 40)
+    depth = np.zeros(64 * 48)
+    depth[pix] = rng.uniform(1.0, 9.0, 40)
+    P = sampling.reproject(depth, pix, cam)
+    pc = P @ np.asarray(cam.R, np.float64).T + np.asarray(cam.t, np.float64)
+    assert np.allclose(pc[:, 2], depth[pix], rtol=1e-12)
+    assert np.allclose(cam.fx * pc[:, 0] / pc[:, 2] + cam.cx, pix % 64 + 0.5, atol=1e-9)
+    assert np.allclose(cam.fy * pc[:, 1] / pc[:, 2] + cam.cy, pix // 64 + 0.5, atol=1e-9)
+
+
+def test_depth_points_draws_among_valid_pixels():
+    cam = scenes.origin_camera(8, 4, 8.0)
+    rng = np.random.default_rng(6)
+    depth = rng.uniform(1, 3, 32)
+    depth[[3, 9]] = 0.0
+    imax = np.where(np.arange(32) % 5 == 0, -1, 7)
+    u = rng.uniform(size=32)
+    target = rng.uniform(size=(3, 4, 8))
+    out = sampling.depth_points(depth, imax, target, u, cam, 6)
+    valid = (imax >= 0) & (depth > 0)
+    sel = out["pixel_idx"]
+    assert len(sel) == 6 and valid[sel].all()
+    assert u[sel].min() >= u[valid & ~np.isin(np.arange(32), sel)].max()
+    assert np.array_equal(out["colours"], target.reshape(3, -1)[:, sel].T)
+    assert len(sampling.depth_points(depth, imax, target, u, cam, 1000)["pixel_idx"]) == valid.sum()
 
 
 def test_l1_loss_closed_form():
