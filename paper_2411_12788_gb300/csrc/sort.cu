@@ -8,7 +8,8 @@
 //   * each CTA of the pass kernel takes the next tile of 3840 keys (dynamic
 //     tile id, so every predecessor tile is already running), ranks its keys
 //     stably by digit inside each warp (the lanes sharing a digit found by
-//     one ballot per digit bit), publishes its per-digit
+//     OR-ing each lane's bit into a shared word per warp and digit and
+//     reading it back), publishes its per-digit
 //     counts, and looks back over its predecessors' published counts
 //     (decoupled look-back) to find its global offset per digit; keys are
 //     then staged in shared memory in output order and written out so that
@@ -123,13 +124,16 @@ constexpr long kCopyWaitLimit = 1L << 22;
 
 __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift, int digit_bits,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift,
     const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ counter,
     uint32_t* __restrict__ lookback, uint32_t* __restrict__ status) {
   extern __shared__ __align__(16) uint32_t s_dyn[];
   uint32_t* s_keys = s_dyn;                       // keys: loaded, then in output order
   uint32_t* s_vin = s_dyn + kSortTile;            // values as loaded
   uint32_t* s_vals = s_dyn + 2 * kSortTile;       // values in output order
+  // per warp and digit: the lanes holding it (ranking only; aliases s_vals,
+  // which is written after the ranking)
+  uint32_t (*s_match)[kRadix] = reinterpret_cast<uint32_t (*)[kRadix]>(s_vals);
   __shared__ uint32_t s_warp_hist[kWarps][kRadix];
   __shared__ uint32_t s_cta_start[kRadix];
   __shared__ uint32_t s_out_base[kRadix];         // output index of the CTA's first key of each digit, minus its start
@@ -143,7 +147,10 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
     s_tile = atomicAdd(counter, 1u);
     mbar_init(&s_bar, 1);
   }
-  for (int i = tid; i < kWarps * kRadix; i += kSortThreads) (&s_warp_hist[0][0])[i] = 0;
+  for (int i = tid; i < kWarps * kRadix; i += kSortThreads) {
+    (&s_warp_hist[0][0])[i] = 0;
+    (&s_match[0][0])[i] = 0;
+  }
   __syncthreads();
   const int64_t tile = s_tile;
   const int64_t tile_start = tile * kSortTile;
@@ -185,13 +192,12 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
     const int i = warp_start + k * 32 + lane;
     const bool valid = i < count;
     const uint32_t d = (key[k] >> shift) & (kRadix - 1);
-    // lanes holding the same digit: AND over the digit's bits of the ballot
-    // of that bit (or of its complement)
-    uint32_t peers = __ballot_sync(0xffffffffu, valid);
-    for (int b = 0; b < digit_bits; ++b) {
-      const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-      peers &= ((d >> b) & 1u) ? bal : ~bal;
-    }
+    // lanes holding the same digit: each ORs its lane bit into the warp's
+    // word for its digit, then reads the word back
+    if (valid) atomicOr(&s_match[warp][d], 1u << lane);
+    __syncwarp();
+    const uint32_t peers = valid ? s_match[warp][d] : 0u;
+    __syncwarp();
     rank[k] = 0;
     if (valid) {
       int leader = __ffs(peers) - 1;
@@ -199,6 +205,7 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
       if (lane == leader) {
         before = s_warp_hist[warp][d];
         s_warp_hist[warp][d] = before + __popc(peers);
+        s_match[warp][d] = 0u;
       }
       before = __shfl_sync(peers, before, leader);
       rank[k] = before + __popc(peers & lt);
@@ -432,7 +439,7 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
   for (int p = 0; p < passes; ++p) {
     GS_TIMED(depth ? "depth_sort_onesweep" : "tile_sort_onesweep", stream,
              (radix_onesweep_kernel<<<(unsigned)tiles, kSortThreads, kOnesweepDynSmem, stream>>>(
-                 kin, vin, kout, vout, n, p * kRadixBits, std::min(kRadixBits, bits - p * kRadixBits),
+                 kin, vin, kout, vout, n, p * kRadixBits,
                  s.hist + p * kRadix, s.counters + p,
                  s.lookback + (size_t)p * tiles * kRadix, status)));
     std::swap(kin, kout);
