@@ -302,6 +302,16 @@ gs_status gs_identify(const gs_plan* plan, const gs_config_identify* cfg, const 
                       uint8_t* flags, uint8_t* visible_mask, uint32_t* counts,
                       void* ws, size_t ws_bytes, void* stream);
 
+/* Aggressive clone (Sec. 5.1): each Gaussian idx[r] (distinct indices)
+ * becomes a pair at the same centre, rotation and SH with opacity
+ * o' = 1 - sqrt(1 - o) and covariance o^2 (2 o' - o'^2 / sqrt(2))^-2 Sigma,
+ * i.e. scales multiplied by o / (2 o' - o'^2 / sqrt(2)).  dst (rows >=
+ * src->n + k, equal sh_coeffs, not overlapping src) receives src in rows
+ * [0, n) with rows idx[r] replaced by the pair's first member and the second
+ * member in row n + r.  Asynchronous. */
+gs_status gs_clone_gaussians(const gs_scene* src, const uint32_t* idx, int64_t k,
+                             const gs_scene_buf* dst, void* stream);
+
 /* ---- sampling (Sec. 4.2, 4.3) ------------------------------------------ */
 
 /* Bytes of the workspace gs_sample_gaussians needs for n Gaussians. */
@@ -348,6 +358,22 @@ gs_status gs_depth_points(const gs_plan* plan, int32_t view, const float* depth,
  * target) / count.  *loss is overwritten. */
 gs_status gs_loss_l1(const float* image, const float* target, int64_t count,
                      float* loss, float* dL_dimage, void* stream);
+
+/* Bytes of the workspace gs_loss_l1_ssim needs for the plan's views. */
+size_t gs_loss_l1_ssim_workspace_size(const gs_plan* plan);
+
+/* The 3DGS photometric objective (Sec. 6.2), fused with its gradient:
+ * *loss = (1 - lambda) L1 + lambda (1 - SSIM), L1 = mean |image - target| and
+ * SSIM = mean SSIM map, both over every pixel and channel of every view of the
+ * plan (planar [3][H][W] per view, concatenated as gs_render_fwd writes
+ * them).  SSIM per channel: 11x11 Gaussian window (sigma 1.5, normalised),
+ * zero padding, C1 = 0.01^2, C2 = 0.03^2.  dL_dimage receives dL/dimage.
+ * l1_out, ssim_out (device scalars, nullable) receive the two means.
+ * 0 <= lambda <= 1; workspace from gs_loss_l1_ssim_workspace_size.
+ * Asynchronous. */
+gs_status gs_loss_l1_ssim(const gs_plan* plan, const float* image, const float* target, float lambda,
+                          float* loss, float* dL_dimage, float* l1_out, float* ssim_out,
+                          void* ws, size_t ws_bytes, void* stream);
 
 /* ---- inspection --------------------------------------------------------- */
 

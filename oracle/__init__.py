@@ -16,6 +16,7 @@ definitions:
   * Sec. 4.1, 4.3, 5.1, 5.2: blur-split candidates, intersected, visible and
     critical Gaussians of a rendered view.
   * Sec. 4.2, 4.3: depth-reinitialization seeds and importance sampling.
+  * Sec. 5.1: the aggressive clone of critical Gaussians.
 Gradients are the exact derivatives of this forward, taken by torch.autograd.
 
 Module map:
@@ -25,9 +26,10 @@ Module map:
   oracle.prune     top-fraction selection by blending weight
   oracle.identify  per-view selections of Gaussians (Sec. 4-5)
   oracle.sampling  primitive sampling and depth-reinitialization seeds
+  oracle.densify   aggressive clone
   oracle.loss      photometric losses used by the training step
 """
 from .config import OracleConfig
-from . import project, render, binning, prune, loss, identify, sampling
+from . import project, render, binning, prune, loss, identify, sampling, densify
 
-__all__ = ["OracleConfig", "project", "render", "binning", "prune", "loss", "identify", "sampling"]
+__all__ = ["OracleConfig", "project", "render", "binning", "prune", "loss", "identify", "sampling", "densify"]

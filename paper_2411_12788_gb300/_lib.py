@@ -112,6 +112,7 @@ SIGNATURES = {
     "gs_identify": (C.c_int, [C.POINTER(Plan), C.POINTER(ConfigIdentify), C.c_void_p, C.c_void_p, C.c_void_p,
                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t,
                               C.c_void_p]),
+    "gs_clone_gaussians": (C.c_int, [C.POINTER(Scene), C.c_void_p, C.c_int64, C.POINTER(SceneBuf), C.c_void_p]),
     "gs_sample_workspace_size": (C.c_size_t, [C.c_int64]),
     "gs_sample_gaussians": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p,
                                       C.c_void_p, C.c_size_t, C.c_void_p]),
@@ -119,6 +120,9 @@ SIGNATURES = {
     "gs_depth_points": (C.c_int, [C.POINTER(Plan), C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                   C.c_size_t, C.c_void_p]),
+    "gs_loss_l1_ssim_workspace_size": (C.c_size_t, [C.POINTER(Plan)]),
+    "gs_loss_l1_ssim": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.c_void_p, C.c_float, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "gs_loss_l1": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
     "gs_device_status": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.c_void_p]),
     "gs_inspect_preprocess": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.POINTER(PreprocessView)]),

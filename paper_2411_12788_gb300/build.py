@@ -17,7 +17,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgs.so")
-SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "binning.cu", "render.cu", "timing.cu", "noalloc.cu", "select.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "binning.cu", "render.cu", "timing.cu", "noalloc.cu", "select.cu", "ssim.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]

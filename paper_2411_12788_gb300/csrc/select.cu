@@ -21,6 +21,10 @@
 //   positive d^mid (the k largest of the caller's uniform draws), their
 //   depth reprojected to world points and coloured from the target image.
 //
+// * Aggressive clone (Sec. 5.1): each listed Gaussian becomes two at the same
+//   centre with opacity 1 - sqrt(1 - o) and covariance scaled by
+//   o^2 (2 o' - o'^2 / sqrt 2)^-2 (scales by its square root).
+//
 // Selection is an MSD radix select on the bit patterns of the (non-negative)
 // values, which order like the values: four passes each histogram the next
 // 8 bits of the keys that still match the prefix found so far, and a single
@@ -593,5 +597,67 @@ extern "C" gs_status gs_depth_points(const gs_plan* plan, int32_t view, const fl
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && k_out) e = cudaMemcpyAsync(k_out, B.k_dev, 4, cudaMemcpyDeviceToDevice, stream);
+  return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
+}
+
+namespace gs {
+namespace {
+
+// Rows [0, n) of dst are src; row idx[r] and row n + r become the clone pair
+// of Gaussian idx[r].
+__global__ void clone_pairs_kernel(const float* __restrict__ src_op, const float* __restrict__ src_sc,
+                                   const uint32_t* __restrict__ idx, int64_t n, int64_t k,
+                                   float* __restrict__ dst_op, float* __restrict__ dst_sc) {
+  const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= k) return;
+  const int64_t i = idx[r];
+  const float o = src_op[i];
+  const float on = o / (1.f + sqrtf(1.f - o));                        // = 1 - sqrt(1 - o), no cancellation
+  const float f = o / (2.f * on - on * on * 0.70710678118654752f);   // sqrt of the covariance factor
+  dst_op[i] = on;
+  dst_op[n + r] = on;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float s = src_sc[3 * i + c] * f;
+    dst_sc[3 * i + c] = s;
+    dst_sc[3 * (n + r) + c] = s;
+  }
+}
+
+}  // namespace
+}  // namespace gs
+
+extern "C" gs_status gs_clone_gaussians(const gs_scene* src, const uint32_t* idx, int64_t k, const gs_scene_buf* dst,
+                                        void* stream_) {
+  if (!src || !dst || k < 0 || src->n < 0 || (k > 0 && !idx) || dst->n < src->n + k ||
+      src->sh_coeffs != dst->sh_coeffs || !src->means || !dst->means || !src->scales || !dst->scales ||
+      !src->rotations || !dst->rotations || !src->opacities || !dst->opacities || !src->sh || !dst->sh)
+    return GS_ERR_INVALID_ARG;
+  if (src->means == dst->means || src->scales == dst->scales || src->opacities == dst->opacities)
+    return GS_ERR_INVALID_ARG;                      // out of place only
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const int64_t n = src->n;
+  struct Part {
+    const float* s;
+    float* d;
+    int w;
+  } parts[5] = {{src->means, dst->means, 3},
+                {src->scales, dst->scales, 3},
+                {src->rotations, dst->rotations, 4},
+                {src->opacities, dst->opacities, 1},
+                {src->sh, dst->sh, 3 * src->sh_coeffs}};
+  cudaError_t e = cudaSuccess;
+  for (const Part& p : parts) {
+    if (n > 0 && e == cudaSuccess)
+      e = cudaMemcpyAsync(p.d, p.s, (size_t)n * p.w * sizeof(float), cudaMemcpyDeviceToDevice, stream);
+    // the clones' rows: the unchanged attributes of the source row
+    if (k > 0 && e == cudaSuccess)
+      GS_TIMED("clone_rows", stream, (gather_rows_kernel<<<ceil_div(k * p.w, 256), 256, 0, stream>>>(
+                                          p.s, idx, k, p.w, p.d + (size_t)n * p.w)));
+  }
+  if (k > 0 && e == cudaSuccess)
+    GS_TIMED("clone_pairs", stream, (clone_pairs_kernel<<<ceil_div(k, 256), 256, 0, stream>>>(
+                                         src->opacities, src->scales, idx, n, k, dst->opacities, dst->scales)));
+  if (e == cudaSuccess) e = cudaGetLastError();
   return e == cudaSuccess ? GS_OK : GS_ERR_CUDA;
 }

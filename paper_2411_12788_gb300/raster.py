@@ -140,6 +140,22 @@ def loss_l1(image, target, loss, dL_dimage, stream=None) -> None:
                                          _ptr(dL_dimage), _stream(stream)))
 
 
+def loss_l1_ssim(plan, image, target, loss, dL_dimage, lam: float = 0.2, ws=None, l1_ssim=None,
+                 stream=None) -> torch.Tensor:
+    """(1 - lam) L1 + lam (1 - SSIM) and its gradient (gs_loss_l1_ssim); the
+    workspace is allocated if not given.  l1_ssim: optional [2] device
+    tensor receiving the two means."""
+    if ws is None:
+        ws = torch.empty(max(int(lib().gs_loss_l1_ssim_workspace_size(C.byref(plan))), 1), dtype=torch.uint8,
+                         device=image.device)
+    l1p = _ptr(l1_ssim) if l1_ssim is not None else None
+    ssp = l1_ssim.data_ptr() + 4 if l1_ssim is not None else None
+    check("gs_loss_l1_ssim", lib().gs_loss_l1_ssim(C.byref(plan), _ptr(image), _ptr(target), C.c_float(lam),
+                                                   _ptr(loss), _ptr(dL_dimage), l1p, ssp, _ptr(ws), ws.numel(),
+                                                   _stream(stream)))
+    return ws
+
+
 def prune_select(importance: torch.Tensor, k: int, stream=None) -> torch.Tensor:
     """Indices (ascending, int32 storage of uint32) of the k largest
     importances, ties to the lower index (gs_prune_select)."""
@@ -178,6 +194,21 @@ def identify(plan, weight_sum: torch.Tensor, max_area: torch.Tensor, imax: torch
                                            _ptr(wmax), _ptr(flags), _ptr(vis), _ptr(counts), _ptr(ws), ws.numel(),
                                            _stream(stream)))
     return {"flags": flags[:I], "visible_mask": vis[:I], "counts": counts}
+
+
+def clone_gaussians(g: "GaussianTensors", idx: torch.Tensor, stream=None) -> "GaussianTensors":
+    """Aggressive clone (gs_clone_gaussians): a scene of n + k rows in which
+    each Gaussian idx[r] is replaced by a clone pair (rows idx[r], n + r)."""
+    n, k = g.n, int(idx.numel())
+    dev = g.means.device
+    out = GaussianTensors(torch.empty((n + k, 3), device=dev), torch.empty((n + k, 3), device=dev),
+                          torch.empty((n + k, 4), device=dev), torch.empty((n + k,), device=dev),
+                          torch.empty((n + k,) + tuple(g.sh.shape[1:]), device=dev), g.sh_degree)
+    d = _lib.SceneBuf(out.means.data_ptr(), out.scales.data_ptr(), out.rotations.data_ptr(),
+                      out.opacities.data_ptr(), out.sh.data_ptr(), n + k, g.sh_degree, int(g.sh.shape[1]))
+    check("gs_clone_gaussians", lib().gs_clone_gaussians(C.byref(g.struct()), _ptr(idx), k, C.byref(d),
+                                                         _stream(stream)))
+    return out
 
 
 def sample_gaussians(importance: torch.Tensor, expo: torch.Tensor, k: int, stream=None) -> torch.Tensor:

@@ -8,7 +8,7 @@ import pytest
 import torch
 
 from oracle import OracleConfig
-from oracle import binning, identify, project as P, render as R, prune, loss, sampling
+from oracle import binning, densify, identify, project as P, render as R, prune, loss, sampling
 from paper_2411_12788_gb300 import scenes
 
 CFG = OracleConfig()
@@ -523,6 +523,93 @@ def test_depth_points_draws_among_valid_pixels():
     assert u[sel].min() >= u[valid & ~np.isin(np.arange(32), sel)].max()
     assert np.array_equal(out["colours"], target.reshape(3, -1)[:, sel].T)
     assert len(sampling.depth_points(depth, imax, target, u, cam, 1000)["pixel_idx"]) == valid.sum()
+
+
+@pytest.mark.parametrize("o", [0.02, 0.3, 0.75, 0.99])
+def test_clone_pair_keeps_peak_opacity_and_line_integral(o):
+    # two coincident clones composite to 1 - (1 - o')^2 = o at the centre
+    on = densify.clone_opacity(o)
+    assert abs(1 - (1 - on) ** 2 - o) < 1e-14
+    # and along a line through the centre (1-D profile g(x) = exp(-x^2 / 2s^2))
+    # the pair's composited opacity integrates to the original's
+    s = 1.7
+    f = densify.clone_scale_factor(o)
+    x = np.linspace(-40, 40, 400001)
+    g1 = np.exp(-0.5 * (x / (f * s)) ** 2)
+    pair = 1 - (1 - on * g1) ** 2
+    assert abs(np.trapezoid(pair, x) - np.trapezoid(o * np.exp(-0.5 * (x / s) ** 2), x)) < 1e-9
+
+
+def test_clone_by_hand():
+    # o = 0.75: o' = 0.5, scale factor 0.75 / (1 - 0.25 / sqrt 2)
+    assert abs(densify.clone_opacity(0.75) - 0.5) < 1e-15
+    assert abs(densify.clone_scale_factor(0.75) - 0.75 / (1 - 0.25 / np.sqrt(2))) < 1e-15
+    m = np.arange(12.0).reshape(4, 3)
+    out = densify.clone(m, np.ones((4, 3)), np.tile([1.0, 0, 0, 0], (4, 1)), np.array([0.1, 0.75, 0.2, 0.5]),
+                        np.zeros((4, 1, 3)), [1, 3])
+    assert out["means"].shape == (6, 3) and np.array_equal(out["means"][4], m[1]) and np.array_equal(out["means"][5], m[3])
+    assert np.allclose(out["opacities"], [0.1, 0.5, 0.2, 1 - np.sqrt(0.5), 0.5, 1 - np.sqrt(0.5)])
+    assert np.allclose(out["scales"][[0, 2]], 1.0)
+
+
+def test_ssim_window_closed_form():
+    w = loss.gaussian_window()
+    g = w[5] / w[5].sum()
+    assert abs(float(w.sum()) - 1) < 1e-14 and torch.allclose(w, w.T) and torch.allclose(g, g.flip(0))
+    assert abs(float(g[5] / g[6]) - np.exp(1 / 4.5)) < 1e-12 and abs(float(g[5] / g[0]) - np.exp(25 / 4.5)) < 1e-9
+
+
+def test_ssim_of_identical_images_is_one():
+    x = torch.rand(3, 23, 17, dtype=torch.float64, generator=torch.Generator().manual_seed(1))
+    assert torch.allclose(loss.ssim_map(x, x), torch.ones(3, 23, 17, dtype=torch.float64), atol=1e-14)
+
+
+def test_ssim_constant_images_closed_form():
+    # away from the border (window fully inside) mu = a, b and every sigma is 0
+    a, b = 0.3, 0.7
+    s = loss.ssim_map(torch.full((1, 20, 20), a, dtype=torch.float64), torch.full((1, 20, 20), b, dtype=torch.float64))
+    ref = (2 * a * b + loss.SSIM_C1) / (a * a + b * b + loss.SSIM_C1)
+    assert torch.allclose(s[0, 5:15, 5:15], torch.full((10, 10), ref, dtype=torch.float64), atol=1e-14)
+
+
+def test_ssim_matches_explicit_window_sums():
+    # brute force: every window sum written out pixel by pixel, zero padding
+    rng = np.random.default_rng(2)
+    x, y = rng.uniform(size=(2, 1, 9, 13))
+    g1 = np.exp(-np.arange(-5, 6) ** 2 / 4.5)
+    g1 /= g1.sum()
+    H, W = 9, 13
+    ref = np.zeros((H, W))
+    for i in range(H):
+        for j in range(W):
+            m = np.zeros(5)
+            for di in range(-5, 6):
+                for dj in range(-5, 6):
+                    u, v = i + di, j + dj
+                    if 0 <= u < H and 0 <= v < W:
+                        w = g1[di + 5] * g1[dj + 5]
+                        xv, yv = x[0, u, v], y[0, u, v]
+                        m += w * np.array([xv, yv, xv * xv, yv * yv, xv * yv])
+            mx, my, exx, eyy, exy = m
+            ref[i, j] = ((2 * mx * my + 1e-4) * (2 * (exy - mx * my) + 9e-4)) / (
+                (mx * mx + my * my + 1e-4) * (exx - mx * mx + eyy - my * my + 9e-4))
+    got = loss.ssim_map(torch.from_numpy(x), torch.from_numpy(y))[0].numpy()
+    assert np.allclose(got, ref, atol=1e-13)
+
+
+def test_l1_ssim_gradient_matches_central_differences():
+    rng = np.random.default_rng(3)
+    x = torch.from_numpy(rng.uniform(size=(3, 7, 8))).requires_grad_(True)
+    y = torch.from_numpy(rng.uniform(size=(3, 7, 8)))
+    L, _, _ = loss.l1_ssim([x], [y], 0.2)
+    (g,) = torch.autograd.grad(L, x)
+    h = 1e-6
+    for idx in [(0, 0, 0), (1, 3, 4), (2, 6, 7), (0, 2, 5)]:
+        xp, xm = x.detach().clone(), x.detach().clone()
+        xp[idx] += h
+        xm[idx] -= h
+        fd = (loss.l1_ssim([xp], [y], 0.2)[0] - loss.l1_ssim([xm], [y], 0.2)[0]) / (2 * h)
+        assert abs(float(fd) - float(g[idx])) < 1e-7
 
 
 def test_l1_loss_closed_form():
