@@ -345,11 +345,13 @@ def run_culling(st: Step, args, ms_unculled: float) -> dict:
 
 
 def run_strategies(st: Step, reps: int = 5) -> dict:
-    """The sampling kernels of the reorganisation on the step's own outputs:
-    primitive sampling of half of the Gaussians with I_i > 0 by P_i ~ I_i
-    (Sec. 4.3; I_i summed over the 8 views) and depth-reinitialization seeds
-    of 10 % of each view's pixels (Sec. 4.2).  Mean of `reps` calls each,
-    CUDA events."""
+    """The kernels of the reorganisation on the step's own outputs: primitive
+    sampling of half of the Gaussians with I_i > 0 by P_i ~ I_i (Sec. 4.3;
+    I_i summed over the 8 views), depth-reinitialization seeds of 10 % of
+    each view's pixels (Sec. 4.2), the fused L1 + D-SSIM loss over the 8
+    views and the aggressive clone of the first view's critical Gaussians
+    (Sec. 5.1; allocation of the grown scene included).  Mean of `reps`
+    calls each, CUDA events."""
     import torch
     r = st.raster
     n = st.g.n
@@ -379,8 +381,37 @@ def run_strategies(st: Step, reps: int = 5) -> dict:
                                         ks[v])["points"].shape[0])
     e1.record(stream)
     torch.cuda.synchronize()
+    depth_ms = e0.elapsed_time(e1) / reps
+    # fused L1 + D-SSIM loss and gradient over the 8 views (the C1 objective)
+    L = torch.zeros(1, device="cuda")
+    dL = torch.empty_like(st.outs["image"])
+    ws = r.loss_l1_ssim(st.plan, st.outs["image"], st.target, L, dL, 0.2)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        r.loss_l1_ssim(st.plan, st.outs["image"], st.target, L, dL, 0.2, ws=ws)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ssim_ms = e0.elapsed_time(e1) / reps
+    # aggressive clone of the first view's critical Gaussians (Sec. 5.1)
+    outs = r.alloc_outputs(st.plan, "cuda", want=("image", "final_T", "n_contrib", "imax", "wmax", "weight_sum",
+                                                  "max_area"))
+    r.render_fwd(st.plan, st.cfg, st.pre_ws, st.sort_ws, outs)
+    ids = r.identify(st.plan, outs["weight_sum"], outs["max_area"], outs["imax"], outs["wmax"])
+    crit = torch.nonzero(ids["flags"][:n] & r.ID_CRITICAL).flatten().to(torch.int32)
+    r.clone_gaussians(st.g, crit)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    for _ in range(reps):
+        cl = r.clone_gaussians(st.g, crit)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clone_ms = e0.elapsed_time(e1) / reps
+    del cl
     return {"sample_gaussians_ms": sample_ms, "sampled": int(kept.numel()), "of_positive": 2 * k,
-            "depth_points_ms_8_views": e0.elapsed_time(e1) / reps, "depth_points_per_call": drawn // reps,
+            "loss_l1_ssim_ms_8_views": ssim_ms,
+            "clone_critical_ms": clone_ms, "cloned": int(crit.numel()),
+            "depth_points_ms_8_views": depth_ms, "depth_points_per_call": drawn // reps,
             "note": "depth_points includes one host read of the drawn count per view (the Python binding "
                     "slices its outputs)"}
 
@@ -458,6 +489,83 @@ def run_e2e(st: Step, args, world) -> dict:
     return {"value": units / sec_max / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": sec_max * 1e3 / args.steps,
             "overlap": "double-buffered: uploads and downloads on a copy stream overlap the previous/next step"}
+
+
+def run_serving(st: Step, args) -> dict:
+    """Serving loop on the resident 1M scene: Poisson arrivals at 200 req/s
+    (seed 3), poses on a sphere of radius U[3, 6], resolutions uniform over
+    640x480 / 1280x720 / 1920x1080 / 3840x2160, 24 GB admission budget; the
+    first 10 % of requests are warm-up.  Batched (3 stream slots, up to 16
+    views per batch) against the same trace served one request at a time."""
+    import torch
+    from paper_2411_12788_gb300 import serve
+    n = args.serve_requests
+    skip = n // 11
+    out = {"rate_per_s": 200.0, "requests_timed": n - skip, "warmup_requests": skip, "budget_gb": 24,
+           "scene_gaussians": st.g.n}
+    for name, streams, views in (("batched", 3, 16), ("one_at_a_time", 1, 1)):
+        trace = serve.poisson_trace(n, rate=200.0, seed=3)
+        srv = serve.RenderServer(st.g, budget_bytes=24 << 30, streams=streams, max_views=views)
+        srv.serve(trace)
+        stats = serve.latency_stats(trace, skip=skip)
+        stats.update({"streams": streams, "max_views": views, "batches": srv.batches_run,
+                      "mean_views_per_batch": srv.views_run / max(1, srv.batches_run),
+                      "peak_reserved_gb": srv.peak_reserved / 2**30})
+        out[name] = stats
+        torch.cuda.synchronize()
+    out["p99_speedup"] = out["one_at_a_time"]["p99_ms"] / out["batched"]["p99_ms"]
+    return out
+
+
+def run_dense(args, iters: int = 3) -> dict:
+    """Dense-phase step (MSv2-D): 3M Gaussians (256 clusters, SH 3), one
+    1920x1080 view: fwd+bwd with L1, keep the top 25 % by accumulated weight,
+    gather them and re-render the sparse set."""
+    import torch
+    from paper_2411_12788_gb300 import raster, scenes
+    sc = scenes.cluster_scene(3_000_000, 256, seed=0, sh_degree=3)
+    cam = scenes.ring_camera(0.3, 1920, 1080)
+    g = raster.GaussianTensors.from_scene(sc, "cuda")
+    target = torch.as_tensor(scenes.target_images([cam], seed=1)[0].reshape(-1)).cuda()
+    cfg = raster.make_config(flags=raster._lib.GS_FLAG_ZERO_ACCUM)
+    k = math.ceil(0.25 * sc.n)
+    loss = torch.zeros(1, device="cuda")
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    times = {"fwd_bwd": 0.0, "prune_gather": 0.0, "rerender": 0.0}
+
+    def once(record):
+        s = torch.cuda.current_stream()
+        if record:
+            ev[0].record(s)
+        fr = raster.forward(g, [cam], cfg)
+        dL = torch.empty_like(fr.outs["image"])
+        raster.loss_l1(fr.outs["image"], target, loss, dL)
+        raster.backward(g, fr, dL)
+        if record:
+            ev[1].record(s)
+        keep = raster.prune_select(fr.outs["weight_sum"], k)
+        h = raster.gather_scene(g, keep)
+        if record:
+            ev[2].record(s)
+        fr2 = raster.forward(h, [cam], cfg)
+        if record:
+            ev[3].record(s)
+            torch.cuda.synchronize()
+            times["fwd_bwd"] += ev[0].elapsed_time(ev[1])
+            times["prune_gather"] += ev[1].elapsed_time(ev[2])
+            times["rerender"] += ev[2].elapsed_time(ev[3])
+        return fr, fr2
+    once(False)
+    torch.cuda.synchronize()
+    for _ in range(iters):
+        fr, fr2 = once(True)
+    ms = {k2: v / iters for k2, v in times.items()}
+    total = sum(ms.values())
+    pix = cam.width * cam.height
+    return {"workload": "3M Gaussians SH3 (256 clusters), 1920x1080: fwd+bwd, top-25% prune, re-render",
+            "ms": ms, "ms_total": total, "kept": k, "entries": int(fr.plan.n_entries),
+            "entries_after_prune": int(fr2.plan.n_entries), "mpix_per_s": 2 * pix / total / 1e3,
+            "note": "each phase allocates its workspaces from the torch caching allocator"}
 
 
 # ---------------------------------------------------------------- oracle arm
