@@ -186,9 +186,59 @@ def kernel_times(collect=True) -> dict:
     return out
 
 
-def roofline(kt: dict, st: "Step", steps: int, peaks: dict, clocks: dict) -> dict:
-    """Roofline of the dominant kernel (largest share of the timed region)."""
-    name = max(kt, key=lambda k: kt[k]["ms"])
+# DRAM bytes per launch measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum) at this workload,
+# valid while the kernel's source file is the one profiled (its SHA-256) and the workload has the same number
+# of tile entries; otherwise the traffic is reported as null.
+PROFILED_TRAFFIC = {
+    "render_bwd": {"bytes": 590.49e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
+                   "sha256": "35293e5867b5fe6c959a37cef25c27bb5c54187d00ecd5da4e28b3d2e8c25ff1",
+                   "profile": "profiles/render_bwd_1M_8views.md"},
+}
+
+
+def profiled_traffic(name: str, entries: int):
+    import hashlib
+    rec = PROFILED_TRAFFIC.get(name)
+    if rec is None or rec["entries"] != entries:
+        return None
+    try:
+        sha = hashlib.sha256(open(os.path.join(ROOT, rec["source"]), "rb").read()).hexdigest()
+    except OSError:
+        return None
+    return rec["bytes"] if sha == rec["sha256"] else None
+
+
+def visible_items(st: "Step") -> int:
+    """Items with at least one touched tile in the step's preprocess
+    workspace (counted on the device)."""
+    import ctypes as C
+    from paper_2411_12788_gb300 import _lib
+    if getattr(st, "_visible", None) is not None:
+        return st._visible
+    v = _lib.PreprocessView()
+    _lib.lib().gs_inspect_preprocess(C.byref(st.plan), C.c_void_p(st.pre_ws.data_ptr()), C.byref(v))
+    off = v.tiles - st.pre_ws.data_ptr()
+    I = int(st.plan.n_items)
+    tiles = st.pre_ws[off: off + 4 * I].view(st.torch.int32)
+    st._visible = int((tiles > 0).sum().item())
+    return st._visible
+
+
+def all_rooflines(kt: dict, st: "Step", peaks: dict, clocks: dict) -> dict:
+    """Roofline of every kernel with an algorithmic figure (same units as the
+    dominant kernel's)."""
+    out = {}
+    for name in kt:
+        r = roofline(kt, st, 0, peaks, clocks, name=name)
+        if r.get("achieved"):
+            out[name] = {k: r[k] for k in ("bound", "achieved", "peak", "unit", "frac")}
+    return out
+
+
+def roofline(kt: dict, st: "Step", steps: int, peaks: dict, clocks: dict, name: str | None = None) -> dict:
+    """Roofline of the dominant kernel (largest share of the timed region),
+    or of `name`."""
+    name = name or max(kt, key=lambda k: kt[k]["ms"])
     ms = kt[name]["ms"] / max(1, kt[name]["launches"])
     E = int(st.plan.n_entries)
     torch = st.torch
@@ -199,8 +249,11 @@ def roofline(kt: dict, st: "Step", steps: int, peaks: dict, clocks: dict) -> dic
         sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
         peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
         ach = flops / (ms * 1e-3) / 1e12
+        traffic = profiled_traffic(name, E)
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
+                "frac": ach / peak, "traffic": traffic,
+                "traffic_note": (f"DRAM bytes per launch from ncu ({PROFILED_TRAFFIC[name]['profile']}); "
+                                 f"algorithmic {flops / traffic:.0f} flop per byte moved") if traffic else None,
                 "units": {"evaluations_per_launch": evals, "flops_per_evaluation": BWD_FLOPS_PER_EVAL},
                 "peak_note": f"FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled)"}
     if name == "render_fwd":
@@ -213,11 +266,19 @@ def roofline(kt: dict, st: "Step", steps: int, peaks: dict, clocks: dict) -> dic
                 "frac": ach / peak, "traffic": None,
                 "units": {"evaluations_per_launch": evals, "flops_per_evaluation": FWD_FLOPS_PER_EVAL},
                 "peak_note": f"FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled)"}
-    # HBM-bound kernels: algorithmic bytes per launch
+    # HBM-bound kernels: algorithmic bytes per launch.  V = items with a tile
+    # (the rest are culled and write only their count and depth key).
     I = int(st.plan.n_items)
-    per = {"tile_sort_onesweep": 16 * E, "depth_sort_onesweep": 16 * I, "duplicate": 8 * E + 20 * I,
-           "preprocess": 236 * st.g.n + 120 * I, "preprocess_backward": 236 * 2 * st.g.n + 48 * I,
-           "tile_sort_histogram": 4 * E, "ranges": 4 * E}
+    V = visible_items(st)
+    N = st.g.n
+    per = {"tile_sort_onesweep": 16 * E, "depth_sort_onesweep": 16 * I, "tile_sort_histogram": 4 * E,
+           "depth_sort_histogram": 4 * I,
+           # item id, tile count and offset of every item; centre and row parameters of visible ones; entries
+           "duplicate": 8 * I + 52 * V + 8 * E,
+           # attributes of every Gaussian; count and key of every item, 136 B of state per visible item
+           "preprocess": 236 * N + 8 * I + 136 * V,
+           # attributes and their gradients; the 2-D gradients of visible items
+           "preprocess_backward": 2 * 236 * N + 48 * V}
     bytes_ = per.get(name, 0)
     ach = bytes_ / (ms * 1e-3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)
@@ -277,6 +338,7 @@ def run_ours(args, rank, world):
     except Exception:
         peaks = {"hbm_gbs": 6800.0, "note": "fallback"}
     rl = roofline(kt, st, args.steps, peaks, ck)
+    rls = all_rooflines(kt, st, peaks, ck)
 
     strategies = None if args.no_culling else run_strategies(st)
     culling = None if args.no_culling else run_culling(st, args, sec_max * 1e3 / args.steps)
@@ -296,7 +358,7 @@ def run_ours(args, rank, world):
                        "pixels_per_step": st.pixels, "entries_per_step": int(st.plan.n_entries),
                        "l2": "inputs larger than L2 (236 MB scene, 1.5 GB workspace)",
                        "parallelism": f"replicas x{world}"},
-            "roofline": rl, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
+            "roofline": rl, "rooflines": rls, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
             "serving": serving, "dense_phase": dense, "culling": culling, "strategies": strategies,
             "clocks": ck, "kernels": kt}
     return line
