@@ -13,65 +13,169 @@ namespace gs {
 namespace {
 
 constexpr int kDupThreads = 256;
+constexpr int kDupWarps = kDupThreads / 32;
 
+// Per-lane state of the item a lane loaded (the warp's 32 consecutive items
+// of the depth order).
+struct DupItem {
+  BinParams b;
+  uint32_t item, off, cnt;
+  int ty0, tiles_x, tile_base;
+};
+
+// One warp per 32 consecutive items of the depth order.  Their entries form
+// one contiguous run of the output, and every item's are its tile rows in
+// order, so the warp enumerates (item, tile row) pairs 32 at a time: each
+// lane evaluates one row's tile interval (the same row_tiles the preprocess
+// counted with), a warp scan turns the row lengths into positions, and the
+// lanes then write the 32 rows' entries together (entry e of the iteration
+// is the e-th of one contiguous run, so the stores coalesce), each finding its
+// row by a 5-step search.
+// Every item's rows must add up to the count the preprocess stored; a
+// mismatch sets kStatusEntryMismatch and nothing is written out of range.
 __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* __restrict__ views, int64_t n_items,
                                                                 int64_t n, const uint32_t* __restrict__ sorted_items,
                                                                 const uint32_t* __restrict__ offsets, ItemState st,
                                                                 uint32_t* __restrict__ keys,
                                                                 uint32_t* __restrict__ vals,
                                                                 uint32_t* __restrict__ status) {
-  const int64_t k = (int64_t)blockIdx.x * kDupThreads + threadIdx.x;
-  if (k >= n_items) return;
-  const uint32_t item = sorted_items[k];
-  const uint32_t cnt = st.tiles[item];
-  if (cnt == 0) return;
-  const uint32_t off = offsets[k];
-  const float4 a = st.xy_tau_z[item];
-  const float4 b0 = st.bin[2 * item], b1 = st.bin[2 * item + 1];
-  BinParams b;
-  b.mx = a.x;
-  b.my = a.y;
-  b.tau = a.z;
-  b.k = b0.x;
-  b.sc = b0.y;
-  b.isyy = b0.z;
-  b.h = b0.w;
-  b.rx = b1.x;
-  b.ys = b1.y;
-  const ViewDev& V = views[item / n];
-  // this item's entries are the contiguous run [off, off + cnt): write it as
-  // scalars up to a 16-byte boundary, then in groups of four (uint4), then
-  // the scalar tail
-  const uint32_t head = min((4u - (off & 3u)) & 3u, cnt);
-  const uint32_t groups_end = head + ((cnt - head) & ~3u);
-  const uint4 vals4 = make_uint4(item, item, item, item);
-  uint32_t buf[4];
-  uint32_t written = 0;
-  int ty0, ty1;
-  if (tile_rows(b, V.tiles_y, &ty0, &ty1)) {
-    for (int ty = ty0; ty <= ty1; ++ty) {
-      int tx_a, tx_b;
-      if (!row_tiles(b, ty, V.tiles_x, &tx_a, &tx_b)) continue;
-      const uint32_t base = (uint32_t)(V.tile_base + ty * V.tiles_x);
-      for (int tx = tx_a; tx <= tx_b; ++tx) {
-        const uint32_t key = base + (uint32_t)tx;
-        if (written < head || (written >= groups_end && written < cnt)) {
-          keys[off + written] = key;
-          vals[off + written] = item;
-        } else if (written < groups_end) {
-          const uint32_t g = (written - head) & 3u;
-          buf[g] = key;
-          if (g == 3u) {
-            const uint32_t at = off + written - 3u;     // 4-aligned
-            *reinterpret_cast<uint4*>(keys + at) = make_uint4(buf[0], buf[1], buf[2], buf[3]);
-            *reinterpret_cast<uint4*>(vals + at) = vals4;
-          }
-        }
-        ++written;
+  __shared__ DupItem s_it[kDupWarps][32];
+  __shared__ uint32_t s_rstart[kDupWarps][33];     // first row unit of each lane's item
+  __shared__ uint32_t s_pre[kDupWarps][33];        // entries before each row of the iteration
+  __shared__ uint32_t s_key0[kDupWarps][32];       // key of each row's first entry
+  __shared__ uint32_t s_item[kDupWarps][32];       // item of each row
+  __shared__ uint32_t s_out0[kDupWarps][32];       // output position of each row's first entry
+  __shared__ uint32_t s_lim[kDupWarps][32];        // entries the row may write (its item's remaining count)
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t k = ((int64_t)blockIdx.x * kDupWarps + warp) * 32 + lane;
+  if (((int64_t)blockIdx.x * kDupWarps + warp) * 32 >= n_items) return;     // warp-uniform
+
+  // 1. this lane's item and its band of tile rows
+  uint32_t nrows = 0;
+  {
+    DupItem d;
+    d.item = 0;
+    d.cnt = 0;
+    d.off = 0;
+    d.ty0 = 0;
+    d.tiles_x = 0;
+    d.tile_base = 0;
+    if (k < n_items) {
+      d.item = sorted_items[k];
+      d.cnt = st.tiles[d.item];
+      if (d.cnt) {
+        d.off = offsets[k];
+        const float4 a = st.xy_tau_z[d.item];
+        const float4 b0 = st.bin[2 * d.item], b1 = st.bin[2 * d.item + 1];
+        d.b.mx = a.x;
+        d.b.my = a.y;
+        d.b.tau = a.z;
+        d.b.k = b0.x;
+        d.b.sc = b0.y;
+        d.b.isyy = b0.z;
+        d.b.h = b0.w;
+        d.b.rx = b1.x;
+        d.b.ys = b1.y;
+        const ViewDev& V = views[d.item / n];
+        d.tiles_x = V.tiles_x;
+        d.tile_base = V.tile_base;
+        int ty1 = -1;
+        if (tile_rows(d.b, V.tiles_y, &d.ty0, &ty1)) nrows = (uint32_t)(ty1 - d.ty0 + 1);
+        else atomicOr(status, kStatusEntryMismatch);      // a counted item always has rows
       }
     }
+    s_it[warp][lane] = d;
   }
-  if (written != cnt) atomicOr(status, kStatusEntryMismatch);
+  uint32_t rs = nrows;                                    // exclusive scan of the row counts
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t t = __shfl_up_sync(0xffffffffu, rs, o);
+    if (lane >= o) rs += t;
+  }
+  const uint32_t R = __shfl_sync(0xffffffffu, rs, 31);
+  s_rstart[warp][lane] = rs - nrows;
+  if (lane == 31) s_rstart[warp][32] = R;
+  __syncwarp();
+
+  // 2. 32 rows at a time
+  int carry_j = -1;                                       // item continuing from the last iteration
+  uint32_t carry = 0;                                     // its entries in earlier iterations
+  for (uint32_t u0 = 0; u0 < R; u0 += 32) {
+    const uint32_t u = u0 + lane;
+    const bool valid = u < R;
+    int j = 32;                                           // owner item (lane index), 32 = none
+    uint32_t c = 0, key0 = 0;
+    if (valid) {
+      int lo = 0, hi = 32;                                // last j with rstart[j] <= u
+#pragma unroll
+      for (int step = 0; step < 5; ++step) {
+        const int mid = (lo + hi) >> 1;
+        if (s_rstart[warp][mid] <= u) lo = mid;
+        else hi = mid;
+      }
+      j = lo;
+      const DupItem& d = s_it[warp][j];
+      const int ty = d.ty0 + (int)(u - s_rstart[warp][j]);
+      int ta, tb;
+      if (row_tiles(d.b, ty, d.tiles_x, &ta, &tb)) {
+        c = (uint32_t)(tb - ta + 1);
+        key0 = (uint32_t)(d.tile_base + ty * d.tiles_x + ta);
+      }
+    }
+    // entries of the same item in earlier lanes of this iteration (segmented
+    // inclusive scan; j is non-decreasing across the lanes)
+    uint32_t seg = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, seg, o);
+      const int jo = __shfl_up_sync(0xffffffffu, j, o);
+      if (lane >= o && jo == j) seg += t;
+    }
+    const uint32_t in_item = seg - c + (j == carry_j ? carry : 0u);    // entries of the item before this row
+    if (valid && u + 1 == s_rstart[warp][j + 1] && in_item + c != s_it[warp][j].cnt)
+      atomicOr(status, kStatusEntryMismatch);            // the item's last row: the totals must agree
+    // positions of the rows in the iteration's run
+    uint32_t pre = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, pre, o);
+      if (lane >= o) pre += t;
+    }
+    const uint32_t T = __shfl_sync(0xffffffffu, pre, 31);
+    s_pre[warp][lane] = pre - c;
+    if (lane == 31) s_pre[warp][32] = T;
+    s_key0[warp][lane] = key0;
+    s_item[warp][lane] = valid ? s_it[warp][j].item : 0u;
+    // a row writes at its item's offset plus the item's earlier entries, and
+    // never beyond the item's count (with counts that agree, consecutive rows
+    // continue one run, so entry e lands at the run start + e)
+    const uint32_t icnt = valid ? s_it[warp][j].cnt : 0u;
+    s_out0[warp][lane] = valid ? s_it[warp][j].off + in_item : 0u;
+    s_lim[warp][lane] = icnt > in_item ? icnt - in_item : 0u;
+    const int next_j = __shfl_sync(0xffffffffu, j, 31);
+    const uint32_t next_carry = __shfl_sync(0xffffffffu, in_item + c, 31);
+    __syncwarp();
+    for (uint32_t e = lane; e < T; e += 32) {
+      int lo = 0, hi = 32;                                // row of entry e
+#pragma unroll
+      for (int step = 0; step < 5; ++step) {
+        const int mid = (lo + hi) >> 1;
+        if (s_pre[warp][mid] <= e) lo = mid;
+        else hi = mid;
+      }
+      // rows with no entries share their successor's prefix; take the last
+      // row with pre <= e, which is the one holding entry e
+      const uint32_t d = e - s_pre[warp][lo];
+      if (d < s_lim[warp][lo]) {
+        const uint32_t at = s_out0[warp][lo] + d;
+        keys[at] = s_key0[warp][lo] + d;
+        vals[at] = s_item[warp][lo];
+      }
+    }
+    __syncwarp();
+    carry_j = next_j;
+    carry = next_carry;
+  }
 }
 
 // [start, end) of every tile in the sorted key list by binary search: thread
