@@ -76,7 +76,8 @@ typedef struct gs_config {
   uint32_t flags;
 } gs_config;
 
-/* gs_render_fwd / gs_render_bwd zero their accumulated outputs first */
+/* gs_render_fwd / gs_render_bwd zero their accumulated outputs first (the
+ * backward writes the attribute gradients instead of adding to them) */
 #define GS_FLAG_ZERO_ACCUM 1u
 
 /* Gaussian attributes, device, FP32, structure of arrays:

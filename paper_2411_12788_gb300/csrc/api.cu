@@ -297,15 +297,10 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
   const SortLayout S = sort_layout(*plan);
   const int64_t n = plan->n;
   cudaError_t e = cudaMemsetAsync(at<char>(pre_ws, L.grad2d), 0, 48 * (size_t)plan->n_items, stream);
-  if (e == cudaSuccess && (cfg->flags & GS_FLAG_ZERO_ACCUM)) {
-    e = cudaMemsetAsync(g->d_means, 0, 12 * (size_t)n, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_scales, 0, 12 * (size_t)n, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_rotations, 0, 16 * (size_t)n, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_opacities, 0, 4 * (size_t)n, stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(g->d_sh, 0, 12 * (size_t)n * scene->sh_coeffs, stream);
-    if (e == cudaSuccess && g->d_mean2d_abs) e = cudaMemsetAsync(g->d_mean2d_abs, 0, 4 * (size_t)n, stream);
-    if (e == cudaSuccess && g->weight_sum) e = cudaMemsetAsync(g->weight_sum, 0, 4 * (size_t)plan->n_items, stream);
-  }
+  // with GS_FLAG_ZERO_ACCUM the preprocess backward writes every attribute
+  // gradient row (no read-modify-write); I_i is accumulated by atomics
+  if (e == cudaSuccess && (cfg->flags & GS_FLAG_ZERO_ACCUM) && g->weight_sum)
+    e = cudaMemsetAsync(g->weight_sum, 0, 4 * (size_t)plan->n_items, stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
   const ItemState st = item_state(pre_ws, L);
   float4* grad2d = at<float4>(pre_ws, L.grad2d);

@@ -221,6 +221,7 @@ struct PreBwdParams {
   float* d_opac;
   float* d_sh;
   float* d_mean2d_abs;
+  bool overwrite;         // write the gradients (every row) instead of adding to them
 };
 
 constexpr int kPreBwdThreads = 64;
@@ -396,18 +397,41 @@ __global__ void __launch_bounds__(kPreBwdThreads) preprocess_backward_kernel(Pre
     }
   }
 
-  // SH gradients: added to the block's rows with coalesced read-modify-writes
+  // SH gradients of the block's rows, coalesced: written whole (coefficients
+  // beyond the degree get 0) or added
   __syncthreads();
   {
     constexpr int per = 3 * K;
     const int64_t rows = (P.n - i0 < kPreBwdThreads) ? (P.n - i0) : (int64_t)kPreBwdThreads;
-    for (int f = threadIdx.x; f < rows * per; f += kPreBwdThreads) {
-      const int g = f / per, c = f - g * per;
-      const float v = s_dsh[g * row + c];
-      if (v != 0.f) P.d_sh[(i0 + g) * (int64_t)P.sh_coeffs * 3 + c] += v;
+    if (P.overwrite) {
+      const int full = 3 * P.sh_coeffs;
+      for (int f = threadIdx.x; f < rows * full; f += kPreBwdThreads) {
+        const int g = f / full, c = f - g * full;
+        P.d_sh[(i0 + g) * (int64_t)full + c] = c < per ? s_dsh[g * row + c] : 0.f;
+      }
+    } else {
+      for (int f = threadIdx.x; f < rows * per; f += kPreBwdThreads) {
+        const int g = f / per, c = f - g * per;
+        const float v = s_dsh[g * row + c];
+        if (v != 0.f) P.d_sh[(i0 + g) * (int64_t)P.sh_coeffs * 3 + c] += v;
+      }
     }
   }
-  if (!live || !any) return;
+  if (!live) return;
+  if (!any) {
+    if (P.overwrite) {     // not rendered in any view: zero gradients
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        P.d_means[3 * i + c] = 0.f;
+        P.d_scales[3 * i + c] = 0.f;
+      }
+#pragma unroll
+      for (int c = 0; c < 4; ++c) P.d_rots[4 * i + c] = 0.f;
+      P.d_opac[i] = 0.f;
+      if (P.d_mean2d_abs) P.d_mean2d_abs[i] = 0.f;
+    }
+    return;
+  }
 
   // Sigma = M M^T, M = Rq diag(s): dM = 2 dSigma M
   const float G[9] = {dSig[0], dSig[1], dSig[2], dSig[1], dSig[3], dSig[4], dSig[2], dSig[4], dSig[5]};
@@ -441,18 +465,20 @@ __global__ void __launch_bounds__(kPreBwdThreads) preprocess_backward_kernel(Pre
   dqy = (dqy - dotq * qy) * qinv;
   dqz = (dqz - dotq * qz) * qinv;
 
-  P.d_means[3 * i] += dp[0];
-  P.d_means[3 * i + 1] += dp[1];
-  P.d_means[3 * i + 2] += dp[2];
-  P.d_scales[3 * i] += ds[0];
-  P.d_scales[3 * i + 1] += ds[1];
-  P.d_scales[3 * i + 2] += ds[2];
-  P.d_rots[4 * i] += dqw;
-  P.d_rots[4 * i + 1] += dqx;
-  P.d_rots[4 * i + 2] += dqy;
-  P.d_rots[4 * i + 3] += dqz;
-  P.d_opac[i] += dop;
-  if (P.d_mean2d_abs) P.d_mean2d_abs[i] += m2abs;
+  const float out[11] = {dp[0], dp[1], dp[2], ds[0], ds[1], ds[2], dqw, dqx, dqy, dqz, dop};
+  float* const dst[11] = {P.d_means + 3 * i,     P.d_means + 3 * i + 1,  P.d_means + 3 * i + 2,
+                          P.d_scales + 3 * i,    P.d_scales + 3 * i + 1, P.d_scales + 3 * i + 2,
+                          P.d_rots + 4 * i,      P.d_rots + 4 * i + 1,   P.d_rots + 4 * i + 2,
+                          P.d_rots + 4 * i + 3,  P.d_opac + i};
+  if (P.overwrite) {
+#pragma unroll
+    for (int c = 0; c < 11; ++c) *dst[c] = out[c];
+    if (P.d_mean2d_abs) P.d_mean2d_abs[i] = m2abs;
+  } else {
+#pragma unroll
+    for (int c = 0; c < 11; ++c) *dst[c] += out[c];
+    if (P.d_mean2d_abs) P.d_mean2d_abs[i] += m2abs;
+  }
 }
 
 }  // namespace
@@ -507,6 +533,7 @@ cudaError_t launch_preprocess_backward(const gs_scene& sc, const ViewDev* views,
   P.d_opac = gr.d_opacities;
   P.d_sh = gr.d_sh;
   P.d_mean2d_abs = gr.d_mean2d_abs;
+  P.overwrite = (cfg.flags & GS_FLAG_ZERO_ACCUM) != 0;
   const int blocks = ceil_div(sc.n, kPreBwdThreads);
   if (blocks == 0) return cudaSuccess;
   switch (sc.sh_degree) {

@@ -388,3 +388,42 @@ def test_training_scale_sampled_pixels():
     assert np.all(dz[same] >= 0)
     assert np.all(np.diff(it)[same & (dz == 0)] > 0)
     assert np.bincount(it, minlength=sc.n).sum() == fr.plan.n_entries
+
+
+# ---------------------------------------------------------------- gradient buffer modes
+@pytest.mark.parametrize("deg", [0, 3])
+def test_backward_overwrite_mode_equals_accumulate_into_zeros(deg):
+    """GS_FLAG_ZERO_ACCUM writes every attribute gradient (the buffers' old
+    contents, here NaN, are never read); without it the gradients are added
+    to what the buffers hold."""
+    _need_gpu()
+    sc = scenes.cluster_scene(30000, 16, seed=17, sh_degree=deg)
+    sc.sh = np.concatenate([sc.sh, np.zeros((sc.n, 2, 3), np.float32)], 1)    # stored rows wider than the degree
+    cams = [scenes.ring_camera(0.5, 96, 80), scenes.ring_camera(2.6, 64, 48)]
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, cams)
+    dL = torch.randn_like(fr.outs["image"])
+    ref = raster.alloc_grads(g)                      # zeros, accumulate mode
+    raster.render_bwd(fr.plan, g.struct(), fr.cfg, fr.pre_ws, fr.sort_ws, dL, fr.outs["image"],
+                      fr.outs["n_contrib"], ref)
+    nan = {k: torch.full_like(v, float("nan")) for k, v in ref.items()}
+    cfg = raster.make_config(flags=raster._lib.GS_FLAG_ZERO_ACCUM)
+    raster.render_bwd(fr.plan, g.struct(), cfg, fr.pre_ws, fr.sort_ws, dL, fr.outs["image"],
+                      fr.outs["n_contrib"], nan)
+    ones = {k: torch.ones_like(v) for k, v in ref.items()}
+    raster.render_bwd(fr.plan, g.struct(), fr.cfg, fr.pre_ws, fr.sort_ws, dL, fr.outs["image"],
+                      fr.outs["n_contrib"], ones)
+    torch.cuda.synchronize()
+    # the per-item 2-D gradients are summed with float atomics, whose order
+    # differs between runs: equal up to rounding
+    for k in ref:
+        tol = 1e-5 * (1e-3 + ref[k].abs().max().item())
+        assert not torch.isnan(nan[k]).any(), k
+        assert torch.allclose(nan[k], ref[k], rtol=0, atol=tol), k
+        assert torch.allclose(ones[k], ref[k] + 1, rtol=0, atol=tol + 1e-6), k
+    # Gaussians rendered in no view get exact zeros
+    unseen = ref["d_means"].abs().sum(1) == 0
+    assert unseen.any() and (nan["d_means"][unseen] == 0).all() and (nan["d_sh"][unseen] == 0).all()
+    # coefficients beyond the degree: zero in both modes
+    K = (deg + 1) ** 2
+    assert (nan["d_sh"][:, K:] == 0).all() and (ones["d_sh"][:, K:] == 1).all()
