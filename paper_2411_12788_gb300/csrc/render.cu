@@ -225,6 +225,40 @@ __device__ __forceinline__ bool box_meets_block(float4 b, float x0, float y0) {
   return b.x <= x0 + 7.f && b.y >= x0 && b.z <= y0 + 3.f && b.w >= y0;
 }
 
+// Whether an entry can pass the exponent test at some pixel of the 8x4 block
+// with pixel centres [x0, x0 + 7] x [y0, y0 + 3]: the maximum over that
+// rectangle of the concave e(dx, dy) = lo + a2 dx^2 + b2 dx dy + c2 dy^2 (at
+// the centre if it lies inside, else on an edge at the clamped vertex) is
+// compared with e_min - margin.  The margin, 2^-18 (|lo| + |e_min| + S) with
+// S = |a2| DX^2 + |b2| DX DY + |c2| DY^2 over the block's largest offsets, is
+// 16 times a bound on the rounding error of the per-pixel FP32 exponent (four
+// roundings of terms no larger than S), so a block that fails the test holds
+// no pixel where the entry is blended.
+__device__ __forceinline__ bool block_may_blend(float4 ex, float mx, float my, float x0, float y0, float e_min) {
+  const float dx0 = x0 - mx, dx1 = (x0 + 7.f) - mx, dy0 = y0 - my, dy1 = (y0 + 3.f) - my;
+  const float a2 = ex.x, b2 = ex.y, c2 = ex.z, lo = ex.w;
+  float best;
+  if (dx0 <= 0.f && dx1 >= 0.f && dy0 <= 0.f && dy1 >= 0.f) {
+    best = 0.f;
+  } else {
+    const float ia = -0.5f / a2, ic = -0.5f / c2;            // a2, c2 < 0
+    best = -INFINITY;
+#pragma unroll
+    for (int s2 = 0; s2 < 2; ++s2) {
+      const float dx = s2 ? dx1 : dx0;                         // vertical edge: best dy
+      const float dy = fminf(fmaxf(b2 * dx * ic, dy0), dy1);
+      best = fmaxf(best, fmaf(fmaf(a2, dx, b2 * dy), dx, c2 * dy * dy));
+      const float ey = s2 ? dy1 : dy0;                         // horizontal edge: best dx
+      const float ex2 = fminf(fmaxf(b2 * ey * ia, dx0), dx1);
+      best = fmaxf(best, fmaf(fmaf(a2, ex2, b2 * ey), ex2, c2 * ey * ey));
+    }
+  }
+  const float DX = fmaxf(fabsf(dx0), fabsf(dx1)), DY = fmaxf(fabsf(dy0), fabsf(dy1));
+  const float S = fabsf(a2) * DX * DX + fabsf(b2) * DX * DY + fabsf(c2) * DY * DY;
+  const float margin = 3.814697265625e-6f * (fabsf(lo) + fabsf(e_min) + S);   // 2^-18
+  return lo + best >= e_min - margin;
+}
+
 // One thread per two pixels: rows y and y + 8 of the tile (warp w < 4 owns
 // the 8x4 blocks at ((w & 1) 8, (w >> 1) 4) and 8 rows below), so the
 // shared-memory reads of an entry and the loop control serve both.
@@ -469,13 +503,14 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
       s_box[tid] = support_box(a.x, a.y, c.w);
     }
     __syncthreads();
-    // the batch entries this warp walks: support box meets its 8x4 block and
-    // list position before the last blended position of its pixels (the
-    // forward pass culls with the same boxes and blocks)
+    // the batch entries this warp walks: list position before the last
+    // blended position of its pixels, support box meeting its 8x4 block and
+    // the exponent able to pass the threshold in the block
     int cnt = 0;
     for (int k0 = 0; k0 < nb; k0 += 32) {
       const int k = k0 + lane;
-      const bool hit = k < nb && bstart + (uint32_t)k < warp_nc && box_meets_block(s_box[k], bxf, byf);
+      bool hit = k < nb && bstart + (uint32_t)k < warp_nc && box_meets_block(s_box[k], bxf, byf);
+      if (hit) hit = block_may_blend(s_ex[k], s_xy[k].x, s_xy[k].y, bxf, byf, P.e_min);
       const uint32_t bal = __ballot_sync(0xffffffffu, hit);
       if (hit) s_list[warp][cnt + __popc(bal & lt_mask)] = (uint8_t)k;
       cnt += __popc(bal);

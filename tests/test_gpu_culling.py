@@ -63,3 +63,26 @@ def test_support_boxes_hold_every_blended_pixel(seed):
     # wider margins, so the ratio stays below 1 / (1.02 + 4e-6 kappa))
     rel = np.maximum(np.abs(px - mx) / ex, np.abs(py - my) / ey)
     assert (rel > 0.75).sum() > 0
+
+
+@pytest.mark.parametrize("seed", [7, 9])
+def test_backward_culling_drops_no_blended_pair(seed):
+    """The backward replays, per 8x4 block, only the entries that pass the
+    box and exponent tests, and collects I_i = sum of the weights it
+    replays.  A blended (pixel, entry) pair culled by mistake would leave
+    that Gaussian's collected I_i short of the forward's (a pair weighs at
+    least alpha_min T); on thin, faint needles the two sums must agree."""
+    _need_gpu()
+    sc = scenes.needle_scene(4000, seed=seed)
+    cams = [scenes.origin_camera(512, 512, 512.0), scenes.origin_camera(300, 200, 300.0)]
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, cams)
+    grads = raster.alloc_grads(g)
+    grads["weight_sum"] = torch.zeros(int(fr.plan.n_items), device="cuda")
+    dL = torch.rand_like(fr.outs["image"]) - 0.5
+    raster.render_bwd(fr.plan, g.struct(), fr.cfg, fr.pre_ws, fr.sort_ws, dL, fr.outs["image"],
+                      fr.outs["n_contrib"], grads)
+    a = grads["weight_sum"].double().cpu()
+    b = fr.outs["weight_sum"].double().cpu()
+    assert (b > 0).sum() > 2000
+    assert torch.all((a - b).abs() <= 2e-6 + 1e-5 * b.abs())
