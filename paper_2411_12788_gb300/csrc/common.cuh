@@ -5,6 +5,7 @@
 #include <stdint.h>
 
 #include <algorithm>
+#include <atomic>
 #include <utility>
 
 #include "../../include/gs.h"
@@ -95,6 +96,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t phase, long bu
     if (done) return true;
   }
   return false;
+}
+
+// Runs `init` once per (device, slot): per-device state such as a kernel's
+// dynamic shared-memory limit or a __constant__ table.  Thread-safe; a failed
+// init is retried on the next call.
+template <typename F>
+cudaError_t once_per_device(std::atomic<uint64_t>& done, F&& init) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  const uint64_t bit = 1ull << dev;
+  if (done.load(std::memory_order_acquire) & bit) return cudaSuccess;
+  e = init();
+  if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_acq_rel);
+  return e;
 }
 
 // ---- onesweep radix sort sizing (sort.cu) ----------------------------------

@@ -417,13 +417,12 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
   if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(keys_alt) | reinterpret_cast<uintptr_t>(vals) |
        reinterpret_cast<uintptr_t>(vals_alt)) & 15)
     return cudaErrorMisalignedAddress;     // the bulk copies need 16-byte aligned rows
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t ea = cudaFuncSetAttribute(radix_onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                          (int)kOnesweepDynSmem);
-    if (ea != cudaSuccess) return ea;
-    attr_set = true;
-  }
+  static std::atomic<uint64_t> attr_done{0};
+  cudaError_t ea = once_per_device(attr_done, [] {
+    return cudaFuncSetAttribute(radix_onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)kOnesweepDynSmem);
+  });
+  if (ea != cudaSuccess) return ea;
   const int passes = (bits + kRadixBits - 1) / kRadixBits;
   RadixScratch s = carve(scratch, n);
   const int64_t tiles = sort_tiles(n);

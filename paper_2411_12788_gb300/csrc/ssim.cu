@@ -278,10 +278,8 @@ extern "C" gs_status gs_loss_l1_ssim(const gs_plan* plan, const float* image, co
   if (ws_bytes < gs_loss_l1_ssim_workspace_size(plan)) return GS_ERR_CAPACITY;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   // the window and the shared-memory limit, once per device
-  static uint64_t init_mask = 0;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return GS_ERR_CUDA;
-  if (!((init_mask >> dev) & 1u)) {
+  static std::atomic<uint64_t> init_done{0};
+  const cudaError_t ei = once_per_device(init_done, [] {
     // normalised 11-tap Gaussian, sigma 1.5
     double g[kW], sum = 0.0;
     for (int t = 0; t < kW; ++t) {
@@ -293,9 +291,9 @@ extern "C" gs_status gs_loss_l1_ssim(const gs_plan* plan, const float* image, co
     cudaError_t e = cudaMemcpyToSymbol(c_win, gf, sizeof(gf));
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(l1_ssim_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SsimSmem));
-    if (e != cudaSuccess) return GS_ERR_CUDA;
-    init_mask |= 1ull << dev;
-  }
+    return e;
+  });
+  if (ei != cudaSuccess) return GS_ERR_CUDA;
   if (count == 0) return cudaMemsetAsync(loss, 0, 4, stream) == cudaSuccess ? GS_OK : GS_ERR_CUDA;
   SsimParams P;
   int tb = 0;
