@@ -347,6 +347,7 @@ def run_ours(args, rank, world):
         e2e = run_e2e(st, args, world)
     serving = None if args.no_serve else run_serving(st, args)
     dense = None if args.no_dense else run_dense(args)
+    c1 = None if args.no_dense else run_c1_step()
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(st.scene, st.cams)
@@ -359,7 +360,8 @@ def run_ours(args, rank, world):
                        "l2": "inputs larger than L2 (236 MB scene, 1.5 GB workspace)",
                        "parallelism": f"replicas x{world}"},
             "roofline": rl, "rooflines": rls, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches // 1,
-            "serving": serving, "dense_phase": dense, "culling": culling, "strategies": strategies,
+            "serving": serving, "dense_phase": dense, "single_view_l1_ssim": c1, "culling": culling,
+            "strategies": strategies,
             "clocks": ck, "kernels": kt}
     return line
 
@@ -478,6 +480,53 @@ def run_strategies(st: Step, reps: int = 5) -> dict:
                     "slices its outputs)"}
 
 
+def run_c1_step(iters: int = 5) -> dict:
+    """The training step of the single-view configuration: 500k Gaussians
+    (SH 3, 64-cluster + shell scene), one 1600x1063 ring view, 0.8 L1 +
+    0.2 D-SSIM against the seeded target; forward (colour, depth, i_max, I_i),
+    fused loss, backward.  Mean of `iters` steps after one warm-up, CUDA
+    events."""
+    import torch
+    from paper_2411_12788_gb300 import raster, scenes
+    sc = scenes.cluster_scene(500_000, 64, seed=0, sh_degree=3)
+    cam = scenes.ring_camera(0.3, 1600, 1063)
+    g = raster.GaussianTensors.from_scene(sc, "cuda")
+    y = torch.as_tensor(scenes.target_images([cam], seed=1)[0].reshape(-1)).cuda()
+    plan = raster.make_plan(sc.n, [cam])
+    cfg = raster.make_config(flags=raster._lib.GS_FLAG_ZERO_ACCUM)
+    pre_ws = torch.empty(raster.preprocess_workspace_size(plan), dtype=torch.uint8, device="cuda")
+    outs = raster.alloc_outputs(plan, "cuda", want=("image", "final_T", "n_contrib", "depth", "imax"))
+    grads = raster.alloc_grads(g)
+    grads["weight_sum"] = torch.zeros(int(plan.n_items), device="cuda")
+    L = torch.zeros(1, device="cuda")
+    dL = torch.empty_like(outs["image"])
+    state = {"sort": torch.empty(0, dtype=torch.uint8, device="cuda"), "ws": None}
+
+    def step():
+        raster.preprocess(plan, g.struct(), cfg, pre_ws)
+        need = raster.bin_sort_workspace_size(plan)
+        if state["sort"].numel() < need:
+            state["sort"] = torch.empty(int(need * 1.1), dtype=torch.uint8, device="cuda")
+        raster.bin_sort(plan, pre_ws, state["sort"])
+        raster.render_fwd(plan, cfg, pre_ws, state["sort"], outs)
+        state["ws"] = raster.loss_l1_ssim(plan, outs["image"], y, L, dL, 0.2, ws=state["ws"])
+        raster.render_bwd(plan, g.struct(), cfg, pre_ws, state["sort"], dL, outs["image"], outs["n_contrib"],
+                          grads)
+    step()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(iters):
+        step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / iters
+    return {"workload": "500k Gaussians SH3, 1600x1063, 0.8 L1 + 0.2 D-SSIM: fwd + fused loss + bwd",
+            "ms_per_step": ms, "mpix_per_s": cam.width * cam.height / ms / 1e3, "entries": int(plan.n_entries),
+            "loss": float(L.item())}
+
+
 def run_e2e(st: Step, args, world) -> dict:
     """The same step with host buffers: every step copies its scene and target
     images in from pinned host memory and its loss and gradients (and I_i)
@@ -558,25 +607,32 @@ def run_serving(st: Step, args) -> dict:
     (seed 3), poses on a sphere of radius U[3, 6], resolutions uniform over
     640x480 / 1280x720 / 1920x1080 / 3840x2160, 24 GB admission budget; the
     first 10 % of requests are warm-up.  Batched (3 stream slots, up to 16
-    views per batch) against the same trace served one request at a time."""
+    views per batch) against the same trace served one request at a time.
+    The same comparison at 600 req/s, where requests contend for the GPU, is
+    reported under "at_600_per_s"."""
     import torch
     from paper_2411_12788_gb300 import serve
     n = args.serve_requests
     skip = n // 11
-    out = {"rate_per_s": 200.0, "requests_timed": n - skip, "warmup_requests": skip, "budget_gb": 24,
-           "scene_gaussians": st.g.n}
-    for name, streams, views in (("batched", 3, 16), ("one_at_a_time", 1, 1)):
-        trace = serve.poisson_trace(n, rate=200.0, seed=3)
-        srv = serve.RenderServer(st.g, budget_bytes=24 << 30, streams=streams, max_views=views)
-        srv.serve(trace)
-        stats = serve.latency_stats(trace, skip=skip)
-        stats.update({"streams": streams, "max_views": views, "batches": srv.batches_run,
-                      "mean_views_per_batch": srv.views_run / max(1, srv.batches_run),
-                      "peak_reserved_gb": srv.peak_reserved / 2**30})
-        out[name] = stats
-        torch.cuda.synchronize()
-    out["p99_speedup"] = out["one_at_a_time"]["p99_ms"] / out["batched"]["p99_ms"]
-    return out
+
+    def compare(rate):
+        out = {"rate_per_s": rate, "requests_timed": n - skip, "warmup_requests": skip, "budget_gb": 24,
+               "scene_gaussians": st.g.n}
+        for name, streams, views in (("batched", 3, 16), ("one_at_a_time", 1, 1)):
+            trace = serve.poisson_trace(n, rate=rate, seed=3)
+            srv = serve.RenderServer(st.g, budget_bytes=24 << 30, streams=streams, max_views=views)
+            srv.serve(trace)
+            stats = serve.latency_stats(trace, skip=skip)
+            stats.update({"streams": streams, "max_views": views, "batches": srv.batches_run,
+                          "mean_views_per_batch": srv.views_run / max(1, srv.batches_run),
+                          "peak_reserved_gb": srv.peak_reserved / 2**30})
+            out[name] = stats
+            torch.cuda.synchronize()
+        out["p99_speedup"] = out["one_at_a_time"]["p99_ms"] / out["batched"]["p99_ms"]
+        return out
+    res = compare(200.0)
+    res["at_600_per_s"] = compare(600.0)
+    return res
 
 
 def run_dense(args, iters: int = 3) -> dict:

@@ -18,6 +18,12 @@ Admission is two-phase because a batch's sort memory is only known after
 preprocessing: a request is admitted on an estimate (its tiles times a
 running entries-per-tile estimate), and the reservation is corrected to the
 exact workspace sizes once the batch's entry count is known.
+
+Each slot keeps its device buffers (workspaces and outputs) and grows them
+when a batch needs more, so requests do not go through the allocator; and
+each slot has a second, high-priority stream for batches above big_pixels
+pixels, the slowest requests, whose blocks are then scheduled first when
+they overlap smaller work.
 """
 from __future__ import annotations
 
@@ -57,7 +63,8 @@ class _Batch:
 
 class RenderServer:
     def __init__(self, g: raster.GaussianTensors, budget_bytes: int = 24 << 30, streams: int = 3,
-                 max_views: int = 16, keep_images: bool = False, cfg=None, entries_per_tile: float = 3000.0):
+                 max_views: int = 16, keep_images: bool = False, cfg=None, entries_per_tile: float = 3000.0,
+                 big_pixels: int | None = 4_000_000):
         self.g = g
         self.budget = int(budget_bytes)
         self.n_slots = int(streams)
@@ -65,7 +72,18 @@ class RenderServer:
         self.keep_images = keep_images
         self.cfg = cfg or raster.make_config()
         self.ept = float(entries_per_tile)          # running estimate of entries per tile
-        self.streams = [torch.cuda.Stream() for _ in range(self.n_slots)]
+        # each slot has a normal and a high-priority stream; batches of more
+        # than big_pixels pixels (the slowest requests, which set the latency
+        # tail) run on the high-priority one, so that their blocks are
+        # scheduled first when they overlap smaller work
+        self.big_pixels = big_pixels
+        lo, hi = torch.cuda.Stream.priority_range()
+        self.streams = [torch.cuda.Stream(priority=lo) for _ in range(self.n_slots)]
+        self.hi_streams = [torch.cuda.Stream(priority=hi) for _ in range(self.n_slots)]
+        # per-slot device buffers, grown on demand and reused by the slot's
+        # batches (a slot runs one batch at a time), so serving does not go
+        # through the allocator per request
+        self.slot_bufs = [dict() for _ in range(self.n_slots)]
         self.reserved = 0
         self.peak_reserved = 0
         self.batches_run = 0
@@ -84,19 +102,45 @@ class RenderServer:
         out = cam.width * cam.height * 24
         return pre + sort + out
 
+    # -------------------------------------------------------------- buffers
+    def _buf(self, slot: int, name: str, nbytes: int) -> torch.Tensor:
+        """The first nbytes of the slot's buffer `name` (uint8), grown by 25 %
+        headroom when too small."""
+        b = self.slot_bufs[slot].get(name)
+        if b is None or b.numel() < nbytes:
+            b = torch.empty(max(int(nbytes * 1.25), 256), dtype=torch.uint8, device="cuda")
+            self.slot_bufs[slot][name] = b
+        return b[:max(nbytes, 1)]
+
+    def _outputs(self, slot: int, plan) -> dict:
+        """Forward outputs of the plan carved from the slot's output buffer."""
+        P = int(plan.total_pixels)
+        layout = (("image", 3 * P, torch.float32), ("final_T", P, torch.float32), ("n_contrib", P, torch.int32),
+                  ("depth", P, torch.float32), ("imax", P, torch.int32))
+        offs, o = [], 0
+        for _, cnt, _ in layout:
+            offs.append(o)
+            o += (4 * cnt + 255) // 256 * 256
+        buf = self._buf(slot, "out", o)
+        return {name: buf[off: off + 4 * cnt].view(dt) for (name, cnt, dt), off in zip(layout, offs)}
+
     # -------------------------------------------------------------- one batch
     def _launch(self, reqs: list, slot: int, bid: int) -> _Batch:
-        s = self.streams[slot]
+        big = self.big_pixels is not None and sum(r.pixels for r in reqs) > self.big_pixels
+        s = self.hi_streams[slot] if big else self.streams[slot]
         est = sum(self._estimate(r.cam) for r in reqs)
         with torch.cuda.stream(s):
             cams = [r.cam for r in reqs]
             plan = raster.make_plan(self.g.n, cams)
-            pre_ws = torch.empty(raster.preprocess_workspace_size(plan), dtype=torch.uint8, device="cuda")
+            pre_ws = self._buf(slot, "pre", raster.preprocess_workspace_size(plan))
             raster.preprocess(plan, self.g.struct(), self.cfg, pre_ws, stream=s)
-            sort_ws = torch.empty(max(raster.bin_sort_workspace_size(plan), 1), dtype=torch.uint8, device="cuda")
+            sort_ws = self._buf(slot, "sort", raster.bin_sort_workspace_size(plan))
             raster.bin_sort(plan, pre_ws, sort_ws, stream=s)
-            outs = raster.alloc_outputs(plan, "cuda", want=("image", "final_T", "n_contrib", "depth", "imax"))
+            outs = self._outputs(slot, plan)
             raster.render_fwd(plan, self.cfg, pre_ws, sort_ws, outs, stream=s)
+            if self.keep_images:
+                for v, r in enumerate(reqs):
+                    r.image = raster.view_image(outs["image"], plan, v).clone()
             ev = torch.cuda.Event(enable_timing=True)
             ev.record(s)
         actual = pre_ws.numel() + sort_ws.numel() + sum(t.numel() * t.element_size() for t in outs.values())
@@ -105,11 +149,7 @@ class RenderServer:
             self.ept = 0.8 * self.ept + 0.2 * (plan.n_entries / tiles)
         self.reserved += actual - est               # correct the admission estimate
         self.peak_reserved = max(self.peak_reserved, self.reserved)
-        b = _Batch(bid, reqs, s, actual, ev, [pre_ws, sort_ws, outs])
-        if self.keep_images:
-            for v, r in enumerate(reqs):
-                r.image = raster.view_image(outs["image"], plan, v)
-        return b
+        return _Batch(bid, reqs, s, actual, ev, [])
 
     # -------------------------------------------------------------- the loop
     def serve(self, trace: list) -> list:

@@ -64,3 +64,34 @@ def test_l1_ssim_on_rendered_views_in_the_training_step():
     Lr, _, _ = OL.l1_ssim(imgs, ys, 0.2)
     assert abs(L.item() - Lr.item()) <= 1e-5 * Lr.item()
     assert all(torch.isfinite(v).all() for v in grads.values())
+
+
+def test_training_step_with_l1_ssim_at_full_size():
+    """500k Gaussians (SH 3), one 1600x1063 view, 0.8 L1 + 0.2 D-SSIM against
+    the seeded target: the loss and its image gradient match the oracle
+    evaluated on the rendered image, and the backward returns finite
+    gradients and the forward's I_i."""
+    _need_gpu()
+    sc = scenes.cluster_scene(500_000, 64, seed=0, sh_degree=3)
+    cam = scenes.ring_camera(0.3, 1600, 1063)
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, [cam])
+    tg = scenes.target_images([cam], seed=1)[0]
+    y = torch.from_numpy(tg.reshape(-1)).cuda()
+    L = torch.zeros(1, device="cuda")
+    d = torch.empty_like(fr.outs["image"])
+    raster.loss_l1_ssim(fr.plan, fr.outs["image"], y, L, d, 0.2)
+    grads = raster.alloc_grads(g)
+    grads["weight_sum"] = torch.zeros(int(fr.plan.n_items), device="cuda")
+    raster.render_bwd(fr.plan, g.struct(), fr.cfg, fr.pre_ws, fr.sort_ws, d, fr.outs["image"],
+                      fr.outs["n_contrib"], grads)
+    torch.cuda.synchronize()
+    x = raster.view_image(fr.outs["image"], fr.plan, 0).cpu().double().requires_grad_(True)
+    Lr, _, _ = OL.l1_ssim([x], [torch.from_numpy(tg).double()], 0.2)
+    (gr,) = torch.autograd.grad(Lr, [x])
+    assert abs(L.item() - Lr.item()) <= 1e-5 * Lr.item()
+    gg = d.cpu().double().reshape(gr.shape)
+    assert (gg - gr).abs().max().item() <= 2e-4 * gr.abs().max().item()
+    assert all(torch.isfinite(v).all() for v in grads.values())
+    a, b = grads["weight_sum"].double().cpu(), fr.outs["weight_sum"].double().cpu()
+    assert torch.all((a - b).abs() <= 1e-4 + 1e-5 * b.abs())
