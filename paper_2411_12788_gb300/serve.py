@@ -27,6 +27,7 @@ they overlap smaller work.
 """
 from __future__ import annotations
 
+import gc
 import math
 import time
 from dataclasses import dataclass, field
@@ -154,7 +155,17 @@ class RenderServer:
     # -------------------------------------------------------------- the loop
     def serve(self, trace: list) -> list:
         """Serves `trace` (Requests sorted by arrival) in real time; returns it
-        with `done` filled in."""
+        with `done` filled in.  Python's cyclic garbage collector is paused
+        for the duration (its sweeps stall the launch loop)."""
+        was = gc.isenabled()
+        gc.disable()
+        try:
+            return self._serve(trace)
+        finally:
+            if was:
+                gc.enable()
+
+    def _serve(self, trace: list) -> list:
         pending = list(trace)
         queue: list = []
         inflight: dict = {}
