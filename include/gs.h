@@ -376,6 +376,18 @@ gs_status gs_loss_l1_ssim(const gs_plan* plan, const float* image, const float* 
                           float* loss, float* dL_dimage, float* l1_out, float* ssim_out,
                           void* ws, size_t ws_bytes, void* stream);
 
+/* ---- failure detection self-check ---------------------------------------- */
+
+/* No counterpart in the paper: checks that the sort's bounded device wait
+ * gives up instead of hanging.  Runs the onesweep look-back for a tile whose
+ * predecessor never publishes its counts; every wait runs out after its bound
+ * (about a second), records the timeout in a status word, and the call
+ * returns GS_ERR_TIMEOUT with the context still usable (GS_OK would mean the
+ * wait did not detect the missing publisher).  scratch: device,
+ * GS_SELFTEST_SCRATCH_BYTES bytes, 16-byte aligned.  Synchronous. */
+#define GS_SELFTEST_SCRATCH_BYTES 4096u
+gs_status gs_selftest_wait_timeout(void* scratch, size_t scratch_bytes, void* stream);
+
 /* ---- inspection --------------------------------------------------------- */
 
 /* Device pointers into a preprocess workspace after gs_preprocess, for tests

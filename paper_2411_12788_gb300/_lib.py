@@ -15,6 +15,8 @@ LIB_PATH = os.path.join(HERE, "libgs.so")
 GS_TILE = 16
 GS_MAX_VIEWS = 64
 GS_FLAG_ZERO_ACCUM = 1
+GS_SELFTEST_SCRATCH_BYTES = 4096
+GS_ERR_TIMEOUT = 4
 
 STATUS = {0: "GS_OK", 1: "GS_ERR_INVALID_ARG", 2: "GS_ERR_CAPACITY", 3: "GS_ERR_CUDA",
           4: "GS_ERR_TIMEOUT", 5: "GS_ERR_DEVICE_CHECK"}
@@ -124,6 +126,7 @@ SIGNATURES = {
     "gs_loss_l1_ssim": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.c_void_p, C.c_float, C.c_void_p, C.c_void_p,
                                   C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "gs_loss_l1": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "gs_selftest_wait_timeout": (C.c_int, [C.c_void_p, C.c_size_t, C.c_void_p]),
     "gs_device_status": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.c_void_p]),
     "gs_inspect_preprocess": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.POINTER(PreprocessView)]),
     "gs_inspect_sort": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.POINTER(SortView)]),

@@ -333,6 +333,21 @@ gs_status gs_device_status(const gs_plan* plan, void* pre_ws, void* stream_) {
   return GS_OK;
 }
 
+gs_status gs_selftest_wait_timeout(void* scratch, size_t scratch_bytes, void* stream_) {
+  if (!scratch || scratch_bytes < GS_SELFTEST_SCRATCH_BYTES || (reinterpret_cast<uintptr_t>(scratch) & 15))
+    return GS_ERR_INVALID_ARG;
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  uint32_t* words = static_cast<uint32_t*>(scratch);
+  uint32_t* status = words + 3 * kRadix;
+  uint32_t word = 0;
+  cudaError_t e = cudaMemsetAsync(status, 0, 4, stream);
+  if (e == cudaSuccess) e = lookback_timeout_probe(words, status, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&word, status, 4, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  return (word & kStatusTimeout) ? GS_ERR_TIMEOUT : GS_OK;
+}
+
 gs_status gs_inspect_preprocess(const gs_plan* plan, const void* pre_ws, gs_preprocess_view* out) {
   if (!valid_plan(plan) || !pre_ws || !out) return GS_ERR_INVALID_ARG;
   const PreLayout L = pre_layout(*plan);

@@ -134,6 +134,8 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 size_t scan_block_bytes(int64_t n);
+// Self-test of the sort's bounded look-back wait (scratch: 3 * 256 words).
+cudaError_t lookback_timeout_probe(uint32_t* scratch, uint32_t* status, cudaStream_t stream);
 // out[k] = sum_{j<k} counts[idx[j]] (idx == nullptr: counts[j]); *total = sum of
 // all (device, 64-bit).
 cudaError_t gather_exclusive_scan(const uint32_t* counts, const uint32_t* idx, uint32_t* out,

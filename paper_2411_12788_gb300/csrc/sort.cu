@@ -116,6 +116,58 @@ __global__ void __launch_bounds__(kRadix) radix_scan_hist_kernel(uint32_t* hist)
   h[threadIdx.x] = s[threadIdx.x] - v;
 }
 
+// Decoupled look-back for digit d of `tile`: the sum of the predecessors'
+// counts for d, read 8 predecessors per round (the loads of a window are
+// independent, so a round costs one L2 latency) back to the first published
+// inclusive prefix.  A round that meets a predecessor with nothing published
+// yet is repeated; after kSpinLimit such rounds the wait gives up, records
+// kStatusTimeout and returns what it has (the sort result is then wrong and
+// the host reports GS_ERR_TIMEOUT), so a missing publisher cannot hang the GPU.
+__device__ __forceinline__ uint32_t lookback_exclusive(const uint32_t* lookback, int64_t tile, int d,
+                                                       uint32_t* status) {
+  uint32_t exclusive = 0;
+  int64_t j = tile - 1;
+  long spins = 0;
+  constexpr int kWin = 8;
+  while (j >= 0) {
+    uint32_t st[kWin];
+#pragma unroll
+    for (int w = 0; w < kWin; ++w)
+      st[w] = (j - w >= 0) ? *(const volatile uint32_t*)(lookback + (j - w) * kRadix + d) : (uint32_t)kFlagPrefix;
+    uint32_t add = 0;
+    int used = 0;
+    bool found = false, stalled = false;
+#pragma unroll
+    for (int w = 0; w < kWin; ++w) {
+      if (found || stalled) continue;
+      const uint32_t flag = st[w] & ~kValueMask;
+      if (flag == 0) {
+        stalled = true;
+        continue;
+      }
+      add += st[w] & kValueMask;
+      ++used;
+      if (flag == kFlagPrefix) found = true;
+    }
+    exclusive += add;
+    j -= used;
+    if (found) break;
+    if (stalled && ++spins > kSpinLimit) {
+      atomicOr(status, kStatusTimeout);
+      break;
+    }
+  }
+  return exclusive;
+}
+
+// Self-test of the bounded wait: one block looks back from tile 1 over a
+// tile 0 that never publishes (its counts are zero), so every digit's wait
+// runs out; out[d] receives what the wait returned.
+__global__ void lookback_timeout_probe_kernel(const uint32_t* __restrict__ lookback, uint32_t* __restrict__ status,
+                                              uint32_t* __restrict__ out) {
+  out[threadIdx.x] = lookback_exclusive(lookback, 1, (int)threadIdx.x, status);
+}
+
 // Dynamic shared memory of the pass kernel: the CTA's keys (original order,
 // then reused for the keys in output order), its values (original order) and
 // its values in output order.
@@ -233,43 +285,11 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
     }
   }
 
-  // 3. decoupled look-back for this digit, 8 predecessors per round: the
-  //    loads of a window are independent, so a round costs one L2 latency
+  // 3. decoupled look-back for this digit, then this tile's inclusive prefix
   uint32_t exclusive = 0;
   if (tile > 0) {
-    const int d = tid;
-    int64_t j = tile - 1;
-    long spins = 0;
-    constexpr int kWin = 8;
-    while (j >= 0) {
-      uint32_t st[kWin];
-#pragma unroll
-      for (int w = 0; w < kWin; ++w)
-        st[w] = (j - w >= 0) ? *(volatile uint32_t*)(lookback + (j - w) * kRadix + d) : (uint32_t)kFlagPrefix;
-      uint32_t add = 0;
-      int used = 0;
-      bool found = false, stalled = false;
-#pragma unroll
-      for (int w = 0; w < kWin; ++w) {
-        if (found || stalled) continue;
-        const uint32_t flag = st[w] & ~kValueMask;
-        if (flag == 0) {
-          stalled = true;
-          continue;
-        }
-        add += st[w] & kValueMask;
-        ++used;
-        if (flag == kFlagPrefix) found = true;
-      }
-      exclusive += add;
-      j -= used;
-      if (found) break;
-      if (stalled && ++spins > kSpinLimit) {
-        atomicOr(status, kStatusTimeout);
-        break;
-      }
-    }
-    *(volatile uint32_t*)(lookback + tile * kRadix + d) = kFlagPrefix | (exclusive + cta_count);
+    exclusive = lookback_exclusive(lookback, tile, tid, status);
+    *(volatile uint32_t*)(lookback + tile * kRadix + tid) = kFlagPrefix | (exclusive + cta_count);
   }
 
   // 4. CTA-local exclusive scan over digits (for the shared-memory staging)
@@ -448,6 +468,14 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
     cudaMemcpyAsync(keys, kin, n * 4, cudaMemcpyDeviceToDevice, stream);
     cudaMemcpyAsync(vals, vin, n * 4, cudaMemcpyDeviceToDevice, stream);
   }
+  return cudaGetLastError();
+}
+
+cudaError_t lookback_timeout_probe(uint32_t* scratch, uint32_t* status, cudaStream_t stream) {
+  // scratch: [2][kRadix] look-back words (tile 0 never published) + [kRadix] outputs
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * kRadix * sizeof(uint32_t), stream);
+  if (e != cudaSuccess) return e;
+  lookback_timeout_probe_kernel<<<1, kRadix, 0, stream>>>(scratch, status, scratch + 2 * kRadix);
   return cudaGetLastError();
 }
 

@@ -258,6 +258,14 @@ def gather_scene(g: "GaussianTensors", idx: torch.Tensor, stream=None) -> "Gauss
     return out
 
 
+def selftest_wait_timeout(stream=None) -> int:
+    """Runs the sort's look-back wait against a predecessor that never
+    publishes (gs_selftest_wait_timeout); returns the gs_status, which is
+    GS_ERR_TIMEOUT when the bounded wait works."""
+    ws = torch.empty(_lib.GS_SELFTEST_SCRATCH_BYTES, dtype=torch.uint8, device="cuda")
+    return int(lib().gs_selftest_wait_timeout(_ptr(ws), ws.numel(), _stream(stream)))
+
+
 def device_status(plan, pre_ws, stream=None) -> int:
     return int(lib().gs_device_status(C.byref(plan), _ptr(pre_ws), _stream(stream)))
 

@@ -427,3 +427,22 @@ def test_backward_overwrite_mode_equals_accumulate_into_zeros(deg):
     # coefficients beyond the degree: zero in both modes
     K = (deg + 1) ** 2
     assert (nan["d_sh"][:, K:] == 0).all() and (ones["d_sh"][:, K:] == 1).all()
+
+
+# ---------------------------------------------------------------- failure detection
+def test_bounded_wait_reports_timeout_and_context_survives():
+    """A look-back wait whose predecessor never publishes gives up after its
+    bound and reports GS_ERR_TIMEOUT; the context keeps working."""
+    _need_gpu()
+    import time
+    t0 = time.perf_counter()
+    st = raster.selftest_wait_timeout()
+    dt = time.perf_counter() - t0
+    assert st == raster._lib.GS_ERR_TIMEOUT
+    assert dt < 30.0
+    sc = scenes.box_scene(256, seed=3)
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, [scenes.origin_camera(64, 64, 64.0)])
+    torch.cuda.synchronize()
+    assert raster.device_status(fr.plan, fr.pre_ws) == 0
+    assert torch.isfinite(fr.outs["image"]).all()

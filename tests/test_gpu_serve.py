@@ -50,3 +50,32 @@ def test_one_at_a_time_is_fifo_and_budget_holds():
     srv.serve(trace)
     assert all(r.done is not None for r in trace)
     assert srv.batches_run == len(trace)
+
+
+def test_allocation_failure_propagates_and_server_recovers():
+    """Host-side fault injection: the third buffer request of the trace
+    fails; the error reaches the caller, the collector is restored, and the
+    same server serves the next trace."""
+    _need_gpu()
+    import gc
+    sc = scenes.cluster_scene(50_000, 64, seed=10, sh_degree=0)
+    g = raster.GaussianTensors.from_scene(sc)
+    srv = serve.RenderServer(g, budget_bytes=1 << 30, streams=2, max_views=4)
+    real = srv._buf
+    calls = {"n": 0}
+
+    def failing(slot, name, nbytes):
+        calls["n"] += 1
+        if calls["n"] == 3:
+            raise RuntimeError("injected allocation failure")
+        return real(slot, name, nbytes)
+    srv._buf = failing
+    with pytest.raises(RuntimeError, match="injected"):
+        srv.serve(serve.poisson_trace(8, rate=5000.0, seed=11, sizes=SIZES))
+    assert gc.isenabled()
+    srv._buf = real
+    torch.cuda.synchronize()
+    srv.reserved = 0
+    trace = serve.poisson_trace(8, rate=5000.0, seed=12, sizes=SIZES)
+    srv.serve(trace)
+    assert all(r.done is not None for r in trace)
