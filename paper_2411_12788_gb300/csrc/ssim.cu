@@ -15,9 +15,10 @@
 //
 // One CTA per 32x32 output tile and channel, everything in shared memory:
 // x, y with a 10-pixel halo (52x52), the horizontal pass of the five moments
-// (52x42), their vertical pass in place (sliding window down each column,
-// 42x42), a, b, c on that 42x42 region, and their two blur passes back to the
-// 32x32 tile.  Each CTA writes its partial L1 and SSIM sums; a one-block
+// (52x42, six outputs per work item from registers), their vertical pass in
+// place (each column in registers, 42x42), a, b, c on that 42x42
+// region, and their two blur passes back to the 32x32 tile (four outputs per
+// work item).  Each CTA writes its partial L1 and SSIM sums; a one-block
 // kernel adds them in double.
 #include "common.cuh"
 
@@ -89,44 +90,53 @@ __global__ void __launch_bounds__(kSsimThreads) l1_ssim_kernel(SsimParams P) {
   }
   __syncthreads();
 
-  // 2. horizontal pass of the five moments: rows 0..51, cols 0..41
-  for (int i = tid; i < kIn * kMid; i += kSsimThreads) {
-    const int r = i / kMid, c = i - r * kMid;
-    float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+  // 2. horizontal pass of the five moments: rows 0..51, cols 0..41, six
+  //    consecutive outputs per work item from 16 loaded values
+  constexpr int kHG = 6;                                  // 42 = 7 x 6
+  for (int i = tid; i < kIn * (kMid / kHG); i += kSsimThreads) {
+    const int r = i / (kMid / kHG), c0 = (i - r * (kMid / kHG)) * kHG;
+    float xv[kHG + kW - 1], yv[kHG + kW - 1];
 #pragma unroll
-    for (int t = 0; t < kW; ++t) {
-      const float w = c_win[t], xv = S.in[0][r][c + t], yv = S.in[1][r][c + t];
-      const float wx = w * xv, wy = w * yv;
-      mx += wx;
-      my += wy;
-      exx = fmaf(wx, xv, exx);
-      eyy = fmaf(wy, yv, eyy);
-      exy = fmaf(wx, yv, exy);
+    for (int t = 0; t < kHG + kW - 1; ++t) {
+      xv[t] = S.in[0][r][c0 + t];
+      yv[t] = S.in[1][r][c0 + t];
     }
-    S.mom[0][r][c] = mx;
-    S.mom[1][r][c] = my;
-    S.mom[2][r][c] = exx;
-    S.mom[3][r][c] = eyy;
-    S.mom[4][r][c] = exy;
+#pragma unroll
+    for (int o = 0; o < kHG; ++o) {
+      float mx = 0.f, my = 0.f, exx = 0.f, eyy = 0.f, exy = 0.f;
+#pragma unroll
+      for (int t = 0; t < kW; ++t) {
+        const float w = c_win[t], a = xv[o + t], b = yv[o + t];
+        const float wx = w * a, wy = w * b;
+        mx += wx;
+        my += wy;
+        exx = fmaf(wx, a, exx);
+        eyy = fmaf(wy, b, eyy);
+        exy = fmaf(wx, b, exy);
+      }
+      S.mom[0][r][c0 + o] = mx;
+      S.mom[1][r][c0 + o] = my;
+      S.mom[2][r][c0 + o] = exx;
+      S.mom[3][r][c0 + o] = eyy;
+      S.mom[4][r][c0 + o] = exy;
+    }
   }
   __syncthreads();
 
-  // 3. vertical pass in place: thread (q, column) slides down the column;
-  //    output row r (0..41) needs input rows r..r+10 and is written after
-  //    row r+10 has been read
+  // 3. vertical pass in place: thread (q, column) holds the column's 52
+  //    values in registers and writes its 42 outputs back over the first
+  //    rows (the loops are unrolled, so the window needs no moves)
   if (tid < 5 * kMid) {
     const int q = tid / kMid, c = tid - q * kMid;
-    float win[kW];
+    float col[kIn];
 #pragma unroll
-    for (int t = 0; t < kW - 1; ++t) win[t] = S.mom[q][t][c];
+    for (int r = 0; r < kIn; ++r) col[r] = S.mom[q][r][c];
+#pragma unroll
     for (int r = 0; r < kMid; ++r) {
-      win[kW - 1] = S.mom[q][r + kW - 1][c];
       float acc = 0.f;
 #pragma unroll
-      for (int t = 0; t < kW; ++t) acc = fmaf(c_win[t], win[t], acc);
+      for (int t = 0; t < kW; ++t) acc = fmaf(c_win[t], col[r + t], acc);
       S.mom[q][r][c] = acc;
-#pragma unroll
-      for (int t = 0; t < kW - 1; ++t) win[t] = win[t + 1];
     }
   }
   __syncthreads();
@@ -159,45 +169,60 @@ __global__ void __launch_bounds__(kSsimThreads) l1_ssim_kernel(SsimParams P) {
   __syncthreads();
 
   // 5. horizontal blur of a, b, c: rows 0..41, cols 0..31, into in[] (3 planes
-  //    of 42x32 laid out in the 2x52x52 buffer)
+  //    of 42x32 laid out in the 2x52x52 buffer), four outputs per work item
+  constexpr int kBG = 4;
   float* hb = &S.in[0][0][0];
-  for (int i = tid; i < kMid * kT; i += kSsimThreads) {
-    const int r = i / kT, c = i - r * kT;
-    float ga = 0.f, gb = 0.f, gc = 0.f;
+  for (int i = tid; i < kMid * (kT / kBG); i += kSsimThreads) {
+    const int r = i / (kT / kBG), c0 = (i - r * (kT / kBG)) * kBG;
 #pragma unroll
-    for (int t = 0; t < kW; ++t) {
-      const float w = c_win[t];
-      ga = fmaf(w, S.mom[0][r][c + t], ga);
-      gb = fmaf(w, S.mom[2][r][c + t], gb);
-      gc = fmaf(w, S.mom[4][r][c + t], gc);
+    for (int q = 0; q < 3; ++q) {
+      const float* src = &S.mom[2 * q][r][c0];            // planes 0, 2, 4 hold a, b, c
+      float v[kBG + kW - 1];
+#pragma unroll
+      for (int t = 0; t < kBG + kW - 1; ++t) v[t] = src[t];
+#pragma unroll
+      for (int o = 0; o < kBG; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int t = 0; t < kW; ++t) acc = fmaf(c_win[t], v[o + t], acc);
+        hb[(q * kMid + r) * kT + c0 + o] = acc;
+      }
     }
-    hb[(0 * kMid + r) * kT + c] = ga;
-    hb[(1 * kMid + r) * kT + c] = gb;
-    hb[(2 * kMid + r) * kT + c] = gc;
   }
   __syncthreads();
 
-  // 6. vertical blur and the gradient of the tile's pixels
+  // 6. vertical blur and the gradient: four consecutive rows of one column per
+  //    work item (32 columns x 8 row groups = the 256 threads)
   float l1_sum = 0.f;
-  for (int i = tid; i < kT * kT; i += kSsimThreads) {
-    const int r = i / kT, c = i - r * kT;
-    const int gx = ox + c, gy = oy + r;
-    if (gx >= V.width || gy >= V.height) continue;
-    float ga = 0.f, gb = 0.f, gc = 0.f;
+  {
+    constexpr int kVG = 4;
+    const int c = tid % kT, r0 = (tid / kT) * kVG;
+    float g[3][kVG];
 #pragma unroll
-    for (int t = 0; t < kW; ++t) {
-      const float w = c_win[t];
-      ga = fmaf(w, hb[(0 * kMid + r + t) * kT + c], ga);
-      gb = fmaf(w, hb[(1 * kMid + r + t) * kT + c], gb);
-      gc = fmaf(w, hb[(2 * kMid + r + t) * kT + c], gc);
+    for (int q = 0; q < 3; ++q) {
+      float v[kVG + kW - 1];
+#pragma unroll
+      for (int t = 0; t < kVG + kW - 1; ++t) v[t] = hb[(q * kMid + r0 + t) * kT + c];
+#pragma unroll
+      for (int o = 0; o < kVG; ++o) {
+        float acc = 0.f;
+#pragma unroll
+        for (int t = 0; t < kW; ++t) acc = fmaf(c_win[t], v[o + t], acc);
+        g[q][o] = acc;
+      }
     }
-    const int64_t o = (int64_t)gy * V.width + gx;
-    const float xv = X[o], yv = Y[o];
-    const float d = xv - yv;
-    l1_sum += fabsf(d);
-    const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
-    const float dssim = ga + 2.f * xv * gb + yv * gc;
-    P.grad[V.base + ch * hw + o] = P.w_l1 * sgn - P.w_ssim * dssim;
+#pragma unroll
+    for (int o = 0; o < kVG; ++o) {
+      const int gx = ox + c, gy = oy + r0 + o;
+      if (gx >= V.width || gy >= V.height) continue;
+      const int64_t off = (int64_t)gy * V.width + gx;
+      const float xv = X[off], yv = Y[off];
+      const float d = xv - yv;
+      l1_sum += fabsf(d);
+      const float sgn = d > 0.f ? 1.f : (d < 0.f ? -1.f : 0.f);
+      const float dssim = g[0][o] + 2.f * xv * g[1][o] + yv * g[2][o];
+      P.grad[V.base + ch * hw + off] = P.w_l1 * sgn - P.w_ssim * dssim;
+    }
   }
 
   // partial sums of the CTA
