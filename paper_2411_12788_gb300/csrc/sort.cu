@@ -8,12 +8,13 @@
 //   * each CTA of the pass kernel takes the next tile of 3840 keys (dynamic
 //     tile id, so every predecessor tile is already running), ranks its keys
 //     stably by digit inside each warp (the lanes sharing a digit found by
-//     OR-ing each lane's bit into a shared word per warp and digit and
-//     reading it back), publishes its per-digit
-//     counts, and looks back over its predecessors' published counts
-//     (decoupled look-back) to find its global offset per digit; keys are
-//     then staged in shared memory in output order and written out so that
-//     runs of equal digits are coalesced.
+//     one ballot per digit bit, the running per-warp digit counts kept by
+//     shared atomics whose results are collected after all rows), publishes
+//     its per-digit counts, stages keys and values in shared memory in
+//     output order, and only then looks back over its predecessors'
+//     published counts (decoupled look-back) for its global offset per
+//     digit, so that the predecessors have had longer to publish; the staged
+//     keys are written out in runs of equal digits, which coalesce.
 // The look-back spin is bounded: after kSpinLimit polls the CTA records
 // kStatusTimeout in the status word and carries on (the result is then
 // wrong, and the host reports GS_ERR_TIMEOUT), so a bug cannot hang the GPU.
@@ -183,9 +184,6 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
   uint32_t* s_keys = s_dyn;                       // keys: loaded, then in output order
   uint32_t* s_vin = s_dyn + kSortTile;            // values as loaded
   uint32_t* s_vals = s_dyn + 2 * kSortTile;       // values in output order
-  // per warp and digit: the lanes holding it (ranking only; aliases s_vals,
-  // which is written after the ranking)
-  uint32_t (*s_match)[kRadix] = reinterpret_cast<uint32_t (*)[kRadix]>(s_vals);
   __shared__ uint32_t s_warp_hist[kWarps][kRadix];
   __shared__ uint32_t s_cta_start[kRadix];
   __shared__ uint32_t s_out_base[kRadix];         // output index of the CTA's first key of each digit, minus its start
@@ -201,7 +199,6 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
   }
   for (int i = tid; i < kWarps * kRadix; i += kSortThreads) {
     (&s_warp_hist[0][0])[i] = 0;
-    (&s_match[0][0])[i] = 0;
   }
   __syncthreads();
   const int64_t tile = s_tile;
@@ -229,7 +226,13 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
   __syncthreads();
 
   // 1. rank the keys stably by digit inside each warp (warp-striped: warp w
-  //    owns keys [480 w, 480 w + 480) of the tile)
+  //    owns keys [480 w, 480 w + 480) of the tile).  Per key row k the lanes
+  //    sharing a digit are found with one ballot per digit bit; their lowest
+  //    lane adds their number to the warp's running count of the digit with
+  //    one shared atomic, whose old value (the count of that digit in rows
+  //    before k) is only collected after the last row, so the rows do not
+  //    wait on one another.  meta[k] = leader lane | (same-digit lanes below
+  //    this one) << 5 | (leader only) old count << 10.
   uint32_t key[kSortItemsPerThread];
   uint32_t rank[kSortItemsPerThread];
   const uint32_t lt = lanemask_lt();
@@ -239,30 +242,30 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
     const int i = warp_start + k * 32 + lane;
     key[k] = i < count ? s_keys[i] : 0u;
   }
+  uint32_t* whist = s_warp_hist[warp];
 #pragma unroll
   for (int k = 0; k < kSortItemsPerThread; ++k) {
     const int i = warp_start + k * 32 + lane;
     const bool valid = i < count;
     const uint32_t d = (key[k] >> shift) & (kRadix - 1);
-    // lanes holding the same digit: each ORs its lane bit into the warp's
-    // word for its digit, then reads the word back
-    if (valid) atomicOr(&s_match[warp][d], 1u << lane);
-    __syncwarp();
-    const uint32_t peers = valid ? s_match[warp][d] : 0u;
-    __syncwarp();
-    rank[k] = 0;
-    if (valid) {
-      int leader = __ffs(peers) - 1;
-      uint32_t before = 0;
-      if (lane == leader) {
-        before = s_warp_hist[warp][d];
-        s_warp_hist[warp][d] = before + __popc(peers);
-        s_match[warp][d] = 0u;
-      }
-      before = __shfl_sync(peers, before, leader);
-      rank[k] = before + __popc(peers & lt);
+    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < kRadixBits; ++b) {
+      const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
+      peers &= ((d >> b) & 1u) ? bal : ~bal;
     }
+    const uint32_t leader = valid ? (uint32_t)(__ffs(peers) - 1) : (uint32_t)lane;
+    uint32_t m = leader | ((uint32_t)__popc(peers & lt) << 5);
+    if (valid && (uint32_t)lane == leader) m |= atomicAdd(&whist[d], (uint32_t)__popc(peers)) << 10;
+    // orders this row's counter update before the next row's (the next
+    // leader may be another lane)
     __syncwarp();
+    rank[k] = m;
+  }
+#pragma unroll
+  for (int k = 0; k < kSortItemsPerThread; ++k) {
+    const uint32_t m = rank[k];
+    rank[k] = (__shfl_sync(0xffffffffu, m, (int)(m & 31u)) >> 10) + ((m >> 5) & 31u);
   }
   __syncthreads();
 
@@ -285,14 +288,8 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
     }
   }
 
-  // 3. decoupled look-back for this digit, then this tile's inclusive prefix
-  uint32_t exclusive = 0;
-  if (tile > 0) {
-    exclusive = lookback_exclusive(lookback, tile, tid, status);
-    *(volatile uint32_t*)(lookback + tile * kRadix + tid) = kFlagPrefix | (exclusive + cta_count);
-  }
-
-  // 4. CTA-local exclusive scan over digits (for the shared-memory staging)
+  // 3. CTA-local exclusive scan over digits (for the shared-memory staging)
+  uint32_t start;
   {
     const int d = tid;
     // warp-level inclusive scan then across warps
@@ -307,13 +304,14 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
     __syncthreads();
     uint32_t add = 0;
     for (int w = 0; w < warp; ++w) add += s_warp_tot[w];
-    uint32_t start = v - cta_count + add;
+    start = v - cta_count + add;
     s_cta_start[d] = start;
-    s_out_base[d] = digit_base[d] + exclusive - start;
   }
   __syncthreads();
 
-  // 5. stage keys and values in output order
+  // 4. stage keys and values in output order (needs only CTA-local offsets,
+  //    so it runs before the look-back and gives the predecessors more time
+  //    to publish their prefixes)
 #pragma unroll
   for (int k = 0; k < kSortItemsPerThread; ++k) {
     const int i = warp_start + k * 32 + lane;
@@ -324,6 +322,14 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
       s_vals[pos] = s_vin[i];
     }
   }
+
+  // 5. decoupled look-back for this digit, then this tile's inclusive prefix
+  uint32_t exclusive = 0;
+  if (tile > 0) {
+    exclusive = lookback_exclusive(lookback, tile, tid, status);
+    *(volatile uint32_t*)(lookback + tile * kRadix + tid) = kFlagPrefix | (exclusive + cta_count);
+  }
+  s_out_base[tid] = digit_base[tid] + exclusive - start;
   __syncthreads();
 
   // 6. write out: runs of equal digits are contiguous in the output
