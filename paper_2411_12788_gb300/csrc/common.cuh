@@ -117,7 +117,7 @@ cudaError_t once_per_device(std::atomic<uint64_t>& done, F&& init) {
 // ---- onesweep radix sort sizing (sort.cu) ----------------------------------
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;
-constexpr int kSortThreads = 256;
+constexpr int kSortThreads = 512;
 constexpr int kSortItemsPerThread = 15;
 constexpr int kSortTile = kSortThreads * kSortItemsPerThread;   // keys per CTA tile
 

@@ -5,7 +5,7 @@
 //
 // Radix sort, per 8-bit digit pass:
 //   * one histogram kernel counts every pass's digits in a single read;
-//   * each CTA of the pass kernel takes the next tile of 3840 keys (dynamic
+//   * each CTA of the pass kernel takes the next tile of 7680 keys (dynamic
 //     tile id, so every predecessor tile is already running), ranks its keys
 //     stably by digit inside each warp (the lanes sharing a digit found by
 //     one ballot per digit bit, the running per-warp digit counts kept by
@@ -29,6 +29,7 @@ constexpr uint32_t kFlagPrefix = 2u << 30;
 constexpr uint32_t kValueMask = (1u << 30) - 1;
 constexpr int kMaxPasses = 4;
 constexpr int kWarps = kSortThreads / 32;
+static_assert(kSortThreads % kRadix == 0, "one digit per thread in the digit phases");
 constexpr int kWarpKeys = kSortItemsPerThread * 32;
 constexpr long kSpinLimit = 1L << 20;
 
@@ -175,7 +176,7 @@ __global__ void lookback_timeout_probe_kernel(const uint32_t* __restrict__ lookb
 constexpr size_t kOnesweepDynSmem = 3 * (size_t)kSortTile * sizeof(uint32_t);
 constexpr long kCopyWaitLimit = 1L << 22;
 
-__global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
+__global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift,
     const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ counter,
@@ -269,10 +270,12 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
   }
   __syncthreads();
 
-  // 2. per digit: offsets of each warp inside the CTA and the CTA's count.
+  // 2. per digit (threads < kRadix, one digit each): offsets of each warp
+  //    inside the CTA and the CTA's count, published for the successors
+  const bool digit_thread = tid < kRadix;
   uint32_t cta_count = 0;
-  {
-    const int d = tid;   // kSortThreads == kRadix
+  if (digit_thread) {
+    const int d = tid;
     for (int w = 0; w < kWarps; ++w) {
       uint32_t c = s_warp_hist[w][d];
       s_warp_hist[w][d] = cta_count;
@@ -288,24 +291,25 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
     }
   }
 
-  // 3. CTA-local exclusive scan over digits (for the shared-memory staging)
-  uint32_t start;
+  // 3. CTA-local exclusive scan over digits (for the shared-memory staging):
+  //    warp-level inclusive scans, then across the digit warps
+  uint32_t start = 0;
   {
-    const int d = tid;
-    // warp-level inclusive scan then across warps
     uint32_t v = cta_count;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
       uint32_t t = __shfl_up_sync(0xffffffffu, v, off);
       if (lane >= off) v += t;
     }
-    __shared__ uint32_t s_warp_tot[kWarps];
-    if (lane == 31) s_warp_tot[warp] = v;
+    __shared__ uint32_t s_warp_tot[kRadix / 32];
+    if (digit_thread && lane == 31) s_warp_tot[warp] = v;
     __syncthreads();
-    uint32_t add = 0;
-    for (int w = 0; w < warp; ++w) add += s_warp_tot[w];
-    start = v - cta_count + add;
-    s_cta_start[d] = start;
+    if (digit_thread) {
+      uint32_t add = 0;
+      for (int w = 0; w < warp; ++w) add += s_warp_tot[w];
+      start = v - cta_count + add;
+      s_cta_start[tid] = start;
+    }
   }
   __syncthreads();
 
@@ -324,12 +328,14 @@ __global__ void __launch_bounds__(kSortThreads, 4) radix_onesweep_kernel(
   }
 
   // 5. decoupled look-back for this digit, then this tile's inclusive prefix
-  uint32_t exclusive = 0;
-  if (tile > 0) {
-    exclusive = lookback_exclusive(lookback, tile, tid, status);
-    *(volatile uint32_t*)(lookback + tile * kRadix + tid) = kFlagPrefix | (exclusive + cta_count);
+  if (digit_thread) {
+    uint32_t exclusive = 0;
+    if (tile > 0) {
+      exclusive = lookback_exclusive(lookback, tile, tid, status);
+      *(volatile uint32_t*)(lookback + tile * kRadix + tid) = kFlagPrefix | (exclusive + cta_count);
+    }
+    s_out_base[tid] = digit_base[tid] + exclusive - start;
   }
-  s_out_base[tid] = digit_base[tid] + exclusive - start;
   __syncthreads();
 
   // 6. write out: runs of equal digits are contiguous in the output

@@ -387,7 +387,14 @@ def test_training_scale_sampled_pixels():
     dz = np.diff(z.view(np.uint32).astype(np.int64))
     assert np.all(dz[same] >= 0)
     assert np.all(np.diff(it)[same & (dz == 0)] > 0)
-    assert np.bincount(it, minlength=sc.n).sum() == fr.plan.n_entries
+    # a permutation of the duplicated entries: every item as often as the
+    # tiles it was counted on, and every entry in its own tile's range
+    np.testing.assert_array_equal(np.bincount(it, minlength=sc.n), st["tiles"].numpy().astype(np.int64))
+    rg = so["ranges"].numpy().astype(np.int64)
+    nonempty = rg[:, 1] > rg[:, 0]
+    assert rg[nonempty, 0].min() == 0 and rg[nonempty, 1].max() == fr.plan.n_entries
+    assert np.all(t[rg[nonempty, 0]] == np.nonzero(nonempty)[0]) and np.all(t[rg[nonempty, 1] - 1] == np.nonzero(nonempty)[0])
+    assert int((rg[nonempty, 1] - rg[nonempty, 0]).sum()) == fr.plan.n_entries
 
 
 # ---------------------------------------------------------------- gradient buffer modes
