@@ -249,12 +249,15 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
     const int i = warp_start + k * 32 + lane;
     const bool valid = i < count;
     const uint32_t d = (key[k] >> shift) & (kRadix - 1);
-    uint32_t peers = __ballot_sync(0xffffffffu, valid);
+    // diff: the lanes whose digit differs from this lane's (or that hold no
+    // key); a bit's ballot XOR this lane's bit replicated marks them
+    uint32_t diff = ~__ballot_sync(0xffffffffu, valid);
 #pragma unroll
     for (int b = 0; b < kRadixBits; ++b) {
-      const uint32_t bal = __ballot_sync(0xffffffffu, (d >> b) & 1u);
-      peers &= ((d >> b) & 1u) ? bal : ~bal;
+      const uint32_t bit = (d >> b) & 1u;
+      diff |= __ballot_sync(0xffffffffu, bit) ^ (0u - bit);
     }
+    const uint32_t peers = ~diff;
     const uint32_t leader = valid ? (uint32_t)(__ffs(peers) - 1) : (uint32_t)lane;
     uint32_t m = leader | ((uint32_t)__popc(peers & lt) << 5);
     if (valid && (uint32_t)lane == leader) m |= atomicAdd(&whist[d], (uint32_t)__popc(peers)) << 10;
