@@ -37,7 +37,7 @@ WORKLOAD = ("batched fwd+bwd, 1M Gaussians SH3 (64-cluster + shell scene), 8 vie
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
@@ -106,7 +106,7 @@ class ClockSampler:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
             self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+                                          "-lms", "50"], stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
 
@@ -435,6 +435,9 @@ def run_strategies(st: Step, reps: int = 5) -> dict:
     sample_ms = e0.elapsed_time(e1) / reps
     us = [1.0 - torch.rand(int(c.width) * int(c.height), device="cuda", generator=g) for c in st.cams]
     ks = [int(c.width) * int(c.height) // 10 for c in st.cams]
+    from paper_2411_12788_gb300 import _lib
+    kernel_times()                                   # drain earlier records
+    _lib.lib().gs_timing_enable(1)
     e0.record(stream)
     drawn = 0
     for _ in range(reps):
@@ -445,6 +448,8 @@ def run_strategies(st: Step, reps: int = 5) -> dict:
                                         ks[v])["points"].shape[0])
     e1.record(stream)
     torch.cuda.synchronize()
+    _lib.lib().gs_timing_enable(0)
+    depth_dev_ms = sum(v["ms"] for v in kernel_times().values()) / reps
     depth_ms = e0.elapsed_time(e1) / reps
     # fused L1 + D-SSIM loss and gradient over the 8 views (the C1 objective)
     L = torch.zeros(1, device="cuda")
@@ -475,9 +480,10 @@ def run_strategies(st: Step, reps: int = 5) -> dict:
     return {"sample_gaussians_ms": sample_ms, "sampled": int(kept.numel()), "of_positive": 2 * k,
             "loss_l1_ssim_ms_8_views": ssim_ms,
             "clone_critical_ms": clone_ms, "cloned": int(crit.numel()),
-            "depth_points_ms_8_views": depth_ms, "depth_points_per_call": drawn // reps,
-            "note": "depth_points includes one host read of the drawn count per view (the Python binding "
-                    "slices its outputs)"}
+            "depth_points_ms_8_views": depth_ms, "depth_points_device_ms_8_views": depth_dev_ms,
+            "depth_points_per_call": drawn // reps,
+            "note": "depth_points_ms includes one host read of the drawn count per view (the Python binding "
+                    "slices its outputs); depth_points_device_ms sums the event-timed kernels of those calls"}
 
 
 def run_c1_step(iters: int = 5) -> dict:
