@@ -71,13 +71,17 @@ def tile_lists(mean2d, conic, opacity, valid, width, height, alpha_min=1.0 / 255
     with np.errstate(divide="ignore", invalid="ignore"):
         sxx = np.where(ok, C / det, 0.0)       # inverse conic = 2-D covariance
         syy = np.where(ok, A / det, 0.0)
-    rx = np.sqrt(np.maximum(tau, 0) * sxx)
-    ry = np.sqrt(np.maximum(tau, 0) * syy)
-    # generous candidate range (one extra tile each side), clipped to the grid
-    tx0 = np.clip(np.floor((mean2d[:, 0] - rx - 15.5) / tile) - 1, 0, tx_n - 1)
-    tx1 = np.clip(np.floor((mean2d[:, 0] + rx - 0.5) / tile) + 1, 0, tx_n - 1)
-    ty0 = np.clip(np.floor((mean2d[:, 1] - ry - 15.5) / tile) - 1, 0, ty_n - 1)
-    ty1 = np.clip(np.floor((mean2d[:, 1] + ry - 0.5) / tile) + 1, 0, ty_n - 1)
+    tau_ok = np.where(ok, tau, 0.0)
+    rx = np.sqrt(tau_ok * sxx)
+    ry = np.sqrt(tau_ok * syy)
+    # generous candidate range (one extra tile each side), clipped to the grid;
+    # items that are not kept (their centre may be undefined) get an empty one
+    mx = np.where(ok, mean2d[:, 0], 0.0)
+    my = np.where(ok, mean2d[:, 1], 0.0)
+    tx0 = np.clip(np.floor((mx - rx - 15.5) / tile) - 1, 0, tx_n - 1)
+    tx1 = np.clip(np.floor((mx + rx - 0.5) / tile) + 1, 0, tx_n - 1)
+    ty0 = np.clip(np.floor((my - ry - 15.5) / tile) - 1, 0, ty_n - 1)
+    ty1 = np.clip(np.floor((my + ry - 0.5) / tile) + 1, 0, ty_n - 1)
     g_all, t_all, near_all, rej_g, rej_t = [], [], [], [], []
     idx = np.nonzero(ok)[0]
     nx = (tx1 - tx0 + 1).astype(np.int64)
