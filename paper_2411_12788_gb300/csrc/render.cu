@@ -1,7 +1,7 @@
 // Per-tile front-to-back alpha blending (Eq. 1) and its derivative.
 //
-// One CTA per 16x16 tile (128 threads forward, 256 backward); pixels are
-// grouped in 8x4 blocks, one per warp.  The tile's depth-ordered list is
+// One CTA per 16x16 tile (128 threads forward, 256 backward); each warp owns
+// a 16x4 strip forward and an 8x4 block backward.  The tile's depth-ordered list is
 // streamed through shared memory in batches of 256 entries, gathered by item
 // id.  Per entry the batch holds its
 // centre, colour, depth and the 2-D Gaussian in exponent form:
@@ -11,9 +11,9 @@
 // then alpha = min(alpha_max, 2^e).  Forward and backward evaluate e with the
 // same explicitly rounded operations, so they make identical decisions.
 //
-// Forward (one thread per two pixels): front-to-back blending with a per-pixel
-// stop before T (1 - alpha) < t_min, the CTA leaving the list once all its
-// pixels stopped.  Side outputs (what the paper's reorganisation reads):
+// Forward (one thread per two pixels of one row, sharing the row part of each
+// entry's exponent): front-to-back blending with a per-pixel stop before
+// T (1 - alpha) < t_min, the CTA leaving the list once all its pixels stopped.  Side outputs (what the paper's reorganisation reads):
 // i_max = argmax_i w_i and w_max, the midpoint depth d^mid_{i_max} (Eq. 2,
 // Sec. 4.1) evaluated once per pixel from the winner's ellipsoid frame, the
 // blended depth sum_i w_i z_i, the per-Gaussian accumulated weight I_i
@@ -72,12 +72,16 @@ __device__ __forceinline__ float4 exponent_form(float4 co) {
                      __log2f(co.w));
 }
 
-// e = lo + a2 dx^2 + b2 dx dy + c2 dy^2, explicitly rounded.
-__device__ __forceinline__ float expo(float4 ex, float dx, float dy) {
-  const float t = __fmaf_rn(ex.x, dx, __fmul_rn(ex.y, dy));
-  const float u = __fmaf_rn(__fmul_rn(ex.z, dy), dy, ex.w);
-  return __fmaf_rn(t, dx, u);
+// e = (a2 dx + b2 dy) dx + (lo + c2 dy^2), explicitly rounded.  The second
+// part and b2 dy depend only on the pixel row, so pixels of one row share
+// them (expo_row); expo_pix finishes one pixel.
+__device__ __forceinline__ float2 expo_row(float4 ex, float dy) {
+  return make_float2(__fmaf_rn(__fmul_rn(ex.z, dy), dy, ex.w), __fmul_rn(ex.y, dy));
 }
+__device__ __forceinline__ float expo_pix(float4 ex, float2 row, float dx) {
+  return __fmaf_rn(__fmaf_rn(ex.x, dx, row.y), dx, row.x);
+}
+__device__ __forceinline__ float expo(float4 ex, float dx, float dy) { return expo_pix(ex, expo_row(ex, dy), dx); }
 
 __device__ __forceinline__ float ex2_approx(float x) {
   float y;
@@ -143,11 +147,11 @@ __device__ __forceinline__ void fwd_pix_init(FwdPix& q, int px, int py, bool ins
   q.done = !inside;
 }
 
-// Blends the entry at list position `pos` into the pixel; returns its weight.
-__device__ __forceinline__ float fwd_pix_blend(FwdPix& q, float2 m, float4 ex, const float4* s_rgbz, int j,
-                                               int pos, float alpha_max, float e_min, float t_min) {
+// Blends the entry at list position `pos`, with exponent e at this pixel, into
+// the pixel; returns its weight.
+__device__ __forceinline__ float fwd_pix_blend(FwdPix& q, float e, const float4* s_rgbz, int j, int pos,
+                                               float alpha_max, float e_min, float t_min) {
   if (q.done) return 0.f;
-  const float e = expo(ex, q.fx - m.x, q.fy - m.y);
   if (e < e_min) return 0.f;
   const float alpha = fminf(alpha_max, ex2_approx(e));
   const float Tn = q.T * (1.f - alpha);
@@ -259,10 +263,47 @@ __device__ __forceinline__ bool block_may_blend(float4 ex, float mx, float my, f
   return lo + best >= e_min - margin;
 }
 
-// One thread per two pixels: rows y and y + 8 of the tile (warp w < 4 owns
-// the 8x4 blocks at ((w & 1) 8, (w >> 1) 4) and 8 rows below), so the
-// shared-memory reads of an entry and the loop control serve both.
+// One thread per two pixels, (x, y) and (x + 8, y) (warp w < 4 owns the 16x4
+// strip at rows 4w .. 4w + 3 of the tile), so the shared-memory reads of an
+// entry, the row part of its exponent and the loop control serve both.
 constexpr int kFwdThreads = kTilePixels / 2;
+
+__device__ __forceinline__ void fwd_pixel_of(const ViewDev& V, int tile, int t, int* px, int* py) {
+  const int local = tile - V.tile_base;
+  const int tx = local % V.tiles_x, ty = local / V.tiles_x;
+  const int warp = t >> 5, lane = t & 31;
+  *px = tx * kTile + (lane & 7);
+  *py = ty * kTile + warp * 4 + (lane >> 3);
+}
+
+// Blends a staged batch of nb entries into the thread's two pixels (same
+// row, so they share the exponent's row part); the warp stops once all
+// its pixels have (checked every 8 entries: a stopped pixel ignores the rest).
+template <bool kWantW>
+__device__ __forceinline__ void fwd_batch(FwdPix& q0, FwdPix& q1, int nb, int pos0, const float2* s_xy,
+                                          const float4* s_ex, const float4* s_rgbz, uint32_t* s_wsum,
+                                          const RenderParams& P, int lane) {
+  for (int j0 = 0; j0 < nb; j0 += 8) {
+    if (__all_sync(0xffffffffu, q0.done && q1.done)) break;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int j = j0 + u;
+      if (j >= nb) break;
+      const float2 m = s_xy[j];
+      const float4 ex = s_ex[j];
+      const float2 row = expo_row(ex, q0.fy - m.y);
+      const float e0 = expo_pix(ex, row, q0.fx - m.x);
+      const float e1 = expo_pix(ex, row, q1.fx - m.x);
+      const float w0 = fwd_pix_blend(q0, e0, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
+      const float w1 = fwd_pix_blend(q1, e1, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
+      if (kWantW && __any_sync(0xffffffffu, w0 > 0.f || w1 > 0.f)) {
+        const uint32_t s = __reduce_add_sync(0xffffffffu, __float2uint_rn(w0 * 16777216.f) +
+                                                              __float2uint_rn(w1 * 16777216.f));
+        if (lane == 0) atomicAdd(&s_wsum[j], s);
+      }
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P, FwdOut O) {
   constexpr int kBatch = kTilePixels;
@@ -282,13 +323,13 @@ __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P,
   const int view = s_view;
   const ViewDev& V = P.views[view];
   int px, py;
-  pixel_of(V, tile, tid, &px, &py);
-  const int py2 = py + kTile / 2;
+  fwd_pixel_of(V, tile, tid, &px, &py);
+  const int px2 = px + kTile / 2;
   const bool in0 = px < V.width && py < V.height;
-  const bool in1 = px < V.width && py2 < V.height;
+  const bool in1 = px2 < V.width && py < V.height;
   FwdPix q0, q1;
   fwd_pix_init(q0, px, py, in0);
-  fwd_pix_init(q1, px, py2, in1);
+  fwd_pix_init(q1, px2, py, in1);
   const uint2 range = P.ranges[tile];
   const bool want_w = O.weight_sum != nullptr;
 
@@ -311,18 +352,8 @@ __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P,
     __syncthreads();
     const int nb = (int)min(range.y - bstart, (uint32_t)kBatch);
     const int pos0 = (int)(bstart - range.x);
-    for (int j = 0; j < nb; ++j) {
-      if (__all_sync(0xffffffffu, q0.done && q1.done)) break;
-      const float2 m = s_xy[j];
-      const float4 ex = s_ex[j];
-      const float w0 = fwd_pix_blend(q0, m, ex, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
-      const float w1 = fwd_pix_blend(q1, m, ex, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
-      if (want_w && __any_sync(0xffffffffu, w0 > 0.f || w1 > 0.f)) {
-        const uint32_t s = __reduce_add_sync(0xffffffffu, __float2uint_rn(w0 * 16777216.f) +
-                                                              __float2uint_rn(w1 * 16777216.f));
-        if (lane == 0) atomicAdd(&s_wsum[j], s);
-      }
-    }
+    if (want_w) fwd_batch<true>(q0, q1, nb, pos0, s_xy, s_ex, s_rgbz, s_wsum, P, lane);
+    else fwd_batch<false>(q0, q1, nb, pos0, s_xy, s_ex, s_rgbz, s_wsum, P, lane);
     __syncthreads();
     if (want_w) {
 #pragma unroll
@@ -344,7 +375,7 @@ __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P,
     add_max_area(O.max_area, in1 && item1 >= 0, item1, lane);
   }
   if (in0) fwd_pix_store(q0, P, O, V, view, px, py, item0);
-  if (in1) fwd_pix_store(q1, P, O, V, view, px, py2, item1);
+  if (in1) fwd_pix_store(q1, P, O, V, view, px2, py, item1);
 }
 
 struct BwdIn {
