@@ -80,6 +80,16 @@ typedef struct gs_config {
  * backward writes the attribute gradients instead of adding to them) */
 #define GS_FLAG_ZERO_ACCUM 1u
 
+/* gs_preprocess lists a Gaussian in the tiles met by the square of half-width
+ * r = ceil(3 sqrt(lambda_max)) around its centre (lambda_max the larger
+ * eigenvalue of the dilated 2-D covariance; a tile is met when the square
+ * meets the rectangle of its pixel centres), the 3-sigma extent of the 3DGS
+ * rasterizer the paper builds on (Sec. 3.1), instead of the tiles its exact
+ * support q <= 2 ln(o / alpha_min) meets.  The per-pixel rule is unchanged,
+ * so a pixel receives the Gaussian only inside the square's tiles: the
+ * support is truncated there.  Must be the same in every call on one plan. */
+#define GS_FLAG_EXTENT_3SIGMA 2u
+
 /* Gaussian attributes, device, FP32, structure of arrays:
  *   means [n][3], scales [n][3], rotations [n][4] (w,x,y,z), opacities [n],
  *   sh [n][sh_coeffs][3] (band-major, m = -l..l, RGB innermost).

@@ -15,6 +15,13 @@ Gaussians that touch it.  The reading adopted here:
     is stable with input order (view, Gaussian index, tiles row-major), so
     ties in z fall back to ascending Gaussian index.
 
+The alternative "3sigma" extent (the tile extent of the 3DGS rasterizer the
+paper builds on, Sec. 3.1) lists Gaussian i in every tile whose pixel-centre
+rectangle meets the square [mx - r, mx + r] x [my - r, my + r] with
+r = ceil(3 sqrt(lambda_max)), lambda_max the larger eigenvalue of the 2-D
+covariance; no ellipse test.  Rendering keeps the per-pixel alpha rule, so the
+support is truncated to those tiles.
+
 These functions take the FP32 projected state as numbers (for the parity check
 they are handed the CUDA path's own stage-P outputs) and decide in float64.
 """
@@ -46,8 +53,68 @@ def rect_min_q(A, B, C, mx, my, x0, x1, y0, y1):
     return np.where(inside, 0.0, best)
 
 
+def lambda_max(sxx, syy, sxy):
+    """Larger eigenvalue of the symmetric 2x2 matrix [[sxx, sxy], [sxy, syy]]:
+    the mean of the diagonal plus the half-difference's hypotenuse with sxy."""
+    sxx, syy, sxy = (np.asarray(a, np.float64) for a in (sxx, syy, sxy))
+    return 0.5 * (sxx + syy) + np.hypot(0.5 * (sxx - syy), sxy)
+
+
+def three_sigma_radius(sxx, syy, sxy):
+    """r = ceil(3 sqrt(lambda_max)) of a 2-D covariance (the 3-sigma extent)."""
+    return np.ceil(3.0 * np.sqrt(lambda_max(sxx, syy, sxy)))
+
+
+def square_tile_range(m, r, n_tiles, tile=16):
+    """First and last tile index t (clipped to [0, n_tiles - 1]) whose pixel
+    centres [tile t + 0.5, tile t + tile - 0.5] meet [m - r, m + r]; last <
+    first when none does."""
+    m, r = np.asarray(m, np.float64), np.asarray(r, np.float64)
+    lo = np.ceil((m - r - (tile - 0.5)) / tile)
+    hi = np.floor((m + r - 0.5) / tile)
+    return np.maximum(lo, 0).astype(np.int64), np.minimum(hi, n_tiles - 1).astype(np.int64)
+
+
+def _square_lists(mean2d, conic, ok, tx_n, ty_n, tile, eps):
+    """Tile lists of the 3-sigma extent; `near` / rejected entries are those
+    whose membership changes when r (through 3 sqrt(lambda_max)) or the centre
+    moves by eps relative."""
+    A, B, C = conic[:, 0], conic[:, 1], conic[:, 2]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        det = A * C - B * B
+        sxx = np.where(ok, C / det, 1.0)            # the covariance is the inverse conic
+        syy = np.where(ok, A / det, 1.0)
+        sxy = np.where(ok, -B / det, 0.0)
+    s3 = 3.0 * np.sqrt(lambda_max(sxx, syy, sxy))
+    mx = np.where(ok, mean2d[:, 0], 0.0)
+    my = np.where(ok, mean2d[:, 1], 0.0)
+
+    def tiles_of(r, dx, dy):
+        x0, x1 = square_tile_range(mx + dx, r, tx_n, tile)
+        y0, y1 = square_tile_range(my + dy, r, ty_n, tile)
+        out = []
+        for i in np.nonzero(ok)[0]:
+            out.extend((int(i), int(ty) * tx_n + int(tx))
+                       for ty in range(y0[i], y1[i] + 1) for tx in range(x0[i], x1[i] + 1))
+        return set(out)
+
+    nominal = tiles_of(np.ceil(s3), 0.0, 0.0)
+    shift = eps * np.maximum(1.0, np.abs(mx) + np.abs(my))
+    variants = [tiles_of(np.ceil(s3 * f), sx * shift, sy * shift)
+                for f in (1.0 - eps, 1.0 + eps) for sx in (-1, 1) for sy in (-1, 1)]
+    sure = set.intersection(nominal, *variants)
+    either = set.union(nominal, *variants)
+    kept = sorted(nominal)
+    g_all = np.asarray([g for g, _ in kept], np.int64)
+    t_all = np.asarray([t for _, t in kept], np.int64)
+    near = np.asarray([e not in sure for e in kept], bool)
+    rej = sorted(either - nominal)
+    return (g_all, t_all, near, np.asarray([g for g, _ in rej], np.int64),
+            np.asarray([t for _, t in rej], np.int64))
+
+
 def tile_lists(mean2d, conic, opacity, valid, width, height, alpha_min=1.0 / 255.0,
-               tile=16, eps=1e-4):
+               tile=16, eps=1e-4, extent="exact"):
     """Per-Gaussian touched tiles for one view.
 
     mean2d [N,2], conic [N,3], opacity [N] (numbers; converted to float64),
@@ -55,7 +122,8 @@ def tile_lists(mean2d, conic, opacity, valid, width, height, alpha_min=1.0 / 255
     (Gaussian index, tiles row-major), where `near` marks entries whose
     decision is within eps (relative to tau) of the boundary, and a second
     array of near-boundary *rejected* candidates (gauss, tiles) for the
-    same tolerance."""
+    same tolerance.  extent="3sigma" gives the lists of the 3-sigma square
+    instead (see the module docstring)."""
     mean2d = np.asarray(mean2d, np.float64)
     conic = np.asarray(conic, np.float64)
     opacity = np.asarray(opacity, np.float64)
@@ -68,6 +136,9 @@ def tile_lists(mean2d, conic, opacity, valid, width, height, alpha_min=1.0 / 255
     A, B, C = conic[:, 0], conic[:, 1], conic[:, 2]
     det = A * C - B * B
     ok &= det > 0
+    if extent == "3sigma":
+        return _square_lists(np.asarray(mean2d, np.float64), np.asarray(conic, np.float64), ok,
+                             tx_n, ty_n, tile, 0.1 * eps)
     with np.errstate(divide="ignore", invalid="ignore"):
         sxx = np.where(ok, C / det, 0.0)       # inverse conic = 2-D covariance
         syy = np.where(ok, A / det, 0.0)

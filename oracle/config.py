@@ -11,6 +11,10 @@ below are the readings this implementation adopts:
   t_min      compositing stops before the entry that would bring the
              transmittance below this; that entry is not blended
   bg         background colour added as T_final * bg
+  extent     "exact": a Gaussian reaches every pixel where alpha >= alpha_min;
+             "3sigma": only the pixels of the tiles its 3-sigma square meets
+             (the tile extent of the 3DGS rasterizer, Sec. 3.1; see
+             oracle.binning)
 """
 from __future__ import annotations
 
@@ -27,3 +31,4 @@ class OracleConfig:
     t_min: float = 1e-4
     bg: tuple = field(default_factory=lambda: (0.0, 0.0, 0.0))
     tile: int = 16
+    extent: str = "exact"

@@ -93,6 +93,7 @@ def render_view(proj: dict, cam, cfg: OracleConfig | None = None, pix=None,
     rgb = proj["rgb"][oi]
     zs = proj["z"][oi]
     bg = torch.tensor(cfg.bg, dtype=f64)
+    sq = _square_rects(proj, oi, cam, cfg) if cfg.extent == "3sigma" else None
 
     colours, tfin, imax, wmax, depth, dblend, last, nbl, flags = ([] for _ in range(9))
     wsum = torch.zeros(N, dtype=f64)
@@ -106,6 +107,13 @@ def render_view(proj: dict, cam, cfg: OracleConfig | None = None, pix=None,
         q = conic[None, :, 0] * dx * dx + 2.0 * conic[None, :, 1] * dx * dy \
             + conic[None, :, 2] * dy * dy
         alpha_raw = opac[None, :] * torch.exp(-0.5 * q)
+        amb = None
+        if cfg.extent == "3sigma":
+            # only the pixels of the tiles the 3-sigma square meets; amb marks
+            # (pixel, Gaussian) pairs whose tile membership a relative change of
+            # 1e-5 in the radius or the centre would flip
+            inside, amb = _square_membership(sq, uu[s:s + step], vv[s:s + step], cfg.tile)
+            alpha_raw = torch.where(torch.as_tensor(inside), alpha_raw, torch.zeros_like(alpha_raw))
         w, tf, blended = composite(alpha_raw, cfg)
         colours.append(w @ rgb + tf[:, None] * bg[None, :])
         tfin.append(tf)
@@ -130,7 +138,13 @@ def render_view(proj: dict, cam, cfg: OracleConfig | None = None, pix=None,
             gsel = gi.clamp(min=0)
             d = midpoint_depth(proj["p_c"].detach()[gsel], proj["ell"][gsel], u, v, cam)
             depth.append(torch.where(has, d, torch.zeros_like(d)))
-        flags.append(_flags(alpha_raw.detach(), wd, blended, zs.detach(), cfg, flag_eps))
+        fl = _flags(alpha_raw.detach(), wd, blended, zs.detach(), cfg, flag_eps)
+        if amb is not None:
+            # bit 5: a Gaussian that reaches alpha_min at the pixel (up to 0.1 %)
+            # has an ambiguous tile membership there
+            reach = (opac[None, :] * torch.exp(-0.5 * q)).detach() >= (1.0 - 1e-3) * cfg.alpha_min
+            fl |= (torch.as_tensor(amb) & reach).any(1).long() << 5
+        flags.append(fl)
     cat = lambda xs: torch.cat(xs) if xs else torch.zeros(0)
     out = dict(colour=cat(colours), t_final=cat(tfin), imax=cat(imax), wmax=cat(wmax),
                depth_blend=cat(dblend), last=cat(last), n_blended=cat(nbl),
@@ -139,6 +153,38 @@ def render_view(proj: dict, cam, cfg: OracleConfig | None = None, pix=None,
     if want_depth:
         out["depth"] = cat(depth)
     return out
+
+
+def _square_rects(proj, oi, cam, cfg):
+    """Tile rectangles of the 3-sigma squares of the ordered Gaussians, nominal
+    and for the radius and centre moved by 1e-5 relative (for the ambiguity
+    flag): a list of (tx0, tx1, ty0, ty1) integer arrays."""
+    from .binning import lambda_max, square_tile_range
+    cov = proj["cov2d"].detach().numpy()[oi.numpy()]
+    m = proj["mean2d"].detach().numpy()[oi.numpy()]
+    s3 = 3.0 * np.sqrt(lambda_max(cov[:, 0, 0], cov[:, 1, 1], cov[:, 0, 1]))
+    tx_n = (cam.width + cfg.tile - 1) // cfg.tile
+    ty_n = (cam.height + cfg.tile - 1) // cfg.tile
+    shift = 1e-5 * np.maximum(1.0, np.abs(m[:, 0]) + np.abs(m[:, 1]))
+    rects = []
+    for f, sx, sy in [(1.0, 0, 0)] + [(f, sx, sy) for f in (1 - 1e-5, 1 + 1e-5) for sx in (-1, 1) for sy in (-1, 1)]:
+        r = np.ceil(s3 * f)
+        x0, x1 = square_tile_range(m[:, 0] + sx * shift, r, tx_n, cfg.tile)
+        y0, y1 = square_tile_range(m[:, 1] + sy * shift, r, ty_n, cfg.tile)
+        rects.append((x0, x1, y0, y1))
+    return rects
+
+
+def _square_membership(rects, u, v, tile):
+    """[P, M] bool: the pixel's tile lies in the nominal rectangle; and whether
+    any perturbed rectangle disagrees."""
+    tx = (np.asarray(u) // tile)[:, None]
+    ty = (np.asarray(v) // tile)[:, None]
+    ins = [(tx >= x0[None]) & (tx <= x1[None]) & (ty >= y0[None]) & (ty <= y1[None]) for x0, x1, y0, y1 in rects]
+    amb = np.zeros_like(ins[0])
+    for other in ins[1:]:
+        amb |= other != ins[0]
+    return ins[0], amb
 
 
 # z: the CUDA path's FP32 z (three rounded operations) and float32 of the
@@ -158,7 +204,9 @@ def _flags(alpha_raw, w, blended, zs, cfg, eps=None):
     bit 3: two contributing entries have depths within eps.z (relative)
            (depth-order tie)
     bit 4: some blended entry has o*G within eps.clamp of alpha_max (the
-           clamp switches the derivative off)"""
+           clamp switches the derivative off)
+    (bit 5, set by render_view in the 3sigma extent: a Gaussian reaching the
+    pixel has an ambiguous tile membership there)"""
     eps = dict(DEFAULT_FLAG_EPS, **(eps or {}))
     P, M = alpha_raw.shape
     out = torch.zeros(P, dtype=torch.long)

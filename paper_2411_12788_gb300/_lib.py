@@ -15,6 +15,7 @@ LIB_PATH = os.path.join(HERE, "libgs.so")
 GS_TILE = 16
 GS_MAX_VIEWS = 64
 GS_FLAG_ZERO_ACCUM = 1
+GS_FLAG_EXTENT_3SIGMA = 2
 GS_SELFTEST_SCRATCH_BYTES = 4096
 GS_ERR_TIMEOUT = 4
 

@@ -33,6 +33,7 @@ struct PreParams {
   int n_views;
   const uint8_t* mask;
   float znear, lowpass, alpha_min;
+  bool three_sigma;            // GS_FLAG_EXTENT_3SIGMA: tile lists from the 3-sigma square
   ItemState st;
 };
 
@@ -124,16 +125,36 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
     }
     const float idet = 1.f / det;
     const float A = cyy * idet, B = -cxy * idet, C = cxx * idet;
+    // largest eigenvalue and condition number of the 2-D covariance
+    const float hd = 0.5f * (cxx - cyy);
+    const float lmax = 0.5f * (cxx + cyy) + sqrtf(hd * hd + cxy * cxy);
+    const float kappa = lmax * lmax / det;
+    // exact support half-extents (they bound the culling boxes in both modes)
+    const float h_sup = sqrtf(tau * cyy), rx_sup = sqrtf(tau * cxx);
     BinParams b;
     b.mx = V.fx * pc.x * iz + V.cx;
     b.my = V.fy * pc.y * iz + V.cy;
-    b.tau = tau;
-    b.k = cxy / cyy;
-    b.sc = sqrtf(det / cyy);
-    b.isyy = 1.f / cyy;
-    b.h = sqrtf(tau * cyy);
-    b.rx = sqrtf(tau * cxx);
-    b.ys = cxy * sqrtf(tau / cxx);
+    if (P.three_sigma) {
+      // the square of half-width r = ceil(3 sqrt(lambda_max)): with tau = 1,
+      // no slope, no y-dependence and the extreme points out of reach, the
+      // row functions return the square's rows and columns
+      const float r = ceilf(3.f * sqrtf(lmax));
+      b.tau = 1.f;
+      b.k = 0.f;
+      b.sc = r;
+      b.isyy = 0.f;
+      b.h = r;
+      b.rx = r;
+      b.ys = INFINITY;
+    } else {
+      b.tau = tau;
+      b.k = cxy / cyy;
+      b.sc = sqrtf(det / cyy);
+      b.isyy = 1.f / cyy;
+      b.h = h_sup;
+      b.rx = rx_sup;
+      b.ys = cxy * sqrtf(tau / cxx);
+    }
     // exact tile count, row by row
     uint32_t count = 0;
     int ty0 = 0, ty1 = -1;
@@ -143,15 +164,11 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
         if (row_tiles(b, ty, V.tiles_x, &a, &c)) count += (uint32_t)(c - a + 1);
       }
     }
-    // condition number of the 2-D covariance (for the culling boxes)
-    const float hd = 0.5f * (cxx - cyy);
-    const float lmax = 0.5f * (cxx + cyy) + sqrtf(hd * hd + cxy * cxy);
-    const float kappa = lmax * lmax / det;
     P.st.tiles[item] = count;
     P.st.depth_key[item] = count ? __float_as_uint(pc.z) : kCulledKey;
     if (!count) continue;
     P.st.rect[item] = make_uint2((uint32_t)ty0 << 16, (uint32_t)(V.tiles_x - 1) | ((uint32_t)ty1 << 16));
-    P.st.xy_tau_z[item] = make_float4(b.mx, b.my, tau, pc.z);
+    P.st.xy_tau_z[item] = make_float4(b.mx, b.my, b.tau, pc.z);
     P.st.conic_o[item] = make_float4(A, B, C, o);
     P.st.bin[2 * item] = make_float4(b.k, b.sc, b.isyy, b.h);
     P.st.bin[2 * item + 1] = make_float4(b.rx, b.ys, 0.f, 0.f);
@@ -172,7 +189,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
       bl += Y[k] * shc[3 * k + 2];
     }
     P.st.rgb[item] = make_float4(fmaxf(r, 0.f), fmaxf(g, 0.f), fmaxf(bl, 0.f), 
-                                 pack_extent(support_extent(b.rx, cxx, kappa), support_extent(b.h, cyy, kappa)));
+                                 pack_extent(support_extent(rx_sup, cxx, kappa), support_extent(h_sup, cyy, kappa)));
 
     // midpoint-depth frame: W = diag(1/s) (R Rq)^T maps camera offsets to the
     // unit-sphere frame of the ellipsoid x^2/sx^2 + y^2/sy^2 + z^2/sz^2 = 1
@@ -499,6 +516,7 @@ cudaError_t launch_preprocess(const gs_scene& sc, const ViewDev* views, int n_vi
   P.znear = cfg.znear;
   P.lowpass = cfg.lowpass;
   P.alpha_min = cfg.alpha_min;
+  P.three_sigma = (cfg.flags & GS_FLAG_EXTENT_3SIGMA) != 0;
   P.st = st;
   const int blocks = ceil_div(sc.n, kPreThreads);
   if (blocks == 0) return cudaSuccess;

@@ -33,6 +33,18 @@ def test_header_functions_are_exported(L):
     assert set(names) == set(_lib.SIGNATURES), set(names) ^ set(_lib.SIGNATURES)
 
 
+def test_header_constants_match_the_binding():
+    """Every #define of include/gs.h that the Python binding also names has
+    the same value there."""
+    from paper_2411_12788_gb300 import _lib
+    src = open(os.path.join(ROOT, "include", "gs.h")).read()
+    defs = dict(re.findall(r"#define\s+(GS_[A-Z0-9_]+)\s+\(?([0-9]+)u?\)?", src))
+    shared = [k for k in defs if hasattr(_lib, k)]
+    assert {"GS_FLAG_ZERO_ACCUM", "GS_FLAG_EXTENT_3SIGMA", "GS_TILE"} <= set(shared)
+    for k in shared:
+        assert getattr(_lib, k) == int(defs[k]), k
+
+
 def test_struct_sizes(L):
     from paper_2411_12788_gb300 import _lib
     assert L.gs_sizeof_plan() == C.sizeof(_lib.Plan)

@@ -16,7 +16,7 @@ import pytest
 import torch
 
 from oracle import OracleConfig, binning as OB, project as OP, render as OR
-from paper_2411_12788_gb300 import raster, scenes
+from paper_2411_12788_gb300 import _lib, raster, scenes
 
 pytestmark = pytest.mark.gpu
 CFG = OracleConfig()
@@ -27,10 +27,10 @@ def _need_gpu():
         pytest.skip("no CUDA device")
 
 
-def _oracle_view(sc, cam, pix=None, want_depth=True):
+def _oracle_view(sc, cam, pix=None, want_depth=True, cfg=None):
     with torch.no_grad():
         pr = OP.project(sc.means, sc.scales, sc.rotations, sc.opacities, sc.sh, sc.sh_degree, cam)
-        out = OR.render_view(pr, cam, pix=pix, want_depth=want_depth)
+        out = OR.render_view(pr, cam, cfg=cfg, pix=pix, want_depth=want_depth)
     return pr, out
 
 
@@ -149,10 +149,10 @@ def test_binning_sort_ranges_bit_exact(case):
 
 
 # ---------------------------------------------------------------- stage R
-def _check_render(sc, cams, fr, max_flag_frac=2e-3):
+def _check_render(sc, cams, fr, max_flag_frac=2e-3, cfg=None):
     n = sc.n
     for v, cam in enumerate(cams):
-        pr, out = _oracle_view(sc, cam)
+        pr, out = _oracle_view(sc, cam, cfg=cfg)
         ok = out["flags"].numpy() == 0
         assert ok.mean() >= 1 - max_flag_frac, ok.mean()
         col = _gpu_colour(fr, v).numpy()
@@ -206,6 +206,46 @@ def test_render_matches_oracle(case):
     _check_render(sc, cams, fr)
 
 
+@pytest.mark.parametrize("case", list(SCENES))
+def test_three_sigma_extent_matches_oracle(case):
+    """GS_FLAG_EXTENT_3SIGMA: every Gaussian is listed in the tiles its 3-sigma
+    square meets (the same entries as the oracle's, except entries whose
+    membership a 1e-5 relative change of the radius or centre would flip),
+    and the render equals the oracle's render with the support truncated to
+    those tiles."""
+    _need_gpu()
+    sc, cams = SCENES[case]()
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, cams, cfg=raster.make_config(flags=_lib.GS_FLAG_EXTENT_3SIGMA))
+    torch.cuda.synchronize()
+    assert raster.device_status(fr.plan, fr.pre_ws) == 0
+    st = raster.inspect_preprocess(fr)
+    so = raster.inspect_sort(fr)
+    n = sc.n
+    bases, total_tiles = OB.view_tile_bases([(c.width, c.height) for c in cams])
+    gpu_set = set(zip(so["tile_ids"].numpy().astype(np.int64).tolist(), so["items"].numpy().astype(np.int64).tolist()))
+    assert len(gpu_set) == int(fr.plan.n_entries) > 0
+    xyz, co, cnt = st["xy_tau_z"].numpy(), st["conic_o"].numpy(), st["tiles"].numpy().astype(np.int64)
+    differ = 0
+    for v, cam in enumerate(cams):
+        sl = slice(v * n, (v + 1) * n)
+        gg, tt, near, rg, rt = OB.tile_lists(xyz[sl, :2], co[sl, :3], co[sl, 3], cnt[sl] > 0, cam.width,
+                                             cam.height, extent="3sigma")
+        exp = set(zip((tt + bases[v]).tolist(), (gg + v * n).tolist()))
+        upper = bases[v + 1] if v + 1 < len(cams) else total_tiles
+        got = {(t, i) for (t, i) in gpu_set if bases[v] <= t < upper}
+        allowed = set(zip((tt[near] + bases[v]).tolist(), (gg[near] + v * n).tolist())) | \
+            set(zip((rt + bases[v]).tolist(), (rg + v * n).tolist()))
+        assert (exp ^ got) <= allowed, list((exp ^ got) - allowed)[:5]
+        differ += len(exp ^ got)
+    assert differ <= max(2, 1e-3 * len(gpu_set))
+    # the exact-support lists differ (the square is another extent)
+    fe = raster.forward(g, cams)
+    ex = raster.inspect_sort(fe)
+    assert set(zip(ex["tile_ids"].numpy().tolist(), ex["items"].numpy().tolist())) != gpu_set
+    _check_render(sc, cams, fr, cfg=OracleConfig(extent="3sigma"))
+
+
 def test_render_is_deterministic():
     _need_gpu()
     sc, cams = SCENES["box512_deg3_multiview"]()
@@ -224,11 +264,11 @@ def _grad_case(seed=2, n=256, deg=3, size=64):
     return sc, cam, target
 
 
-def _oracle_grads(sc, cam, target):
+def _oracle_grads(sc, cam, target, cfg=None):
     params = [torch.tensor(np.asarray(a, np.float64), requires_grad=True)
               for a in (sc.means, sc.scales, sc.rotations, sc.opacities, sc.sh)]
     pr = OP.project(*params, sc.sh_degree, cam)
-    out = OR.render_view(pr, cam, want_depth=False)
+    out = OR.render_view(pr, cam, cfg=cfg, want_depth=False)
     img = OR.planar(out["colour"], cam)
     L = torch.abs(img - torch.as_tensor(target, dtype=torch.float64)).mean()
     L.backward()
@@ -243,12 +283,13 @@ def _assert_grad_close(name, g, ref, keep):
     assert not bad.any(), (name, int(bad.sum()), g[bad][:4], ref[bad][:4])
 
 
-@pytest.mark.parametrize("deg,seed", [(3, 2), (0, 0), (1, 5)])
-def test_backward_matches_oracle(deg, seed):
+@pytest.mark.parametrize("deg,seed,extent", [(3, 2, "exact"), (0, 0, "exact"), (1, 5, "exact"), (3, 7, "3sigma")])
+def test_backward_matches_oracle(deg, seed, extent):
     _need_gpu()
     sc, cam, target = _grad_case(seed=seed, deg=deg)
     g = raster.GaussianTensors.from_scene(sc)
-    fr = raster.forward(g, [cam])
+    three = extent == "3sigma"
+    fr = raster.forward(g, [cam], cfg=raster.make_config(flags=_lib.GS_FLAG_EXTENT_3SIGMA) if three else None)
     img = fr.outs["image"]
     tgt = torch.as_tensor(target.reshape(-1)).cuda()
     loss = torch.zeros(1, device="cuda")
@@ -256,7 +297,7 @@ def test_backward_matches_oracle(deg, seed):
     raster.loss_l1(img, tgt, loss, dL)
     grads = raster.backward(g, fr, dL)
     torch.cuda.synchronize()
-    L, ref, out, pr = _oracle_grads(sc, cam, target)
+    L, ref, out, pr = _oracle_grads(sc, cam, target, cfg=OracleConfig(extent=extent))
     assert abs(loss.item() - L) <= 1e-6
     ok = out["flags"].numpy() == 0
     uu, vv = out["u"].numpy(), out["v"].numpy()
@@ -268,6 +309,44 @@ def test_backward_matches_oracle(deg, seed):
     for name, r in zip(names, ref):
         gg = grads[name].cpu().double().numpy()
         _assert_grad_close(name, gg, r, keep)
+
+
+def test_mean2d_abs_gradient_matches_oracle():
+    """d_mean2d_abs: per view the length of dL/d(projected centre), summed over
+    the views (the densification statistic of 3DGS); two ragged views against
+    the oracle's autograd derivative of each view's mean2d."""
+    _need_gpu()
+    sc = scenes.box_scene(384, seed=6, sh_degree=1)
+    cams = _multiview_cams()[:2]
+    targets = scenes.target_images(cams, seed=3)
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, cams)
+    img = fr.outs["image"]
+    tgt = torch.cat([torch.as_tensor(t.reshape(-1)) for t in targets]).cuda()
+    loss = torch.zeros(1, device="cuda")
+    dL = torch.empty_like(img)
+    raster.loss_l1(img, tgt, loss, dL)
+    grads = raster.backward(g, fr, dL)
+    torch.cuda.synchronize()
+    params = [torch.tensor(np.asarray(a, np.float64), requires_grad=True)
+              for a in (sc.means, sc.scales, sc.rotations, sc.opacities, sc.sh)]
+    total = sum(3 * c.width * c.height for c in cams)
+    L = 0.0
+    prs, keep = [], np.ones(sc.n, bool)
+    for cam, t in zip(cams, targets):
+        pr = OP.project(*params, sc.sh_degree, cam)
+        pr["mean2d"].retain_grad()
+        out = OR.render_view(pr, cam, want_depth=False)
+        L = L + torch.abs(OR.planar(out["colour"], cam) - torch.as_tensor(t, dtype=torch.float64)).sum() / total
+        ok = out["flags"].numpy() == 0
+        bad = OR.contributors(pr, np.stack([out["u"].numpy()[~ok], out["v"].numpy()[~ok]], 1), CFG.alpha_min)
+        keep[bad] = False
+        prs.append(pr)
+    L.backward()
+    assert abs(loss.item() - L.item()) <= 1e-6
+    ref = sum(pr["mean2d"].grad.norm(dim=1).numpy() for pr in prs)
+    assert keep.mean() > 0.9 and (ref[keep] > 0).sum() > 50
+    _assert_grad_close("d_mean2d_abs", grads["d_mean2d_abs"].cpu().double().numpy(), ref, keep)
 
 
 def test_backward_collects_the_forward_weight_sums():

@@ -372,6 +372,70 @@ def test_tile_lists_cover_every_supporting_pixel():
     assert len(g) > 200
 
 
+def test_three_sigma_radius_against_eigvalsh():
+    """lambda_max in closed form agrees with numpy's symmetric eigensolver, and
+    r = ceil(3 sqrt(lambda_max)) on matrices with known eigenvalues."""
+    rng = np.random.default_rng(21)
+    for _ in range(200):
+        L = rng.normal(size=(2, 2)) * rng.uniform(0.1, 30)
+        S = L @ L.T + 0.3 * np.eye(2)
+        ref = np.linalg.eigvalsh(S)[-1]
+        assert abs(binning.lambda_max(S[0, 0], S[1, 1], S[0, 1]) - ref) <= 1e-12 * ref
+    # eigenvalues (4, 1): diagonal and rotated by 45 degrees; (2, 2)
+    assert binning.three_sigma_radius(4.0, 1.0, 0.0) == 6.0
+    assert binning.three_sigma_radius(2.5, 2.5, 1.5) == 6.0
+    assert binning.three_sigma_radius(2.0, 2.0, 0.0) == math.ceil(3 * math.sqrt(2))
+
+
+def test_square_tile_range_brute_force():
+    """The tiles whose pixel centres meet [m - r, m + r], by enumerating the
+    centres, equal the closed-form range (clipped to the grid)."""
+    rng = np.random.default_rng(22)
+    for _ in range(500):
+        n = int(rng.integers(1, 12))
+        m = rng.uniform(-40, 16 * n + 40)
+        r = float(rng.integers(1, 40))
+        lo, hi = binning.square_tile_range(m, r, n)
+        centres = np.arange(16 * n) + 0.5
+        hit = np.abs(centres - m) <= r
+        ref = sorted(set((np.nonzero(hit)[0] // 16).tolist()))
+        got = list(range(int(lo), int(hi) + 1))
+        assert got == ref, (m, r, n, got, ref)
+
+
+def test_three_sigma_extent_truncates_the_support():
+    """One opaque Gaussian whose exact support (3.33 sigma at o = 0.99) reaches
+    past its 3-sigma square: in the 3sigma extent the pixels of tiles the
+    square misses get the background, the others the exact-extent colour;
+    the tile lists are the square's tiles."""
+    s, z0 = 0.1, 4.0
+    # sigma^2 = (128 s / z0)^2 + 0.3 = 10.54 px^2: r = ceil(3 sigma) = 10 px
+    # while the exact support reaches sigma sqrt(2 ln(0.99 * 255)) = 10.8 px;
+    # centred at (54, 54) the square ends at 64 < 64.5, the first pixel
+    # centre of the next tile, which the exact support still reaches
+    sc = _one_scene([[(54.0 - 64.0) * z0 / 128.0, (54.0 - 64.0) * z0 / 128.0, z0]], [[s, s, s]],
+                    [[1, 0, 0, 0]], [0.99], [[0.9, 0.4, 0.2]])
+    cam = scenes.origin_camera()
+    exact = R.render(sc, [cam])[0]
+    tri = R.render(sc, [cam], cfg=OracleConfig(extent="3sigma"))[0]
+    pr = P.project(sc.means, sc.scales, sc.rotations, sc.opacities, sc.sh, 0, cam)
+    cov = pr["cov2d"].numpy()[0]
+    r = binning.three_sigma_radius(cov[0, 0], cov[1, 1], cov[0, 1])
+    m = pr["mean2d"].numpy()[0]
+    assert r == 10.0 and np.allclose(m, 54.0)
+    x0, x1 = binning.square_tile_range(m[0], r, 8)
+    y0, y1 = binning.square_tile_range(m[1], r, 8)
+    u, v = tri["u"].numpy(), tri["v"].numpy()
+    inside = (u // 16 >= x0) & (u // 16 <= x1) & (v // 16 >= y0) & (v // 16 <= y1)
+    ce, ct = exact["colour"].numpy(), tri["colour"].numpy()
+    np.testing.assert_array_equal(ct[inside], ce[inside])
+    assert np.all(ct[~inside] == 0.0)
+    assert (ce[~inside, 0] > 0).sum() > 0           # the exact support reaches past the square's tiles
+    g, t, _, _, _ = binning.tile_lists(pr["mean2d"].numpy(), pr["conic"].numpy(), [0.99], [True], 128, 128,
+                                       extent="3sigma")
+    assert sorted(t.tolist()) == sorted(ty * 8 + tx for ty in range(y0, y1 + 1) for tx in range(x0, x1 + 1))
+
+
 def test_sort_and_ranges_on_handmade_keys():
     """Stable (tile, z) order and [start, end) ranges on a hand-made list."""
     tile = np.array([3, 1, 3, 0, 1, 3])
