@@ -137,6 +137,10 @@ typedef struct gs_fwd_outputs {
   float* depth_blend;       /* [total_pixels] sum_i w_i z_i (Sec. 4.1) */
   float* weight_sum;        /* [n_items] += sum over the view's pixels of w_i (Sec. 3.2) */
   uint32_t* max_area;       /* [n_items] += #pixels with i_max = i (S_i, Sec. 4.1) */
+  uint64_t* weight_sum_fixed; /* [n_items], 8-byte aligned: += I_i in units of 2^-24.  Every
+                               pixel's weight is rounded once to a multiple of 2^-24 and the
+                               sums are integer, so the result does not depend on the order of
+                               the atomic adds (bit-reproducible, unlike weight_sum) */
 } gs_fwd_outputs;
 
 /* Gradients, device, ACCUMULATED (+=) over views, same layouts as gs_scene;
@@ -145,7 +149,8 @@ typedef struct gs_fwd_outputs {
  * statistic).  weight_sum (nullable, [n_items]) += the accumulated blending
  * weight I_i of Sec. 3.2, the same quantity as gs_fwd_outputs.weight_sum,
  * collected during the backward pass: a training step can take I_i from here
- * and skip it in the forward pass. */
+ * and skip it in the forward pass; weight_sum_fixed likewise in fixed point
+ * (bit-reproducible). */
 typedef struct gs_grads {
   float* d_means;
   float* d_scales;
@@ -154,6 +159,8 @@ typedef struct gs_grads {
   float* d_sh;
   float* d_mean2d_abs;
   float* weight_sum;
+  uint64_t* weight_sum_fixed; /* nullable, [n_items], 8-byte aligned: I_i collected in the
+                               backward in the fixed point of gs_fwd_outputs.weight_sum_fixed */
 } gs_grads;
 
 /* ---- plan and sizes (host only) ------------------------------------- */

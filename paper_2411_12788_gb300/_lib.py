@@ -63,13 +63,14 @@ class SceneBuf(C.Structure):
 class FwdOutputs(C.Structure):
     _fields_ = [("image", C.c_void_p), ("final_T", C.c_void_p), ("n_contrib", C.c_void_p),
                 ("imax", C.c_void_p), ("wmax", C.c_void_p), ("depth", C.c_void_p),
-                ("depth_blend", C.c_void_p), ("weight_sum", C.c_void_p), ("max_area", C.c_void_p)]
+                ("depth_blend", C.c_void_p), ("weight_sum", C.c_void_p), ("max_area", C.c_void_p),
+                ("weight_sum_fixed", C.c_void_p)]
 
 
 class Grads(C.Structure):
     _fields_ = [("d_means", C.c_void_p), ("d_scales", C.c_void_p), ("d_rotations", C.c_void_p),
                 ("d_opacities", C.c_void_p), ("d_sh", C.c_void_p), ("d_mean2d_abs", C.c_void_p),
-                ("weight_sum", C.c_void_p)]
+                ("weight_sum", C.c_void_p), ("weight_sum_fixed", C.c_void_p)]
 
 
 class PreprocessView(C.Structure):

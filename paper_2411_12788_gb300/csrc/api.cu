@@ -270,6 +270,7 @@ gs_status gs_render_fwd(const gs_plan* plan, const gs_config* cfg, void* pre_ws,
   if (!valid_plan(plan) || !valid_config(cfg) || plan->n_entries < 0 || !pre_ws || !sort_ws || !out)
     return GS_ERR_INVALID_ARG;
   if (!out->image || !out->final_T || !out->n_contrib) return GS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(out->weight_sum_fixed) & 7u) return GS_ERR_INVALID_ARG;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   const PreLayout L = pre_layout(*plan);
   const SortLayout S = sort_layout(*plan);
@@ -277,6 +278,8 @@ gs_status gs_render_fwd(const gs_plan* plan, const gs_config* cfg, void* pre_ws,
   if (cfg->flags & GS_FLAG_ZERO_ACCUM) {
     if (out->weight_sum) e = cudaMemsetAsync(out->weight_sum, 0, 4 * (size_t)plan->n_items, stream);
     if (e == cudaSuccess && out->max_area) e = cudaMemsetAsync(out->max_area, 0, 4 * (size_t)plan->n_items, stream);
+    if (e == cudaSuccess && out->weight_sum_fixed)
+      e = cudaMemsetAsync(out->weight_sum_fixed, 0, 8 * (size_t)plan->n_items, stream);
     if (e != cudaSuccess) return GS_ERR_CUDA;
   }
   e = launch_render_fwd(at<ViewDev>(pre_ws, L.views), plan->n_views, plan->n, plan->total_tiles,
@@ -292,6 +295,7 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
       !sort_ws || !dL_dimage || !image || !n_contrib || !g)
     return GS_ERR_INVALID_ARG;
   if (!g->d_means || !g->d_scales || !g->d_rotations || !g->d_opacities || !g->d_sh) return GS_ERR_INVALID_ARG;
+  if (reinterpret_cast<uintptr_t>(g->weight_sum_fixed) & 7u) return GS_ERR_INVALID_ARG;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
   const PreLayout L = pre_layout(*plan);
   const SortLayout S = sort_layout(*plan);
@@ -301,12 +305,14 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
   // gradient row (no read-modify-write); I_i is accumulated by atomics
   if (e == cudaSuccess && (cfg->flags & GS_FLAG_ZERO_ACCUM) && g->weight_sum)
     e = cudaMemsetAsync(g->weight_sum, 0, 4 * (size_t)plan->n_items, stream);
+  if (e == cudaSuccess && (cfg->flags & GS_FLAG_ZERO_ACCUM) && g->weight_sum_fixed)
+    e = cudaMemsetAsync(g->weight_sum_fixed, 0, 8 * (size_t)plan->n_items, stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
   const ItemState st = item_state(pre_ws, L);
   float4* grad2d = at<float4>(pre_ws, L.grad2d);
   e = launch_render_bwd(at<ViewDev>(pre_ws, L.views), plan->n_views, n, plan->total_tiles,
                         at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals), st, *cfg, dL_dimage, image,
-                        n_contrib, grad2d, g->weight_sum, stream);
+                        n_contrib, grad2d, g->weight_sum, g->weight_sum_fixed, stream);
   if (e == cudaSuccess)
     e = launch_preprocess_backward(*scene, at<ViewDev>(pre_ws, L.views), plan->n_views, *cfg, st.tiles, grad2d, *g,
                                    stream);

@@ -173,7 +173,7 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
 cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
                               const uint32_t* vals, const ItemState& st, const gs_config& cfg,
                               const float* dL_dimage, const float* image, const uint32_t* n_contrib,
-                              float4* grad2d, float* weight_sum, cudaStream_t stream);
+                              float4* grad2d, float* weight_sum, uint64_t* weight_sum_fixed, cudaStream_t stream);
 cudaError_t launch_iota(uint32_t* out, int64_t n, cudaStream_t stream);
 cudaError_t launch_loss_l1(const float* image, const float* target, int64_t count, float* loss, float* dL,
                            cudaStream_t stream);

@@ -33,7 +33,6 @@ struct PreParams {
   int n_views;
   const uint8_t* mask;
   float znear, lowpass, alpha_min;
-  bool three_sigma;            // GS_FLAG_EXTENT_3SIGMA: tile lists from the 3-sigma square
   ItemState st;
 };
 
@@ -55,7 +54,7 @@ __device__ __forceinline__ void cull(const ItemState& st, int64_t item) {
   st.depth_key[item] = kCulledKey;
 }
 
-template <int DEG>
+template <int DEG, bool THREE_SIGMA>
 __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
   constexpr int K = (DEG + 1) * (DEG + 1);
   constexpr int row = 3 * K + 1;
@@ -125,19 +124,22 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
     }
     const float idet = 1.f / det;
     const float A = cyy * idet, B = -cxy * idet, C = cxx * idet;
-    // largest eigenvalue and condition number of the 2-D covariance
-    const float hd = 0.5f * (cxx - cyy);
-    const float lmax = 0.5f * (cxx + cyy) + sqrtf(hd * hd + cxy * cxy);
-    const float kappa = lmax * lmax / det;
-    // exact support half-extents (they bound the culling boxes in both modes)
+    // support half-extents (exact support; they bound the culling boxes in both modes)
     const float h_sup = sqrtf(tau * cyy), rx_sup = sqrtf(tau * cxx);
+    // largest eigenvalue of the 2-D covariance
+    const auto eig_max = [&]() {
+      const float hd = 0.5f * (cxx - cyy);
+      return 0.5f * (cxx + cyy) + sqrtf(hd * hd + cxy * cxy);
+    };
+    float lmax = 0.f;
     BinParams b;
     b.mx = V.fx * pc.x * iz + V.cx;
     b.my = V.fy * pc.y * iz + V.cy;
-    if (P.three_sigma) {
+    if (THREE_SIGMA) {
       // the square of half-width r = ceil(3 sqrt(lambda_max)): with tau = 1,
       // no slope, no y-dependence and the extreme points out of reach, the
       // row functions return the square's rows and columns
+      lmax = eig_max();
       const float r = ceilf(3.f * sqrtf(lmax));
       b.tau = 1.f;
       b.k = 0.f;
@@ -164,6 +166,9 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
         if (row_tiles(b, ty, V.tiles_x, &a, &c)) count += (uint32_t)(c - a + 1);
       }
     }
+    // condition number of the 2-D covariance (for the culling boxes)
+    if (!THREE_SIGMA) lmax = eig_max();
+    const float kappa = lmax * lmax / det;
     P.st.tiles[item] = count;
     P.st.depth_key[item] = count ? __float_as_uint(pc.z) : kCulledKey;
     if (!count) continue;
@@ -516,15 +521,24 @@ cudaError_t launch_preprocess(const gs_scene& sc, const ViewDev* views, int n_vi
   P.znear = cfg.znear;
   P.lowpass = cfg.lowpass;
   P.alpha_min = cfg.alpha_min;
-  P.three_sigma = (cfg.flags & GS_FLAG_EXTENT_3SIGMA) != 0;
   P.st = st;
   const int blocks = ceil_div(sc.n, kPreThreads);
   if (blocks == 0) return cudaSuccess;
-  switch (sc.sh_degree) {
-    case 0: GS_TIMED("preprocess", stream, (preprocess_kernel<0><<<blocks, kPreThreads, 0, stream>>>(P))); break;
-    case 1: GS_TIMED("preprocess", stream, (preprocess_kernel<1><<<blocks, kPreThreads, 0, stream>>>(P))); break;
-    case 2: GS_TIMED("preprocess", stream, (preprocess_kernel<2><<<blocks, kPreThreads, 0, stream>>>(P))); break;
-    default: GS_TIMED("preprocess", stream, (preprocess_kernel<3><<<blocks, kPreThreads, 0, stream>>>(P))); break;
+  // the 3-sigma extent (GS_FLAG_EXTENT_3SIGMA) is a separate instance, so the
+  // default path carries none of it
+  const bool sq = (cfg.flags & GS_FLAG_EXTENT_3SIGMA) != 0;
+  switch (sc.sh_degree * 2 + (sq ? 1 : 0)) {
+#define GS_PRE(D, Q) \
+    GS_TIMED("preprocess", stream, (preprocess_kernel<D, Q><<<blocks, kPreThreads, 0, stream>>>(P))); break
+    case 0: GS_PRE(0, false);
+    case 1: GS_PRE(0, true);
+    case 2: GS_PRE(1, false);
+    case 3: GS_PRE(1, true);
+    case 4: GS_PRE(2, false);
+    case 5: GS_PRE(2, true);
+    case 7: GS_PRE(3, true);
+    default: GS_PRE(3, false);
+#undef GS_PRE
   }
   return cudaGetLastError();
 }

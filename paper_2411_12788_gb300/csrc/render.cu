@@ -64,6 +64,7 @@ struct FwdOut {
   float* depth_blend;
   float* weight_sum;
   uint32_t* max_area;
+  uint64_t* weight_sum_fixed;   // I_i in units of 2^-24 (integer sums: order-independent)
 };
 
 // Exponent form of an entry's 2-D Gaussian (identical in both kernels).
@@ -305,6 +306,7 @@ __device__ __forceinline__ void fwd_batch(FwdPix& q0, FwdPix& q1, int nb, int po
   }
 }
 
+template <bool kWantW>
 __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P, FwdOut O) {
   constexpr int kBatch = kTilePixels;
   __shared__ int s_view;
@@ -331,8 +333,6 @@ __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P,
   fwd_pix_init(q0, px, py, in0);
   fwd_pix_init(q1, px2, py, in1);
   const uint2 range = P.ranges[tile];
-  const bool want_w = O.weight_sum != nullptr;
-
   for (uint32_t bstart = range.x; bstart < range.y; bstart += kBatch) {
     if (__syncthreads_count(q0.done && q1.done) == kFwdThreads) break;
 #pragma unroll
@@ -352,16 +352,19 @@ __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P,
     __syncthreads();
     const int nb = (int)min(range.y - bstart, (uint32_t)kBatch);
     const int pos0 = (int)(bstart - range.x);
-    if (want_w) fwd_batch<true>(q0, q1, nb, pos0, s_xy, s_ex, s_rgbz, s_wsum, P, lane);
-    else fwd_batch<false>(q0, q1, nb, pos0, s_xy, s_ex, s_rgbz, s_wsum, P, lane);
+    fwd_batch<kWantW>(q0, q1, nb, pos0, s_xy, s_ex, s_rgbz, s_wsum, P, lane);
     __syncthreads();
-    if (want_w) {
+    if (kWantW) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int k = tid + h * kFwdThreads;
         if (k < nb) {
           const uint32_t s = s_wsum[k];
-          if (s) atomicAdd(&O.weight_sum[s_item[k]], (float)s * (1.f / 16777216.f));
+          if (s) {
+            if (O.weight_sum) atomicAdd(&O.weight_sum[s_item[k]], (float)s * (1.f / 16777216.f));
+            if (O.weight_sum_fixed)
+              atomicAdd(reinterpret_cast<unsigned long long*>(O.weight_sum_fixed) + s_item[k], (unsigned long long)s);
+          }
           s_wsum[k] = 0u;
         }
       }
@@ -384,6 +387,7 @@ struct BwdIn {
   const uint32_t* n_contrib;
   float4* grad2d;               // 3 x float4 per item
   float* weight_sum;            // optional: += I_i per item
+  uint64_t* weight_sum_fixed;   // optional: += I_i per item in units of 2^-24
 };
 
 // Backward of Eq. 1, two entries per lane.  For pixel x with blended entries
@@ -411,6 +415,7 @@ struct BwdEntry {
   float3 col;
   float acc[9];        // d(centre x, y), d(a2, b2, c2), d log2 o, d colour
   float wsum;          // blending weight over the warp's pixels (I_i)
+  uint32_t wfix;       // the same, each pixel's weight rounded to a multiple of 2^-24
 };
 
 __device__ __forceinline__ void bwd_entry_load(BwdEntry& E, bool valid, const float2* s_xy, const float4* s_ex,
@@ -425,13 +430,16 @@ __device__ __forceinline__ void bwd_entry_load(BwdEntry& E, bool valid, const fl
 #pragma unroll
   for (int k = 0; k < 9; ++k) E.acc[k] = 0.f;
   E.wsum = 0.f;
+  E.wfix = 0u;
 }
 
 // Adds one pixel's contribution to an active entry's gradient sums.
+template <bool kFix>
 __device__ __forceinline__ void bwd_entry_accumulate(BwdEntry& E, const float4& pg, float dx, float dy, float a,
                                                      float araw, float Tl, float Fl, float cg, float alpha_max) {
   const float w = a * Tl;
   E.wsum += w;
+  if (kFix) E.wfix += __float2uint_rn(w * 16777216.f);
   E.acc[6] = fmaf(w, pg.x, E.acc[6]);
   E.acc[7] = fmaf(w, pg.y, E.acc[7]);
   E.acc[8] = fmaf(w, pg.z, E.acc[8]);
@@ -449,14 +457,17 @@ __device__ __forceinline__ void bwd_entry_accumulate(BwdEntry& E, const float4& 
   }
 }
 
+template <bool kFix>
 __device__ __forceinline__ void bwd_entry_flush(const BwdEntry& E, float (*s_g)[kRenderThreads], float* s_wsum,
-                                                int idx, bool want_w) {
+                                                uint32_t* s_wfix, int idx, bool want_w) {
 #pragma unroll
   for (int k = 0; k < 9; ++k)
     if (E.acc[k] != 0.f) atomicAdd(&s_g[k][idx], E.acc[k]);
   if (want_w && E.wsum != 0.f) atomicAdd(&s_wsum[idx], E.wsum);
+  if (kFix && E.wfix) atomicAdd(&s_wfix[idx], E.wfix);
 }
 
+template <bool kFix>
 __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderParams P, BwdIn B) {
   constexpr int kWarps = kRenderThreads / 32;
   constexpr int kChunk = 64;                   // entries per warp step
@@ -469,6 +480,7 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
   __shared__ uint32_t s_item[kRenderThreads];
   __shared__ float s_g[9][kRenderThreads];
   __shared__ float s_wsum[kRenderThreads];     // I_i of the batch's entries (optional output)
+  __shared__ uint32_t s_wfix[kRenderThreads];  // the same in 2^-24 fixed point (optional output)
   __shared__ uint8_t s_list[kWarps][kRenderThreads];   // the batch entries each warp walks
   // per-pixel state, indexed by the pixel's thread id (warp w owns 32w..32w+31)
   __shared__ float4 s_pg[kRenderThreads];     // dL/dI (r, g, b) and I . dL/dI
@@ -513,6 +525,7 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
 #pragma unroll
   for (int k = 0; k < 9; ++k) s_g[k][tid] = 0.f;
   s_wsum[tid] = 0.f;
+  s_wfix[tid] = 0u;
   __syncthreads();
   const uint32_t max_nc = s_max_nc;
   const uint32_t warp_nc = s_warp_nc[warp];
@@ -601,11 +614,11 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
           float2* stp = reinterpret_cast<float2*>(&s_st[pt]);
           *stp = make_float2(T0 * m, fmaf(T0, f, F0));
         }
-        if (acta) bwd_entry_accumulate(A, pg, dxa, dya, aa, arawa, Ta, Fa, cga, P.alpha_max);
-        if (actb) bwd_entry_accumulate(Bn, pg, dxb, dyb, ab, arawb, Tb, Fb, cgb, P.alpha_max);
+        if (acta) bwd_entry_accumulate<kFix>(A, pg, dxa, dya, aa, arawa, Ta, Fa, cga, P.alpha_max);
+        if (actb) bwd_entry_accumulate<kFix>(Bn, pg, dxb, dyb, ab, arawb, Tb, Fb, cgb, P.alpha_max);
       }
-      if (va) bwd_entry_flush(A, s_g, s_wsum, ia, want_w);
-      if (vb) bwd_entry_flush(Bn, s_g, s_wsum, ib, want_w);
+      if (va) bwd_entry_flush<kFix>(A, s_g, s_wsum, s_wfix, ia, want_w);
+      if (vb) bwd_entry_flush<kFix>(Bn, s_g, s_wsum, s_wfix, ib, want_w);
     }
     __syncthreads();
     if (tid < nb) {
@@ -622,6 +635,11 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
       if (v[4] != 0.f || v[5] != 0.f || v[6] != 0.f || v[7] != 0.f)
         atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
       if (v[8] != 0.f) atomicAdd(&dst[2].x, v[8]);
+      if (kFix) {
+        const uint32_t wf = s_wfix[tid];
+        s_wfix[tid] = 0u;
+        if (wf) atomicAdd(reinterpret_cast<unsigned long long*>(B.weight_sum_fixed) + item, (unsigned long long)wf);
+      }
       if (want_w) {
         const float ws = s_wsum[tid];
         s_wsum[tid] = 0.f;
@@ -660,20 +678,27 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
                               const gs_fwd_outputs& out, cudaStream_t stream) {
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
   FwdOut O{out.image, out.final_T, out.n_contrib, out.imax, out.wmax, out.depth, out.depth_blend,
-           out.weight_sum, out.max_area};
+           out.weight_sum, out.max_area, out.weight_sum_fixed};
   if (total_tiles > 0)
-    GS_TIMED("render_fwd", stream, (render_fwd_kernel<<<total_tiles, kFwdThreads, 0, stream>>>(P, O)));
+    GS_TIMED("render_fwd", stream,
+             (O.weight_sum || O.weight_sum_fixed
+                  ? render_fwd_kernel<true><<<total_tiles, kFwdThreads, 0, stream>>>(P, O)
+                  : render_fwd_kernel<false><<<total_tiles, kFwdThreads, 0, stream>>>(P, O)));
   return cudaGetLastError();
 }
 
 cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
                               const uint32_t* vals, const ItemState& st, const gs_config& cfg,
                               const float* dL_dimage, const float* image, const uint32_t* n_contrib,
-                              float4* grad2d, float* weight_sum, cudaStream_t stream) {
+                              float4* grad2d, float* weight_sum, uint64_t* weight_sum_fixed, cudaStream_t stream) {
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
-  BwdIn B{dL_dimage, image, n_contrib, grad2d, weight_sum};
-  if (total_tiles > 0)
-    GS_TIMED("render_bwd", stream, (render_bwd_kernel<<<total_tiles, kRenderThreads, 0, stream>>>(P, B)));
+  BwdIn B{dL_dimage, image, n_contrib, grad2d, weight_sum, weight_sum_fixed};
+  if (total_tiles > 0) {
+    if (weight_sum_fixed)
+      GS_TIMED("render_bwd", stream, (render_bwd_kernel<true><<<total_tiles, kRenderThreads, 0, stream>>>(P, B)));
+    else
+      GS_TIMED("render_bwd", stream, (render_bwd_kernel<false><<<total_tiles, kRenderThreads, 0, stream>>>(P, B)));
+  }
   return cudaGetLastError();
 }
 

@@ -311,15 +311,17 @@ FWD_OUTPUTS = ("image", "final_T", "n_contrib", "imax", "wmax", "depth", "depth_
 def alloc_outputs(plan, device="cuda", want=FWD_OUTPUTS) -> dict:
     P, I = int(plan.total_pixels), int(plan.n_items)
     f32, i32 = torch.float32, torch.int32
+    # weight_sum_fixed (not among the defaults): I_i in units of 2^-24 as
+    # integers, bit-reproducible (unsigned 64-bit in the library, int64 here)
     spec = {"image": (3 * P, f32), "final_T": (P, f32), "n_contrib": (P, i32), "imax": (P, i32),
             "wmax": (P, f32), "depth": (P, f32), "depth_blend": (P, f32),
-            "weight_sum": (I, f32), "max_area": (I, i32)}
+            "weight_sum": (I, f32), "max_area": (I, i32), "weight_sum_fixed": (I, torch.int64)}
     out = {}
-    for k in FWD_OUTPUTS:
+    for k in spec:
         if k in want or k in ("image", "final_T", "n_contrib"):
             n, dt = spec[k]
             out[k] = torch.empty(max(n, 1), dtype=dt, device=device)[:n]
-    for k in ("weight_sum", "max_area"):
+    for k in ("weight_sum", "max_area", "weight_sum_fixed"):
         if k in out:
             out[k].zero_()
     return out

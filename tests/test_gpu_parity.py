@@ -366,6 +366,34 @@ def test_backward_collects_the_forward_weight_sums():
     assert torch.all((a - b).abs() <= 1e-4 + 1e-5 * b.abs())
 
 
+def test_fixed_point_weight_sums_are_reproducible():
+    """weight_sum_fixed (I_i in units of 2^-24, integer sums): bit-identical over
+    repeated forward and backward passes, and within the per-pixel rounding of
+    the float I_i; the backward's equals the forward's within the same bound."""
+    _need_gpu()
+    sc, cams = SCENES["box512_deg3_multiview"]()
+    g = raster.GaussianTensors.from_scene(sc)
+    want = raster.FWD_OUTPUTS + ("weight_sum_fixed",)
+    runs = [raster.forward(g, cams, want=want) for _ in range(3)]
+    fx = [fr.outs["weight_sum_fixed"].cpu() for fr in runs]
+    assert all(torch.equal(fx[0], f) for f in fx[1:])
+    fl = runs[0].outs["weight_sum"].double().cpu()
+    fixed = fx[0].double() / 2.0 ** 24
+    assert fl.max() > 1.0
+    assert torch.all((fixed - fl).abs() <= 1e-4 + 1e-5 * fl.abs())
+    fr = runs[0]
+    dL = torch.rand_like(fr.outs["image"]) - 0.5
+    bw = []
+    for _ in range(2):
+        grads = raster.alloc_grads(g)
+        grads["weight_sum_fixed"] = torch.zeros(int(fr.plan.n_items), dtype=torch.int64, device="cuda")
+        raster.render_bwd(fr.plan, g.struct(), fr.cfg, fr.pre_ws, fr.sort_ws, dL, fr.outs["image"],
+                          fr.outs["n_contrib"], grads)
+        bw.append(grads["weight_sum_fixed"].cpu())
+    assert torch.equal(bw[0], bw[1])
+    assert torch.all((bw[0].double() / 2.0 ** 24 - fixed).abs() <= 1e-4 + 1e-5 * fixed.abs())
+
+
 def test_autograd_function_and_recompute():
     """The torch.autograd.Function gives the same gradients whether the sorted
     lists are kept or rebuilt in backward."""
