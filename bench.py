@@ -536,9 +536,10 @@ def run_c1_step(iters: int = 5) -> dict:
 def run_e2e(st: Step, args, world) -> dict:
     """The same step with host buffers: every step copies its scene and target
     images in from pinned host memory and its loss and gradients (and I_i)
-    back out.  The copies run on a second stream with two device buffer sets,
-    so step k+1's upload and step k's download overlap step k's compute; all
-    of them are inside the timed region."""
+    back out.  Uploads and downloads run on two more streams (one per
+    direction, so both copy directions are busy at once) with two device
+    buffer sets, so step k+1's upload and step k's download overlap step k's
+    compute; all of them are inside the timed region."""
     import torch
     from paper_2411_12788_gb300 import raster
     names = ("means", "scales", "rotations", "opacities", "sh")
@@ -556,30 +557,33 @@ def run_e2e(st: Step, args, world) -> dict:
     h2d = sum(t.numel() * 4 for t in host_in.values()) + host_tg.numel() * 4
     d2h = sum(t.numel() * 4 for t in sets[0]["host_out"].values()) + 4
     compute = torch.cuda.current_stream()
-    copy = torch.cuda.Stream()
-    ready = [torch.cuda.Event(), torch.cuda.Event()]
-    done = [torch.cuda.Event(), torch.cuda.Event()]
+    copy_in, copy_out = torch.cuda.Stream(), torch.cuda.Stream()
+    ready = [torch.cuda.Event(), torch.cuda.Event()]       # set b's inputs are uploaded
+    done = [torch.cuda.Event(), torch.cuda.Event()]        # the step using set b has finished
+    fetched = [torch.cuda.Event(), torch.cuda.Event()]     # set b's outputs are downloaded
     orig = (st.g, st.target, st.grads, st.loss)
 
     def upload(b):
-        with torch.cuda.stream(copy):
-            copy.wait_event(done[b])                 # the step that last read set b is finished
+        with torch.cuda.stream(copy_in):
+            copy_in.wait_event(done[b])              # the step that last read set b is finished
             for k in names:
                 getattr(sets[b]["g"], k).copy_(host_in[k], non_blocking=True)
             sets[b]["target"].copy_(host_tg, non_blocking=True)
-            ready[b].record(copy)
+            ready[b].record(copy_in)
 
     def run(k):
         b = k % 2
         compute.wait_event(ready[b])
+        compute.wait_event(fetched[b])               # the last download of set b's outputs
         st.g, st.target, st.grads, st.loss = sets[b]["g"], sets[b]["target"], sets[b]["grads"], sets[b]["loss"]
         st.run()
         done[b].record(compute)
-        with torch.cuda.stream(copy):
-            copy.wait_event(done[b])
+        with torch.cuda.stream(copy_out):
+            copy_out.wait_event(done[b])
             for key, v in sets[b]["grads"].items():
                 sets[b]["host_out"][key].copy_(v, non_blocking=True)
             sets[b]["host_loss"].copy_(sets[b]["loss"], non_blocking=True)
+            fetched[b].record(copy_out)
 
     def steps(n):
         upload(0)
@@ -588,7 +592,8 @@ def run_e2e(st: Step, args, world) -> dict:
             run(k)
             if k + 2 < n:
                 upload(k % 2)                       # inputs of step k+2 go into the set step k used
-        compute.wait_stream(copy)                   # the last downloads are part of the run
+        compute.wait_stream(copy_in)
+        compute.wait_stream(copy_out)               # the last downloads are part of the run
 
     steps(3)
     torch.cuda.synchronize()
@@ -605,7 +610,8 @@ def run_e2e(st: Step, args, world) -> dict:
     units, sec_max = aggregate(st.pixels * args.steps, sec, world)
     return {"value": units / sec_max / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": sec_max * 1e3 / args.steps,
-            "overlap": "double-buffered: uploads and downloads on a copy stream overlap the previous/next step"}
+            "overlap": "double-buffered: uploads and downloads on one stream per direction overlap the "
+                       "previous/next step"}
 
 
 def run_serving(st: Step, args) -> dict:

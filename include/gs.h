@@ -20,6 +20,10 @@
  *  - Every call is asynchronous on `stream` (a cudaStream_t, NULL = legacy
  *    default stream) except gs_preprocess, which reads back one 8-byte
  *    count (the number of tile entries) and therefore synchronises `stream`.
+ *    The read-back goes through one pinned, mapped host word per host thread
+ *    (allocated on first use and kept), written by a kernel: no copy engine
+ *    is involved, so large transfers on other streams do not delay it; the
+ *    per-view constants are likewise passed to a kernel by value.
  *  - Every call returns a gs_status; arguments are validated on the host
  *    before any launch (GS_ERR_INVALID_ARG).  Device-side checks (entry
  *    overflow, a radix-sort look-back that exceeded its spin budget) set a
@@ -190,7 +194,8 @@ size_t gs_bin_sort_workspace_size(const gs_plan* plan);
  * min over its pixel-centre rectangle of d^T conic d <= 2 ln(o / alpha_min).
  * Then sorts the items by the float32 depth of their centres (stable, ties
  * by item) and scans the tile counts in that order; stores the total in
- * plan->n_entries (one device->host read, synchronises `stream`).
+ * plan->n_entries (one read-back through mapped host memory, synchronises
+ * `stream`).
  * mask: device [n_items] bytes or NULL (view-dependent culling, Sec. 5.2).
  * cfg is read on the host. */
 gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* cfg,

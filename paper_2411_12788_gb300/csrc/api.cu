@@ -1,6 +1,8 @@
 // C ABI of the rasterizer: plans, workspace layouts, argument validation and
 // the launch sequences of gs_preprocess / gs_bin_sort / gs_render_fwd /
-// gs_render_bwd.  No allocation happens here: every buffer is the caller's.
+// gs_render_bwd.  Every device buffer is the caller's; the only allocation is
+// one pinned, mapped 16-byte host word per host thread (first use, kept for
+// the process) through which gs_preprocess reads its status and entry count.
 #include <math.h>
 #include <string.h>
 
@@ -10,6 +12,52 @@
 
 namespace gs {
 namespace {
+
+// The per-view constants, handed to a kernel by value (so the upload takes
+// no copy engine, whose queue may hold other streams' large transfers).
+struct ViewTable {
+  ViewDev v[GS_MAX_VIEWS];
+};
+static_assert(sizeof(ViewTable) <= 32000, "kernel parameters are limited to 32764 bytes");
+
+// Writes the plan's views into the workspace and clears the status words.
+__global__ void set_views_kernel(const ViewTable t, int n_views, ViewDev* __restrict__ dst,
+                                 uint32_t* __restrict__ status) {
+  const int i = threadIdx.x;
+  if (i < n_views) dst[i] = t.v[i];
+  if (i < 4) status[i] = 0u;
+}
+
+// Copies the status word and the entry count (16 bytes) into mapped host
+// memory: the read-back then needs only the stream synchronisation.
+__global__ void copy_head_kernel(const uint64_t* __restrict__ src, volatile uint64_t* dst) {
+  if (threadIdx.x < 2) dst[threadIdx.x] = src[threadIdx.x];
+}
+
+struct HostHead {
+  volatile uint64_t* host = nullptr;   // pinned, mapped
+  uint64_t* dev = nullptr;             // its device address
+};
+
+// This host thread's head word pair, allocated on first use.
+cudaError_t host_head(HostHead** out) {
+  thread_local HostHead hh;
+  if (!hh.host) {
+    void* p = nullptr;
+    cudaError_t e = cudaHostAlloc(&p, 16, cudaHostAllocMapped | cudaHostAllocPortable);
+    if (e != cudaSuccess) return e;
+    void* dp = nullptr;
+    e = cudaHostGetDevicePointer(&dp, p, 0);
+    if (e != cudaSuccess) {
+      cudaFreeHost(p);
+      return e;
+    }
+    hh.host = static_cast<volatile uint64_t*>(p);
+    hh.dev = static_cast<uint64_t*>(dp);
+  }
+  *out = &hh;
+  return cudaSuccess;
+}
 
 PreLayout pre_layout(const gs_plan& p) {
   PreLayout L;
@@ -187,8 +235,9 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
   if (pre_ws_bytes < L.total) return GS_ERR_CAPACITY;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
 
-  ViewDev views[GS_MAX_VIEWS];
-  memset(views, 0, sizeof(views));
+  ViewTable table;
+  memset(&table, 0, sizeof(table));
+  ViewDev* views = table.v;
   for (int v = 0; v < plan->n_views; ++v) {
     const gs_camera& c = plan->cams[v];
     ViewDev& V = views[v];
@@ -208,9 +257,12 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
     V.tile_base = plan->tile_base[v];
     V.pixel_base = plan->pixel_base[v];
   }
-  cudaError_t e = cudaMemcpyAsync(at<ViewDev>(pre_ws, L.views), views, sizeof(ViewDev) * plan->n_views,
-                                  cudaMemcpyHostToDevice, stream);
-  if (e == cudaSuccess) e = cudaMemsetAsync(at<char>(pre_ws, L.status), 0, 16, stream);
+  HostHead* head = nullptr;
+  cudaError_t e = host_head(&head);
+  if (e != cudaSuccess) return GS_ERR_CUDA;
+  set_views_kernel<<<1, GS_MAX_VIEWS, 0, stream>>>(table, plan->n_views, at<ViewDev>(pre_ws, L.views),
+                                                    at<uint32_t>(pre_ws, L.status));
+  e = cudaGetLastError();
   if (e != cudaSuccess) return GS_ERR_CUDA;
   if (plan->n_items == 0) {
     plan->n_entries = 0;
@@ -229,14 +281,15 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
                               plan->n_items, at<uint64_t>(pre_ws, L.scan_blocks),
                               at<unsigned long long>(pre_ws, L.n_entries), stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
-  uint64_t head[2];
-  e = cudaMemcpyAsync(head, at<char>(pre_ws, L.status), 16, cudaMemcpyDeviceToHost, stream);
+  copy_head_kernel<<<1, 32, 0, stream>>>(at<uint64_t>(pre_ws, L.status), head->dev);
+  e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
-  const uint32_t st_word = (uint32_t)(head[0] & 0xffffffffu);
+  const uint64_t h0 = head->host[0], h1 = head->host[1];
+  const uint32_t st_word = (uint32_t)(h0 & 0xffffffffu);
   if (st_word & kStatusTimeout) return GS_ERR_TIMEOUT;
-  if (head[1] >= ((uint64_t)1 << 30)) return GS_ERR_CAPACITY;    // entries beyond the sort's range
-  plan->n_entries = (int64_t)head[1];
+  if (h1 >= ((uint64_t)1 << 30)) return GS_ERR_CAPACITY;    // entries beyond the sort's range
+  plan->n_entries = (int64_t)h1;
   return GS_OK;
 }
 
