@@ -145,6 +145,8 @@ typedef struct gs_fwd_outputs {
                                pixel's weight is rounded once to a multiple of 2^-24 and the
                                sums are integer, so the result does not depend on the order of
                                the atomic adds (bit-reproducible, unlike weight_sum) */
+  float* depth_center;      /* [total_pixels] d^center = camera z of i_max's centre (the
+                               alternative depth of Sec. 4.1), 0 if none */
 } gs_fwd_outputs;
 
 /* Gradients, device, ACCUMULATED (+=) over views, same layouts as gs_scene;

@@ -76,7 +76,8 @@ def render_view(proj: dict, cam, cfg: OracleConfig | None = None, pix=None,
     pix: optional [P, 2] integer (u, v) pixel coordinates; default the full
     image in row-major order.  Returns per-pixel tensors of length P:
       colour [P,3], t_final, imax (Gaussian index or -1), wmax, depth (d^mid
-      of i_max, 0 if none), depth_blend, last (index of the last blended
+      of i_max, 0 if none), depth_center (z of i_max's centre, the
+      alternative of Sec. 4.1, 0 if none), depth_blend, last (index of the last blended
       Gaussian or -1), n_blended, flags (near-threshold events, see
       _flags); and per-Gaussian: weight_sum [N] (I_i) and max_area [N] (S_i).
     """
@@ -95,7 +96,7 @@ def render_view(proj: dict, cam, cfg: OracleConfig | None = None, pix=None,
     bg = torch.tensor(cfg.bg, dtype=f64)
     sq = _square_rects(proj, oi, cam, cfg) if cfg.extent == "3sigma" else None
 
-    colours, tfin, imax, wmax, depth, dblend, last, nbl, flags = ([] for _ in range(9))
+    colours, tfin, imax, wmax, depth, dblend, last, nbl, flags, dcen = ([] for _ in range(10))
     wsum = torch.zeros(N, dtype=f64)
     area = torch.zeros(N, dtype=torch.long)
     step = max(1, chunk_elems // max(M, 1))
@@ -123,6 +124,7 @@ def render_view(proj: dict, cam, cfg: OracleConfig | None = None, pix=None,
         am = torch.argmax(wd, dim=1) if M > 0 else torch.zeros(len(u), dtype=torch.long)
         gi = torch.where(has, oi[am] if M > 0 else am, torch.full_like(am, -1))
         imax.append(gi)
+        dcen.append(torch.where(has, proj["z"].detach()[gi.clamp(min=0)], torch.zeros(len(u), dtype=f64)))
         wmax.append(torch.where(has, wd.gather(1, am[:, None])[:, 0] if M > 0 else wd.sum(1),
                                 torch.zeros(len(u), dtype=f64)))
         pos = torch.arange(M).expand(len(u), M)
@@ -147,7 +149,7 @@ def render_view(proj: dict, cam, cfg: OracleConfig | None = None, pix=None,
         flags.append(fl)
     cat = lambda xs: torch.cat(xs) if xs else torch.zeros(0)
     out = dict(colour=cat(colours), t_final=cat(tfin), imax=cat(imax), wmax=cat(wmax),
-               depth_blend=cat(dblend), last=cat(last), n_blended=cat(nbl),
+               depth_blend=cat(dblend), depth_center=cat(dcen), last=cat(last), n_blended=cat(nbl),
                flags=cat(flags), weight_sum=wsum, max_area=area,
                u=torch.as_tensor(uu), v=torch.as_tensor(vv))
     if want_depth:

@@ -65,6 +65,7 @@ struct FwdOut {
   float* weight_sum;
   uint32_t* max_area;
   uint64_t* weight_sum_fixed;   // I_i in units of 2^-24 (integer sums: order-independent)
+  float* depth_center;          // camera z of i_max's centre
 };
 
 // Exponent form of an entry's 2-D Gaussian (identical in both kernels).
@@ -189,6 +190,7 @@ __device__ __forceinline__ void fwd_pix_store(const FwdPix& q, const RenderParam
   if (O.imax) O.imax[pix] = imax_item >= 0 ? (int32_t)(imax_item - (int64_t)view * P.n) : -1;
   if (O.wmax) O.wmax[pix] = q.wmax;
   if (O.depth_blend) O.depth_blend[pix] = q.dblend;
+  if (O.depth_center) O.depth_center[pix] = imax_item >= 0 ? P.xy_tau_z[imax_item].w : 0.f;
   if (O.depth) {
     float d = 0.f;
     if (imax_item >= 0) {
@@ -678,7 +680,7 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
                               const gs_fwd_outputs& out, cudaStream_t stream) {
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
   FwdOut O{out.image, out.final_T, out.n_contrib, out.imax, out.wmax, out.depth, out.depth_blend,
-           out.weight_sum, out.max_area, out.weight_sum_fixed};
+           out.weight_sum, out.max_area, out.weight_sum_fixed, out.depth_center};
   if (total_tiles > 0)
     GS_TIMED("render_fwd", stream,
              (O.weight_sum || O.weight_sum_fixed

@@ -167,6 +167,9 @@ def _check_render(sc, cams, fr, max_flag_frac=2e-3, cfg=None):
         d = _gpu_pixels(fr, v, "depth").double().numpy()
         dref = out["depth"].numpy()
         assert np.all(np.abs(d - dref)[ok] <= 1e-4 * np.maximum(1.0, np.abs(dref[ok])))
+        dc = _gpu_pixels(fr, v, "depth_center").double().numpy()
+        dcr = out["depth_center"].numpy()
+        assert np.all(np.abs(dc - dcr)[ok] <= 1e-5 * np.maximum(1.0, np.abs(dcr[ok])))
         db = _gpu_pixels(fr, v, "depth_blend").double().numpy()
         dbr = out["depth_blend"].numpy()
         assert np.all(np.abs(db - dbr)[ok] <= 1e-4 * np.maximum(1.0, np.abs(dbr[ok])))

@@ -184,6 +184,8 @@ def test_single_isotropic_gaussian_closed_form(o):
     d_ref = z0 / (1 + (dx / f) ** 2 + (dy / f) ** 2)
     np.testing.assert_allclose(out["depth"].numpy()[hit], d_ref[hit], rtol=1e-12)
     np.testing.assert_allclose(out["depth_blend"].numpy(), a * z0, rtol=1e-12)
+    # d^center is the centre's depth wherever the Gaussian is the max-weight one
+    np.testing.assert_array_equal(out["depth_center"].numpy(), np.where(hit, z0, 0.0))
     if o >= 0.99 / math.exp(-(0.5 ** 2 * 2) / (2 * sig2)):
         # the four central pixels are clamped to exactly alpha_max
         centre = (np.abs(dx) == 0.5) & (np.abs(dy) == 0.5)
