@@ -94,6 +94,11 @@ typedef struct gs_config {
  * support is truncated there.  Must be the same in every call on one plan. */
 #define GS_FLAG_EXTENT_3SIGMA 2u
 
+/* gs_preprocess reads its mask as bits (see gs_preprocess): the per-view
+ * visibility of many training views (Sec. 5.2) kept at one bit per
+ * Gaussian. */
+#define GS_FLAG_MASK_BITS 4u
+
 /* Gaussian attributes, device, FP32, structure of arrays:
  *   means [n][3], scales [n][3], rotations [n][4] (w,x,y,z), opacities [n],
  *   sh [n][sh_coeffs][3] (band-major, m = -l..l, RGB innermost).
@@ -198,11 +203,20 @@ size_t gs_bin_sort_workspace_size(const gs_plan* plan);
  * by item) and scans the tile counts in that order; stores the total in
  * plan->n_entries (one read-back through mapped host memory, synchronises
  * `stream`).
- * mask: device [n_items] bytes or NULL (view-dependent culling, Sec. 5.2).
- * cfg is read on the host. */
+ * mask: device [n_items] bytes or NULL (view-dependent culling, Sec. 5.2);
+ * with GS_FLAG_MASK_BITS in cfg->flags it is instead a bit mask of
+ * n_views rows of ceil(n / 32) 32-bit words (4-byte aligned): Gaussian g of
+ * view v is kept iff bit g % 32 of word v * ceil(n / 32) + g / 32 is set
+ * (gs_pack_mask makes one from a byte mask).  cfg is read on the host. */
 gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* cfg,
                         const uint8_t* mask, void* pre_ws, size_t pre_ws_bytes,
                         void* stream);
+
+/* Packs a byte mask (device [n_views * n], non-zero = keep) into the bit
+ * mask GS_FLAG_MASK_BITS reads: bits, device [n_views][ceil(n / 32)] 32-bit
+ * words, 4-byte aligned, OVERWRITTEN (padding bits zero).  Asynchronous;
+ * GS_ERR_INVALID_ARG for bad sizes or pointers. */
+gs_status gs_pack_mask(const uint8_t* mask, int64_t n, int32_t n_views, uint32_t* bits, void* stream);
 
 /* Emits one (global tile id, item) entry per touched tile in depth order,
  * radix-sorts the entries by tile id (stable, so each tile's list stays in

@@ -16,6 +16,7 @@ GS_TILE = 16
 GS_MAX_VIEWS = 64
 GS_FLAG_ZERO_ACCUM = 1
 GS_FLAG_EXTENT_3SIGMA = 2
+GS_FLAG_MASK_BITS = 4
 GS_SELFTEST_SCRATCH_BYTES = 4096
 GS_ERR_TIMEOUT = 4
 
@@ -99,6 +100,7 @@ SIGNATURES = {
     "gs_bin_sort_workspace_size": (C.c_size_t, [C.POINTER(Plan)]),
     "gs_preprocess": (C.c_int, [C.POINTER(Plan), C.POINTER(Scene), C.POINTER(Config), C.c_void_p,
                                 C.c_void_p, C.c_size_t, C.c_void_p]),
+    "gs_pack_mask": (C.c_int, [C.c_void_p, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p]),
     "gs_bin_sort": (C.c_int, [C.POINTER(Plan), C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]),
     "gs_render_fwd": (C.c_int, [C.POINTER(Plan), C.POINTER(Config), C.c_void_p, C.c_void_p,
                                 C.POINTER(FwdOutputs), C.c_void_p]),

@@ -34,6 +34,17 @@ __global__ void copy_head_kernel(const uint64_t* __restrict__ src, volatile uint
   if (threadIdx.x < 2) dst[threadIdx.x] = src[threadIdx.x];
 }
 
+// bits[v][g / 32] bit g % 32 = (mask[v * n + g] != 0); one ballot per 32
+// Gaussians (blockIdx.y = view), padding bits zero.
+__global__ void pack_mask_kernel(const uint8_t* __restrict__ mask, int64_t n, uint32_t* __restrict__ bits,
+                                 int64_t words) {
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t v = blockIdx.y;
+  const bool keep = g < n && mask[v * n + g] != 0;
+  const uint32_t b = __ballot_sync(0xffffffffu, keep);
+  if ((threadIdx.x & 31) == 0 && (g >> 5) < words) bits[v * words + (g >> 5)] = b;
+}
+
 struct HostHead {
   volatile uint64_t* host = nullptr;   // pinned, mapped
   uint64_t* dev = nullptr;             // its device address
@@ -231,6 +242,7 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
                         void* pre_ws, size_t pre_ws_bytes, void* stream_) {
   if (!valid_plan(plan) || !valid_config(cfg) || !valid_scene(plan, scene)) return GS_ERR_INVALID_ARG;
   if (!pre_ws || !aligned(pre_ws, 256)) return GS_ERR_INVALID_ARG;
+  if (mask && (cfg->flags & GS_FLAG_MASK_BITS) && !aligned(mask, 4)) return GS_ERR_INVALID_ARG;
   const PreLayout L = pre_layout(*plan);
   if (pre_ws_bytes < L.total) return GS_ERR_CAPACITY;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
@@ -376,6 +388,18 @@ gs_status gs_loss_l1(const float* image, const float* target, int64_t count, flo
                      void* stream) {
   if (!image || !target || !loss || !dL_dimage || count < 0) return GS_ERR_INVALID_ARG;
   return cuda_status(launch_loss_l1(image, target, count, loss, dL_dimage, static_cast<cudaStream_t>(stream)));
+}
+
+gs_status gs_pack_mask(const uint8_t* mask, int64_t n, int32_t n_views, uint32_t* bits, void* stream_) {
+  if (n < 0 || n_views < 1 || n_views > 65535 || (n > 0 && (!mask || !bits || !aligned(bits, 4))))
+    return GS_ERR_INVALID_ARG;
+  if (n == 0) return GS_OK;
+  const int64_t words = (n + 31) / 32;
+  const int64_t blocks = (words * 32 + 255) / 256;
+  if (blocks > 0x7fffffff) return GS_ERR_INVALID_ARG;
+  pack_mask_kernel<<<dim3((unsigned)blocks, (unsigned)n_views), 256, 0, static_cast<cudaStream_t>(stream_)>>>(
+      mask, n, bits, words);
+  return cuda_status(cudaGetLastError());
 }
 
 gs_status gs_device_status(const gs_plan* plan, void* pre_ws, void* stream_) {

@@ -32,6 +32,8 @@ struct PreParams {
   const ViewDev* views;
   int n_views;
   const uint8_t* mask;
+  bool mask_bits;              // GS_FLAG_MASK_BITS: mask is [n_views][mask_words] 32-bit words
+  int64_t mask_words;
   float znear, lowpass, alpha_min;
   ItemState st;
 };
@@ -82,7 +84,12 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
     const ViewDev& V = P.views[v];
     const int64_t item = (int64_t)v * P.n + i;
     bool vis = tau > 0.f;
-    if (vis && P.mask) vis = P.mask[item] != 0;
+    if (vis && P.mask) {
+      if (P.mask_bits)
+        vis = (reinterpret_cast<const uint32_t*>(P.mask)[v * P.mask_words + (i >> 5)] >> (i & 31)) & 1u;
+      else
+        vis = P.mask[item] != 0;
+    }
     if (!vis) {
       cull(P.st, item);
       continue;
@@ -518,6 +525,8 @@ cudaError_t launch_preprocess(const gs_scene& sc, const ViewDev* views, int n_vi
   P.views = views;
   P.n_views = n_views;
   P.mask = mask;
+  P.mask_bits = (cfg.flags & GS_FLAG_MASK_BITS) != 0;
+  P.mask_words = (sc.n + 31) / 32;
   P.znear = cfg.znear;
   P.lowpass = cfg.lowpass;
   P.alpha_min = cfg.alpha_min;

@@ -196,6 +196,16 @@ def identify(plan, weight_sum: torch.Tensor, max_area: torch.Tensor, imax: torch
     return {"flags": flags[:I], "visible_mask": vis[:I], "counts": counts}
 
 
+def pack_mask(mask: torch.Tensor, n: int, n_views: int, stream=None) -> torch.Tensor:
+    """Byte mask [n_views * n] -> the bit mask GS_FLAG_MASK_BITS reads
+    (gs_pack_mask): int32 [n_views, ceil(n / 32)], bit g % 32 of word g / 32
+    of row v keeps Gaussian g in view v."""
+    words = (int(n) + 31) // 32
+    bits = torch.empty((int(n_views), max(words, 1)), dtype=torch.int32, device=mask.device)
+    check("gs_pack_mask", lib().gs_pack_mask(_ptr(mask), int(n), int(n_views), _ptr(bits), _stream(stream)))
+    return bits[:, :words]
+
+
 def clone_gaussians(g: "GaussianTensors", idx: torch.Tensor, stream=None) -> "GaussianTensors":
     """Aggressive clone (gs_clone_gaussians): a scene of n + k rows in which
     each Gaussian idx[r] is replaced by a clone pair (rows idx[r], n + r)."""

@@ -10,7 +10,7 @@ import pytest
 import torch
 
 from oracle import identify as OI
-from paper_2411_12788_gb300 import raster, scenes
+from paper_2411_12788_gb300 import _lib, raster, scenes
 
 pytestmark = pytest.mark.gpu
 
@@ -108,6 +108,32 @@ def test_visibility_mask_culls_in_preprocess():
     for k in ("image", "final_T", "n_contrib", "depth"):
         assert torch.equal(masked.outs[k], sub.outs[k]), k
     assert masked.plan.n_entries < fr.plan.n_entries
+
+
+def test_bit_mask_culls_like_the_byte_mask():
+    """GS_FLAG_MASK_BITS: the mask packed by gs_pack_mask (one bit per
+    Gaussian and view, rows padded to 32-bit words) culls exactly what the
+    byte mask culls; the packed bits are the byte mask's, padding zero."""
+    _need_gpu()
+    n = 3001                                       # rows end in a partial word
+    sc = scenes.cluster_scene(n, 16, seed=8, sh_degree=1)
+    cams = _cams()
+    g = raster.GaussianTensors.from_scene(sc)
+    rng = np.random.default_rng(9)
+    byte = (rng.random(n * len(cams)) < 0.7).astype(np.uint8)
+    mask = torch.as_tensor(byte).cuda()
+    bits = raster.pack_mask(mask, n, len(cams))
+    words = bits.cpu().numpy().view(np.uint32)
+    assert words.shape == (len(cams), (n + 31) // 32)
+    unpacked = ((words[:, :, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(len(cams), -1)
+    np.testing.assert_array_equal(unpacked[:, :n].reshape(-1), byte)
+    assert not unpacked[:, n:].any()
+    a = raster.forward(g, cams, mask=mask)
+    b = raster.forward(g, cams, cfg=raster.make_config(flags=_lib.GS_FLAG_MASK_BITS), mask=bits.contiguous())
+    assert a.plan.n_entries == b.plan.n_entries
+    np.testing.assert_array_equal(raster.inspect_preprocess(a)["tiles"].numpy(), raster.inspect_preprocess(b)["tiles"].numpy())
+    for k in ("image", "final_T", "n_contrib", "imax", "depth"):
+        assert torch.equal(a.outs[k], b.outs[k]), k
 
 
 def test_identify_view_that_sees_nothing():
