@@ -191,8 +191,8 @@ def kernel_times(collect=True) -> dict:
 # valid while the kernel's source file is the one profiled (its SHA-256) and the workload has the same number
 # of tile entries; otherwise the traffic is reported as null.
 PROFILED_TRAFFIC = {
-    "render_bwd": {"bytes": 589.91e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
-                   "sha256": "48cf3c4f2276c2506dcaa788684a3a5ee88ed22a5d93525c5ba7faa0a34bf210",
+    "render_bwd": {"bytes": 591.03e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
+                   "sha256": "cfff5f9173fa09b74eef5ae9eb8ae2e4af187ac4a3b938b3951c00b5f0c46e03",
                    "profile": "profiles/render_bwd_1M_8views.md"},
 }
 
