@@ -140,6 +140,7 @@ ItemState item_state(void* ws, const PreLayout& L) {
   s.bin = at<float4>(ws, L.bin);
   s.tiles = at<uint32_t>(ws, L.tiles);
   s.depth_key = at<uint32_t>(ws, L.depth_key);
+  s.depth_val = at<uint32_t>(ws, L.sort_vals);
   return s;
 }
 
@@ -283,7 +284,6 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
   const ItemState st = item_state(pre_ws, L);
   uint32_t* status = at<uint32_t>(pre_ws, L.status);
   e = launch_preprocess(*scene, at<ViewDev>(pre_ws, L.views), plan->n_views, mask, *cfg, st, stream);
-  if (e == cudaSuccess) e = launch_iota(at<uint32_t>(pre_ws, L.sort_vals), plan->n_items, stream);
   if (e == cudaSuccess)
     e = radix_sort_pairs(st.depth_key, at<uint32_t>(pre_ws, L.sort_keys_alt), at<uint32_t>(pre_ws, L.sort_vals),
                          at<uint32_t>(pre_ws, L.sort_vals_alt), plan->n_items, 32,

@@ -217,10 +217,6 @@ __global__ void l1_kernel(const float* __restrict__ img, const float* __restrict
   }
 }
 
-__global__ void iota_kernel(uint32_t* __restrict__ out, int64_t n) {
-  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = (uint32_t)i;
-}
 
 }  // namespace
 
@@ -245,10 +241,6 @@ cudaError_t launch_ranges(const uint32_t* keys, int64_t n_entries, uint2* ranges
   return cudaGetLastError();
 }
 
-cudaError_t launch_iota(uint32_t* out, int64_t n, cudaStream_t stream) {
-  if (n > 0) GS_TIMED("iota", stream, (iota_kernel<<<ceil_div(n, 256), 256, 0, stream>>>(out, n)));
-  return cudaGetLastError();
-}
 
 cudaError_t launch_loss_l1(const float* image, const float* target, int64_t count, float* loss, float* dL,
                            cudaStream_t stream) {

@@ -43,6 +43,7 @@ struct ItemState {
   float4* bin;               // 2 x float4 per item: (k, sc, 1/Syy, h), (rx, ys, 0, 0); see BinParams
   uint32_t* tiles;           // exact touched-tile count (0 = culled)
   uint32_t* depth_key;       // float bits of z, kCulledKey if culled
+  uint32_t* depth_val;       // the item's own index: the depth sort's values
 };
 
 // Offsets of the preprocess workspace regions (bytes), host-computed.
@@ -174,7 +175,6 @@ cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int 
                               const uint32_t* vals, const ItemState& st, const gs_config& cfg,
                               const float* dL_dimage, const float* image, const uint32_t* n_contrib,
                               float4* grad2d, float* weight_sum, uint64_t* weight_sum_fixed, cudaStream_t stream);
-cudaError_t launch_iota(uint32_t* out, int64_t n, cudaStream_t stream);
 cudaError_t launch_loss_l1(const float* image, const float* target, int64_t count, float* loss, float* dL,
                            cudaStream_t stream);
 

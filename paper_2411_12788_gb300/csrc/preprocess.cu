@@ -54,6 +54,7 @@ __device__ __forceinline__ void stage_sh(const float* __restrict__ sh, int sh_co
 __device__ __forceinline__ void cull(const ItemState& st, int64_t item) {
   st.tiles[item] = 0u;
   st.depth_key[item] = kCulledKey;
+  st.depth_val[item] = (uint32_t)item;
 }
 
 template <int DEG, bool THREE_SIGMA>
@@ -178,6 +179,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
     const float kappa = lmax * lmax / det;
     P.st.tiles[item] = count;
     P.st.depth_key[item] = count ? __float_as_uint(pc.z) : kCulledKey;
+    P.st.depth_val[item] = (uint32_t)item;
     if (!count) continue;
     P.st.rect[item] = make_uint2((uint32_t)ty0 << 16, (uint32_t)(V.tiles_x - 1) | ((uint32_t)ty1 << 16));
     P.st.xy_tau_z[item] = make_float4(b.mx, b.my, b.tau, pc.z);
