@@ -372,15 +372,23 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
   return x - v + add;
 }
 
+// Block sums of the (gathered) counts; with idx the gathered counts are also
+// stored in `gathered` (the output array), so the final pass reads them in
+// order instead of gathering a second time.
 __global__ void __launch_bounds__(kScanThreads) scan_block_sums_kernel(const uint32_t* __restrict__ counts,
                                                                        const uint32_t* __restrict__ idx,
-                                                                       int64_t n, uint64_t* __restrict__ sums) {
+                                                                       int64_t n, uint64_t* __restrict__ sums,
+                                                                       uint32_t* __restrict__ gathered) {
   __shared__ uint32_t s_warp[kScanThreads / 32];
   int64_t base = (int64_t)blockIdx.x * kScanTile;
   uint32_t acc = 0;
   for (int k = 0; k < kScanItems; ++k) {
     int64_t i = base + k * kScanThreads + threadIdx.x;
-    if (i < n) acc += counts[idx ? idx[i] : i];
+    if (i < n) {
+      const uint32_t c = counts[idx ? idx[i] : i];
+      if (idx) gathered[i] = c;
+      acc += c;
+    }
   }
   uint32_t tot;
   block_exclusive_scan(acc, s_warp, &tot);
@@ -424,7 +432,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const uint32_t
 #pragma unroll
   for (int k = 0; k < kScanItems; ++k) {
     int64_t i = base + k;
-    c[k] = i < n ? counts[idx ? idx[i] : i] : 0u;
+    c[k] = i < n ? (idx ? out[i] : counts[i]) : 0u;     // with idx: the block-sum pass's gathered copy
     acc += c[k];
   }
   uint32_t tot;
@@ -501,7 +509,7 @@ cudaError_t gather_exclusive_scan(const uint32_t* counts, const uint32_t* idx, u
   if (n <= 0) return cudaMemsetAsync(total, 0, 8, stream);
   int nb = ceil_div(n, kScanTile);
   GS_TIMED("scan_block_sums", stream,
-           (scan_block_sums_kernel<<<nb, kScanThreads, 0, stream>>>(counts, idx, n, block_scratch)));
+           (scan_block_sums_kernel<<<nb, kScanThreads, 0, stream>>>(counts, idx, n, block_scratch, out)));
   GS_TIMED("scan_top", stream, (scan_top_kernel<<<1, 1024, 0, stream>>>(block_scratch, nb, total)));
   GS_TIMED("scan_final", stream,
            (scan_final_kernel<<<nb, kScanThreads, 0, stream>>>(counts, idx, n, block_scratch, out)));
