@@ -2,10 +2,10 @@
 // the depth order of the items (Sec. 3.1), then tile ranges of the list
 // sorted by tile id.  Also the L1 photometric loss of the training step.
 //
-// Duplication: one thread per item of the depth order walks the item's tile
-// rows with the same interval form of the support as the counting pass in
-// preprocess (identical arithmetic on the same stored parameters) and writes
-// its entries at its scanned offset, row-major.
+// Duplication: the entries of each item of the depth order, its tile rows
+// evaluated with the same interval form of the support as the counting pass
+// in preprocess (identical arithmetic on the same stored parameters), written
+// at its scanned offset, row-major.
 #include "project.cuh"
 
 namespace gs {
@@ -29,8 +29,11 @@ struct DupItem {
 // lane evaluates one row's tile interval (the same row_tiles the preprocess
 // counted with), a warp scan turns the row lengths into positions, and the
 // lanes then write the 32 rows' entries together (entry e of the iteration
-// is the e-th of one contiguous run, so the stores coalesce), each finding its
-// row by a 5-step search.
+// is the e-th of one contiguous run, so the stores coalesce).  A lane finds
+// the row of its entry (and the item of its row) without a search: the rows
+// with entries have distinct, increasing starts, so the row holding e is the
+// last one starting at or before e, counted with one ballot (starts before
+// the window of 32) and one OR-reduction (one bit per start inside it).
 // Every item's rows must add up to the count the preprocess stored; a
 // mismatch sets kStatusEntryMismatch and nothing is written out of range.
 __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* __restrict__ views, int64_t n_items,
@@ -46,6 +49,8 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* _
   __shared__ uint32_t s_item[kDupWarps][32];       // item of each row
   __shared__ uint32_t s_out0[kDupWarps][32];       // output position of each row's first entry
   __shared__ uint32_t s_lim[kDupWarps][32];        // entries the row may write (its item's remaining count)
+  __shared__ uint8_t s_nerow[kDupWarps][32];       // the lanes of the rows with entries, in order
+  __shared__ uint8_t s_neitem[kDupWarps][32];      // the lanes of the items with rows, in order
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t k = ((int64_t)blockIdx.x * kDupWarps + warp) * 32 + lane;
   if (((int64_t)blockIdx.x * kDupWarps + warp) * 32 >= n_items) return;     // warp-uniform
@@ -95,6 +100,9 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* _
   const uint32_t R = __shfl_sync(0xffffffffu, rs, 31);
   s_rstart[warp][lane] = rs - nrows;
   if (lane == 31) s_rstart[warp][32] = R;
+  const uint32_t rstart = rs - nrows;                     // this lane's item's first row unit
+  const uint32_t has_rows = __ballot_sync(0xffffffffu, nrows > 0);
+  if (nrows > 0) s_neitem[warp][__popc(has_rows & ((1u << lane) - 1u))] = (uint8_t)lane;
   __syncwarp();
 
   // 2. 32 rows at a time
@@ -105,15 +113,13 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* _
     const bool valid = u < R;
     int j = 32;                                           // owner item (lane index), 32 = none
     uint32_t c = 0, key0 = 0;
+    // the item owning row u: the last item with rows whose first row is at or
+    // before u (items before the window, plus one bit per start inside it)
+    const bool in_window = nrows > 0 && rstart >= u0 && rstart < u0 + 32;
+    const uint32_t M = __reduce_or_sync(0xffffffffu, in_window ? 1u << (rstart - u0) : 0u);
+    const uint32_t before = __popc(__ballot_sync(0xffffffffu, nrows > 0 && rstart < u0));
     if (valid) {
-      int lo = 0, hi = 32;                                // last j with rstart[j] <= u
-#pragma unroll
-      for (int step = 0; step < 5; ++step) {
-        const int mid = (lo + hi) >> 1;
-        if (s_rstart[warp][mid] <= u) lo = mid;
-        else hi = mid;
-      }
-      j = lo;
+      j = s_neitem[warp][before + __popc(M & ((2u << lane) - 1u)) - 1u];
       const DupItem& d = s_it[warp][j];
       const int ty = d.ty0 + (int)(u - s_rstart[warp][j]);
       int ta, tb;
@@ -154,22 +160,27 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* _
     s_lim[warp][lane] = icnt > in_item ? icnt - in_item : 0u;
     const int next_j = __shfl_sync(0xffffffffu, j, 31);
     const uint32_t next_carry = __shfl_sync(0xffffffffu, in_item + c, 31);
+    // the rows with entries, ranked: their starts are distinct and increasing
+    const uint32_t start = pre - c;
+    const uint32_t nonempty = __ballot_sync(0xffffffffu, c > 0);
+    if (c > 0) s_nerow[warp][__popc(nonempty & ((1u << lane) - 1u))] = (uint8_t)lane;
     __syncwarp();
-    for (uint32_t e = lane; e < T; e += 32) {
-      int lo = 0, hi = 32;                                // row of entry e
-#pragma unroll
-      for (int step = 0; step < 5; ++step) {
-        const int mid = (lo + hi) >> 1;
-        if (s_pre[warp][mid] <= e) lo = mid;
-        else hi = mid;
-      }
-      // rows with no entries share their successor's prefix; take the last
-      // row with pre <= e, which is the one holding entry e
-      const uint32_t d = e - s_pre[warp][lo];
-      if (d < s_lim[warp][lo]) {
-        const uint32_t at = s_out0[warp][lo] + d;
-        keys[at] = s_key0[warp][lo] + d;
-        vals[at] = s_item[warp][lo];
+    for (uint32_t e0 = 0; e0 < T; e0 += 32) {
+      // the row holding entry e = e0 + lane is the last row with entries that
+      // starts at or before e: those starting before e0, plus those starting
+      // in [e0, e] (one bit each in M)
+      const bool in_window = c > 0 && start >= e0 && start < e0 + 32;
+      const uint32_t M = __reduce_or_sync(0xffffffffu, in_window ? 1u << (start - e0) : 0u);
+      const uint32_t before = __popc(__ballot_sync(0xffffffffu, c > 0 && start < e0));
+      const uint32_t e = e0 + lane;
+      if (e < T) {
+        const int lo = s_nerow[warp][before + __popc(M & ((2u << lane) - 1u)) - 1u];
+        const uint32_t d = e - s_pre[warp][lo];
+        if (d < s_lim[warp][lo]) {
+          const uint32_t at = s_out0[warp][lo] + d;
+          keys[at] = s_key0[warp][lo] + d;
+          vals[at] = s_item[warp][lo];
+        }
       }
     }
     __syncwarp();
