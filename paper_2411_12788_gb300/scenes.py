@@ -68,6 +68,25 @@ class Scene:
                      self.rotations[idx].copy(), self.opacities[idx].copy(),
                      self.sh[idx].copy(), self.sh_degree, dict(self.meta))
 
+    def save(self, path) -> None:
+        """Writes the scene as flat arrays (numpy .npz): a checkpoint of the
+        Gaussians that `load` reads back exactly."""
+        np.savez(path, means=self.means, scales=self.scales, rotations=self.rotations,
+                 opacities=self.opacities, sh=self.sh, sh_degree=np.int64(self.sh_degree))
+
+
+def load(path) -> Scene:
+    """A scene written by Scene.save (or any .npz with the same arrays)."""
+    with np.load(path) as z:
+        return Scene(z["means"], z["scales"], z["rotations"], z["opacities"], z["sh"], int(z["sh_degree"]))
+
+
+def scene_from_tensors(g) -> Scene:
+    """The host copy of device Gaussians (raster.GaussianTensors), e.g. to save
+    a trained or pruned scene."""
+    f = lambda t: t.detach().cpu().numpy().astype(np.float32)
+    return Scene(f(g.means), f(g.scales), f(g.rotations), f(g.opacities), f(g.sh), int(g.sh_degree))
+
 
 def _unit_quaternions(rng: np.random.Generator, n: int) -> np.ndarray:
     q = rng.standard_normal((n, 4))

@@ -1,8 +1,8 @@
 """Host-side pieces of the server that need no GPU: the Poisson trace and
-the latency statistics."""
+the latency statistics; scene checkpoints."""
 import numpy as np
 
-from paper_2411_12788_gb300 import serve
+from paper_2411_12788_gb300 import scenes, serve
 
 
 def test_poisson_trace_rate_and_sizes():
@@ -23,3 +23,15 @@ def test_latency_stats():
     st = serve.latency_stats(tr, skip=0)
     assert abs(st["p50_ms"] - 1.0) < 1e-6
     assert st["max_ms"] > 49.9 and st["requests"] == 200
+
+
+def test_scene_save_load_round_trip(tmp_path):
+    """A scene written with Scene.save reads back bit-identical."""
+    sc = scenes.cluster_scene(500, 8, seed=2, sh_degree=3)
+    path = tmp_path / "scene.npz"
+    sc.save(path)
+    back = scenes.load(path)
+    assert back.sh_degree == sc.sh_degree
+    for k in ("means", "scales", "rotations", "opacities", "sh"):
+        a, b = getattr(sc, k), getattr(back, k)
+        assert a.dtype == b.dtype and np.array_equal(a, b), k
