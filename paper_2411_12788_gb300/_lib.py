@@ -10,7 +10,9 @@ import ctypes as C
 import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(HERE, "libgs.so")
+# GS_CHECKED=1 selects the checked build (index checks that report instead of
+# faulting; build.build(checked=True))
+LIB_PATH = os.path.join(HERE, "libgs_checked.so" if os.environ.get("GS_CHECKED") == "1" else "libgs.so")
 
 GS_TILE = 16
 GS_MAX_VIEWS = 64

@@ -3,6 +3,13 @@
 Each CUDA translation unit is compiled in parallel into _build/, then linked
 into paper_2411_12788_gb300/libgs.so (in-tree, next to this file).  The
 library exports the C ABI declared in include/gs.h.
+
+build(checked=True) makes libgs_checked.so instead (objects in
+_build_checked/): the same code with GS_CHECKED defined, where every
+computed index into an entry, item or output array is checked first and an
+out-of-range one sets a bit in the device status word (gs_device_status then
+returns GS_ERR_DEVICE_CHECK) and is skipped; the binding loads it when the
+environment variable GS_CHECKED is 1.
 """
 from __future__ import annotations
 
@@ -17,6 +24,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgs.so")
+BUILD_CHECKED = os.path.join(HERE, "_build_checked")
+LIB_CHECKED = os.path.join(HERE, "libgs_checked.so")
 SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "binning.cu", "render.cu", "timing.cu", "noalloc.cu", "select.cu", "ssim.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
@@ -37,16 +46,18 @@ def _stale(obj: str, deps: list[str]) -> bool:
     return any(os.path.getmtime(d) > t for d in deps)
 
 
-def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = False) -> str:
-    os.makedirs(BUILD, exist_ok=True)
+def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = False, checked: bool = False) -> str:
+    build_dir, lib = (BUILD_CHECKED, LIB_CHECKED) if checked else (BUILD, LIB)
+    extra = ["-DGS_CHECKED"] if checked else []
+    os.makedirs(build_dir, exist_ok=True)
     headers = [os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "gs.h"))
     jobs = []
     for src in SOURCES:
         s = os.path.join(CSRC, src)
-        o = os.path.join(BUILD, src.replace(".cu", ".o"))
+        o = os.path.join(build_dir, src.replace(".cu", ".o"))
         if force or _stale(o, [s] + headers):
-            cmd = [nvcc(), *ARCH, *FLAGS, "-c", s, "-o", o]
+            cmd = [nvcc(), *ARCH, *FLAGS, *extra, "-c", s, "-o", o]
             if ptxas_verbose:
                 cmd.insert(1, "-Xptxas=-v")
             jobs.append(cmd)
@@ -54,7 +65,7 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
     def run(cmd):
         r = subprocess.run(cmd, capture_output=True, text=True)
         return cmd, r
-    objs = [os.path.join(BUILD, s.replace(".cu", ".o")) for s in SOURCES]
+    objs = [os.path.join(build_dir, s.replace(".cu", ".o")) for s in SOURCES]
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:
             for cmd, r in ex.map(run, jobs):
@@ -62,14 +73,15 @@ def build(verbose: bool = False, force: bool = False, ptxas_verbose: bool = Fals
                     sys.stderr.write(r.stdout + r.stderr)
                 if r.returncode != 0:
                     raise RuntimeError("nvcc failed: " + " ".join(cmd))
-    if force or jobs or _stale(LIB, objs):
-        cmd = [nvcc(), *ARCH, "-shared", "-o", LIB, *objs]
+    if force or jobs or _stale(lib, objs):
+        cmd = [nvcc(), *ARCH, "-shared", "-o", lib, *objs]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             sys.stderr.write(r.stdout + r.stderr)
             raise RuntimeError("link failed: " + " ".join(cmd))
-    return LIB
+    return lib
 
 
 if __name__ == "__main__":
-    print(build(verbose=True, force="--force" in sys.argv, ptxas_verbose="-v" in sys.argv))
+    print(build(verbose=True, force="--force" in sys.argv, ptxas_verbose="-v" in sys.argv,
+                checked="--checked" in sys.argv))

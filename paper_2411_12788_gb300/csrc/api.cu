@@ -141,6 +141,8 @@ ItemState item_state(void* ws, const PreLayout& L) {
   s.tiles = at<uint32_t>(ws, L.tiles);
   s.depth_key = at<uint32_t>(ws, L.depth_key);
   s.depth_val = at<uint32_t>(ws, L.sort_vals);
+  s.status = at<uint32_t>(ws, L.status);
+  s.n_entries = at<unsigned long long>(ws, L.n_entries);
   return s;
 }
 
@@ -412,7 +414,7 @@ gs_status gs_device_status(const gs_plan* plan, void* pre_ws, void* stream_) {
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
   if (word & kStatusTimeout) return GS_ERR_TIMEOUT;
-  if (word & kStatusEntryMismatch) return GS_ERR_DEVICE_CHECK;
+  if (word & (kStatusEntryMismatch | kStatusBounds)) return GS_ERR_DEVICE_CHECK;
   return GS_OK;
 }
 

@@ -67,7 +67,9 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* _
     d.tile_base = 0;
     if (k < n_items) {
       d.item = sorted_items[k];
-      d.cnt = st.tiles[d.item];
+      const bool known = GS_IN_RANGE(d.item, n_items, status);
+      if (!known) d.item = 0;
+      d.cnt = known ? st.tiles[d.item] : 0u;
       if (d.cnt) {
         d.off = offsets[k];
         const float4 a = st.xy_tau_z[d.item];
@@ -178,8 +180,10 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* _
         const uint32_t d = e - s_pre[warp][lo];
         if (d < s_lim[warp][lo]) {
           const uint32_t at = s_out0[warp][lo] + d;
-          keys[at] = s_key0[warp][lo] + d;
-          vals[at] = s_item[warp][lo];
+          if (GS_IN_RANGE(at, *st.n_entries, status)) {
+            keys[at] = s_key0[warp][lo] + d;
+            vals[at] = s_item[warp][lo];
+          }
         }
       }
     }

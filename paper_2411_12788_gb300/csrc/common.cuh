@@ -19,6 +19,17 @@ constexpr uint32_t kCulledKey = 0xFFFFFFFFu;   // depth key of a culled item
 // Device status word bits (preprocess workspace).
 constexpr uint32_t kStatusTimeout = 1u;        // a look-back spin ran out
 constexpr uint32_t kStatusEntryMismatch = 2u;  // duplicate != counted tiles
+constexpr uint32_t kStatusBounds = 4u;         // checked build: an index out of its array
+
+// Index check of the checked build (GS_CHECKED): true when 0 <= i < n;
+// otherwise it records kStatusBounds in *status and is false, so that the
+// caller skips the access.  Without GS_CHECKED it is always true.
+#ifdef GS_CHECKED
+#define GS_IN_RANGE(i, n, status) \
+  ((uint64_t)(i) < (uint64_t)(n) ? true : (atomicOr((status), ::gs::kStatusBounds), false))
+#else
+#define GS_IN_RANGE(i, n, status) true
+#endif
 
 // Per-view constants, uploaded into the preprocess workspace.
 struct ViewDev {
@@ -44,6 +55,8 @@ struct ItemState {
   uint32_t* tiles;           // exact touched-tile count (0 = culled)
   uint32_t* depth_key;       // float bits of z, kCulledKey if culled
   uint32_t* depth_val;       // the item's own index: the depth sort's values
+  uint32_t* status;          // device status word (kStatus* bits)
+  const unsigned long long* n_entries;   // tile entries, written by the scan
 };
 
 // Offsets of the preprocess workspace regions (bytes), host-computed.

@@ -52,7 +52,18 @@ struct RenderParams {
   const float4* depth_frame;
   float alpha_max, e_min, t_min;   // e_min = log2(alpha_min)
   float bg[3];
+  uint32_t* status;             // device status word (the checked build's index checks)
+  const unsigned long long* n_entries;
 };
+
+// The item of list position idx, with the checked build's checks: a position
+// past the entries or an item past the items records kStatusBounds and reads
+// as item 0 (the results are then wrong, but no access leaves its array).
+__device__ __forceinline__ uint32_t list_item(const RenderParams& P, uint64_t idx) {
+  uint32_t item = GS_IN_RANGE(idx, *P.n_entries, P.status) ? P.vals[idx] : 0u;
+  if (!GS_IN_RANGE(item, (uint64_t)P.n * (uint64_t)P.n_views, P.status)) item = 0u;
+  return item;
+}
 
 struct FwdOut {
   float* image;
@@ -342,7 +353,7 @@ __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P,
       const int k = tid + h * kFwdThreads;
       const uint32_t idx = bstart + k;
       if (idx < range.y) {
-        const uint32_t item = P.vals[idx];
+        const uint32_t item = list_item(P, idx);
         s_item[k] = item;
         const float4 a = P.xy_tau_z[item];
         s_xy[k] = make_float2(a.x, a.y);
@@ -373,8 +384,8 @@ __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P,
     }
   }
 
-  const int64_t item0 = q0.imax_pos >= 0 ? (int64_t)P.vals[range.x + q0.imax_pos] : -1;
-  const int64_t item1 = q1.imax_pos >= 0 ? (int64_t)P.vals[range.x + q1.imax_pos] : -1;
+  const int64_t item0 = q0.imax_pos >= 0 ? (int64_t)list_item(P, (uint64_t)range.x + q0.imax_pos) : -1;
+  const int64_t item1 = q1.imax_pos >= 0 ? (int64_t)list_item(P, (uint64_t)range.x + q1.imax_pos) : -1;
   if (O.max_area) {
     add_max_area(O.max_area, in0 && item0 >= 0, item0, lane);
     add_max_area(O.max_area, in1 && item1 >= 0, item1, lane);
@@ -539,7 +550,7 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
   for (uint32_t bstart = 0; bstart < max_nc; bstart += kRenderThreads) {
     const int nb = (int)min(max_nc - bstart, (uint32_t)kRenderThreads);
     if (tid < nb) {
-      const uint32_t item = P.vals[range.x + bstart + tid];
+      const uint32_t item = list_item(P, (uint64_t)range.x + bstart + tid);
       s_item[tid] = item;
       const float4 a = P.xy_tau_z[item];
       s_xy[tid] = make_float2(a.x, a.y);
@@ -664,6 +675,8 @@ RenderParams make_params(const ViewDev* views, int n_views, int64_t n, const uin
   P.conic_o = st.conic_o;
   P.rgb = st.rgb;
   P.depth_frame = st.depth_frame;
+  P.status = st.status;
+  P.n_entries = st.n_entries;
   P.alpha_max = cfg.alpha_max;
   P.e_min = (float)log2((double)cfg.alpha_min);
   P.t_min = cfg.t_min;

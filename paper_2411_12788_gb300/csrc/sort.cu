@@ -325,8 +325,10 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
     if (i < count) {
       const uint32_t d = (key[k] >> shift) & (kRadix - 1);
       const uint32_t pos = s_cta_start[d] + s_warp_hist[warp][d] + rank[k];
-      s_keys[pos] = key[k];
-      s_vals[pos] = s_vin[i];
+      if (GS_IN_RANGE(pos, count, status)) {
+        s_keys[pos] = key[k];
+        s_vals[pos] = s_vin[i];
+      }
     }
   }
 
@@ -346,8 +348,10 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
     const uint32_t k = s_keys[i];
     const uint32_t d = (k >> shift) & (kRadix - 1);
     const uint32_t out = s_out_base[d] + (uint32_t)i;
-    keys_out[out] = k;
-    vals_out[out] = s_vals[i];
+    if (GS_IN_RANGE(out, n, status)) {
+      keys_out[out] = k;
+      vals_out[out] = s_vals[i];
+    }
   }
 }
 
