@@ -275,8 +275,9 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
   HostHead* head = nullptr;
   cudaError_t e = host_head(&head);
   if (e != cudaSuccess) return GS_ERR_CUDA;
-  set_views_kernel<<<1, GS_MAX_VIEWS, 0, stream>>>(table, plan->n_views, at<ViewDev>(pre_ws, L.views),
-                                                    at<uint32_t>(pre_ws, L.status));
+  GS_TIMED("preprocess_views", stream,
+           (set_views_kernel<<<1, GS_MAX_VIEWS, 0, stream>>>(table, plan->n_views, at<ViewDev>(pre_ws, L.views),
+                                                              at<uint32_t>(pre_ws, L.status))));
   e = cudaGetLastError();
   if (e != cudaSuccess) return GS_ERR_CUDA;
   if (plan->n_items == 0) {
@@ -295,7 +296,8 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
                               plan->n_items, at<uint64_t>(pre_ws, L.scan_blocks),
                               at<unsigned long long>(pre_ws, L.n_entries), stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
-  copy_head_kernel<<<1, 32, 0, stream>>>(at<uint64_t>(pre_ws, L.status), head->dev);
+  GS_TIMED("preprocess_readback", stream,
+           (copy_head_kernel<<<1, 32, 0, stream>>>(at<uint64_t>(pre_ws, L.status), head->dev)));
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
