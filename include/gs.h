@@ -26,8 +26,10 @@
  *    per-view constants are likewise passed to a kernel by value.
  *  - Every call returns a gs_status; arguments are validated on the host
  *    before any launch (GS_ERR_INVALID_ARG).  Device-side checks (entry
- *    overflow, a radix-sort look-back that exceeded its spin budget) set a
- *    status word in the preprocess workspace that gs_device_status() reads.
+ *    overflow, a radix-sort look-back that exceeded its spin budget, and in
+ *    the checked build, libgs_checked.so compiled with GS_CHECKED, any
+ *    out-of-range index into an entry, item or output array) set a status
+ *    word in the preprocess workspace that gs_device_status() reads.
  *  - Floating point is FP32 throughout.  Gaussian attributes are the
  *    activated values: linear scales, a (w,x,y,z) quaternion that need not be
  *    unit (it is normalised inside), opacity in (0,1), raw SH coefficients.
@@ -198,7 +200,8 @@ size_t gs_bin_sort_workspace_size(const gs_plan* plan);
  * lowpass I, conic, projected centre, SH colour max(0, sum sh Y + 0.5) in
  * the direction from the camera centre (Sec. 3.1), the midpoint-depth frame
  * (Sec. 4.1), and the exact number of touched tiles: tile T is touched iff
- * min over its pixel-centre rectangle of d^T conic d <= 2 ln(o / alpha_min).
+ * min over its pixel-centre rectangle of d^T conic d <= 2 ln(o / alpha_min)
+ * (with GS_FLAG_EXTENT_3SIGMA: iff that rectangle meets the 3-sigma square).
  * Then sorts the items by the float32 depth of their centres (stable, ties
  * by item) and scans the tile counts in that order; stores the total in
  * plan->n_entries (one read-back through mapped host memory, synchronises
