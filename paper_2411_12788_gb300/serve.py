@@ -46,6 +46,9 @@ class Request:
     done: float | None = None   # seconds after the trace start (device time)
     batch: int = -1
     image: torch.Tensor | None = None
+    # set by the caller at any time before the request is admitted: the
+    # server then drops it (done stays None, batch -1)
+    cancelled: bool = False
 
     @property
     def pixels(self) -> int:
@@ -193,6 +196,9 @@ class RenderServer:
             while queue and free_slots:
                 take, need = [], 0
                 while queue and len(take) < self.max_views:
+                    if queue[0].cancelled:
+                        queue.pop(0)
+                        continue
                     est = self._estimate(queue[0].cam)
                     if take and self.reserved + need + est > self.budget:
                         break
@@ -227,9 +233,12 @@ def poisson_trace(n: int, rate: float, seed: int = 3, sizes=None) -> list:
 
 
 def latency_stats(reqs: list, skip: int = 0) -> dict:
-    lat = np.array([r.done - r.arrival for r in reqs[skip:]]) * 1e3
-    span = max(r.done for r in reqs[skip:]) - min(r.arrival for r in reqs[skip:])
-    pix = sum(r.pixels for r in reqs[skip:])
+    """Latency percentiles and throughput of the served requests after the
+    first `skip` (cancelled requests, which have no completion, are left out)."""
+    reqs = [r for r in reqs[skip:] if r.done is not None]
+    lat = np.array([r.done - r.arrival for r in reqs]) * 1e3
+    span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
+    pix = sum(r.pixels for r in reqs)
     return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
             "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "requests": len(lat),
             "mpix_per_s": pix / span / 1e6}

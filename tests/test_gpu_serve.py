@@ -79,3 +79,25 @@ def test_allocation_failure_propagates_and_server_recovers():
     trace = serve.poisson_trace(8, rate=5000.0, seed=12, sizes=SIZES)
     srv.serve(trace)
     assert all(r.done is not None for r in trace)
+
+
+def test_cancelled_requests_are_dropped():
+    """Requests cancelled before admission (host-side fault injection of a
+    client that gives up) are never rendered and leave no completion; the
+    rest of the trace is served and the statistics count only them."""
+    _need_gpu()
+    sc = scenes.cluster_scene(50_000, 64, seed=13, sh_degree=0)
+    g = raster.GaussianTensors.from_scene(sc)
+    trace = serve.poisson_trace(15, rate=3000.0, seed=14, sizes=SIZES)
+    for r in trace[::3]:
+        r.cancelled = True
+    srv = serve.RenderServer(g, budget_bytes=1 << 30, streams=2, max_views=4)
+    srv.serve(trace)
+    for r in trace:
+        if r.cancelled:
+            assert r.done is None and r.batch == -1
+        else:
+            assert r.done is not None and r.done >= r.arrival
+    assert srv.views_run == len(trace) - len(trace[::3])
+    assert serve.latency_stats(trace)["requests"] == len(trace) - len(trace[::3])
+

@@ -35,3 +35,16 @@ def test_scene_save_load_round_trip(tmp_path):
     for k in ("means", "scales", "rotations", "opacities", "sh"):
         a, b = getattr(sc, k), getattr(back, k)
         assert a.dtype == b.dtype and np.array_equal(a, b), k
+
+
+def test_latency_stats_leave_out_cancelled_requests():
+    tr = serve.poisson_trace(10, rate=100.0, seed=4)
+    for k, r in enumerate(tr):
+        if k % 2:
+            r.cancelled = True
+        else:
+            r.done = r.arrival + 0.001 * (k + 1)
+    st = serve.latency_stats(tr)
+    assert st["requests"] == 5
+    assert abs(st["max_ms"] - 9.0) < 1e-9
+
