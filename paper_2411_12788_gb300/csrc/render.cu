@@ -583,18 +583,26 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
       const uint32_t posa = bstart + ia, posb = bstart + ib;   // list positions
       // pixels of this warp still blending at the chunk's first entry
       const uint32_t pmask = __ballot_sync(0xffffffffu, my_nc > bstart + s_list[warp][c]);
+      // the block's 4 rows, 8 pixels each: the row part of each entry's
+      // exponent is computed once per row
+#pragma unroll 1
+      for (int r = 0; r < 4; ++r) {
+      if (!((pmask >> (8 * r)) & 0xffu)) continue;
+      // pixel centre minus entry centre, rounded exactly as in the forward
+      const float fy = byf + (float)r;
+      const float dya = fy - A.my, dyb = fy - Bn.my;
+      const float2 rowa = expo_row(A.ex, dya), rowb = expo_row(Bn.ex, dyb);
 #pragma unroll 4
-      for (int p = 0; p < 32; ++p) {
+      for (int cx = 0; cx < 8; ++cx) {
+        const int p = 8 * r + cx;
         if (!(pmask & (1u << p))) continue;
         const int pt = warp * 32 + p;                 // the pixel's thread id
         const float4 st = s_st[pt];
         const uint32_t nc = __float_as_uint(st.z);
-        // pixel centre minus entry centre, rounded exactly as in the forward
-        const float fx = bxf + (float)(p & 7), fy = byf + (float)(p >> 3);
-        const float dxa = fx - A.mx, dya = fy - A.my;
-        const float dxb = fx - Bn.mx, dyb = fy - Bn.my;
-        const float ea = expo(A.ex, dxa, dya);
-        const float eb = expo(Bn.ex, dxb, dyb);
+        const float fx = bxf + (float)cx;
+        const float dxa = fx - A.mx, dxb = fx - Bn.mx;
+        const float ea = expo_pix(A.ex, rowa, dxa);
+        const float eb = expo_pix(Bn.ex, rowb, dxb);
         const bool acta = posa < nc && ea >= P.e_min;
         const bool actb = posb < nc && eb >= P.e_min;
         if (!__any_sync(0xffffffffu, acta || actb)) continue;
@@ -629,6 +637,7 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
         }
         if (acta) bwd_entry_accumulate<kFix>(A, pg, dxa, dya, aa, arawa, Ta, Fa, cga, P.alpha_max);
         if (actb) bwd_entry_accumulate<kFix>(Bn, pg, dxb, dyb, ab, arawb, Tb, Fb, cgb, P.alpha_max);
+      }
       }
       if (va) bwd_entry_flush<kFix>(A, s_g, s_wsum, s_wfix, ia, want_w);
       if (vb) bwd_entry_flush<kFix>(Bn, s_g, s_wsum, s_wfix, ib, want_w);
