@@ -191,8 +191,8 @@ def kernel_times(collect=True) -> dict:
 # valid while the kernel's source file is the one profiled (its SHA-256) and the workload has the same number
 # of tile entries; otherwise the traffic is reported as null.
 PROFILED_TRAFFIC = {
-    "render_bwd": {"bytes": 589.96e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
-                   "sha256": "0359acfda21a4b2c6950a72443652edcf327043b8be7b56aace1deb8a88ac188",
+    "render_bwd": {"bytes": 590.12e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
+                   "sha256": "97634706ad11eba134b870f8a609f589e4c66070f20da2f1c349139e8ef3b9ed",
                    "profile": "profiles/render_bwd_1M_8views.md"},
 }
 
