@@ -472,7 +472,10 @@ int gs_timing_collect(gs_kernel_time* out, int max_out);
 /* ---- status ------------------------------------------------------------ */
 
 /* Reads (and clears) the device status word of a preprocess workspace;
- * synchronises `stream`.  Returns GS_OK, GS_ERR_TIMEOUT or GS_ERR_DEVICE_CHECK. */
+ * synchronises `stream`.  Returns GS_OK, GS_ERR_TIMEOUT or GS_ERR_DEVICE_CHECK.
+ * gs_preprocess also clears the word when it starts (and itself returns
+ * GS_ERR_TIMEOUT for its own depth sort), so a frame's bin, render and
+ * backward checks are read before the next gs_preprocess on the workspace. */
 gs_status gs_device_status(const gs_plan* plan, void* pre_ws, void* stream);
 
 const char* gs_status_string(gs_status s);
