@@ -258,8 +258,8 @@ struct PreBwdParams {
 constexpr int kPreBwdThreads = 64;
 
 // One thread per Gaussian; its SH row and the row's gradient live in shared
-// memory (per-thread rows, odd stride) rather than in registers, which keeps
-// the kernel near 90 registers and several blocks per SM.
+// memory (per-thread rows, odd stride) rather than in registers: at degree 3
+// the kernel takes 128 registers and 25 KB of shared memory, 8 blocks per SM.
 template <int DEG>
 __global__ void __launch_bounds__(kPreBwdThreads) preprocess_backward_kernel(PreBwdParams P) {
   constexpr int K = (DEG + 1) * (DEG + 1);
@@ -274,7 +274,6 @@ __global__ void __launch_bounds__(kPreBwdThreads) preprocess_backward_kernel(Pre
   const bool live = i < P.n;
   const float* shc = s_sh + threadIdx.x * row;      // coefficient k, channel c at [3k + c]
   float* dsh = s_dsh + threadIdx.x * row;
-  bool any = false;
   float dp[3] = {0.f, 0.f, 0.f};
   float dSig[6] = {0, 0, 0, 0, 0, 0};       // symmetric dL/dSigma (00,01,02,11,12,22)
   float dop = 0.f, m2abs = 0.f;
@@ -306,12 +305,43 @@ __global__ void __launch_bounds__(kPreBwdThreads) preprocess_backward_kernel(Pre
   sig[4] = M[3] * M[6] + M[4] * M[7] + M[5] * M[8];
   sig[5] = M[6] * M[6] + M[7] * M[7] + M[8] * M[8];
 
-  for (int v = 0; v < P.n_views && live; ++v) {
-    const int64_t item = (int64_t)v * P.n + i;
-    if (P.tiles[item] == 0) continue;
-    any = true;
+  // The views in which this Gaussian has tiles, their counts loaded together;
+  // the warp walks the union of its lanes' views in order (the view constants
+  // stay warp-uniform), each lane's 2-D gradients loaded one view ahead.
+  uint64_t vis = 0;
+  if (live) {
+#pragma unroll 8
+    for (int v = 0; v < P.n_views; ++v) vis |= (uint64_t)(P.tiles[(int64_t)v * P.n + i] != 0u) << v;
+  }
+  uint64_t wvis = ((uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)(vis >> 32)) << 32) |
+                  (uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)vis);
+  const bool any = vis != 0;
+  float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, n2 = n0;
+  if (wvis) {
+    const int v0 = __ffsll((long long)wvis) - 1;
+    if ((vis >> v0) & 1u) {
+      const int64_t item = (int64_t)v0 * P.n + i;
+      n0 = P.grad2d[3 * item];
+      n1 = P.grad2d[3 * item + 1];
+      n2 = P.grad2d[3 * item + 2];
+    }
+  }
+  while (wvis) {
+    const int v = __ffsll((long long)wvis) - 1;
+    wvis &= wvis - 1;
+    const bool mine = (vis >> v) & 1u;
+    const float4 g0 = n0, g1 = n1, g2 = n2;
+    if (wvis) {
+      const int vn = __ffsll((long long)wvis) - 1;
+      if ((vis >> vn) & 1u) {
+        const int64_t item = (int64_t)vn * P.n + i;
+        n0 = P.grad2d[3 * item];
+        n1 = P.grad2d[3 * item + 1];
+        n2 = P.grad2d[3 * item + 2];
+      }
+    }
+    if (!mine) continue;
     const ViewDev& V = P.views[v];
-    const float4 g0 = P.grad2d[3 * item], g1 = P.grad2d[3 * item + 1], g2 = P.grad2d[3 * item + 2];
     // the render backward differentiates the exponent form
     // e = log2 o - log2(e) (A dx^2 / 2 + B dx dy + C dy^2 / 2): convert to (A, B, C, o)
     const float dmx = g0.x, dmy = g0.y;
