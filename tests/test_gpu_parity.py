@@ -546,6 +546,35 @@ def test_backward_overwrite_mode_equals_accumulate_into_zeros(deg):
     assert (nan["d_sh"][:, K:] == 0).all() and (ones["d_sh"][:, K:] == 1).all()
 
 
+def test_backward_over_many_views_is_the_sum_of_single_view_passes():
+    """40 ragged views in one batch, more than a warp has lanes: each view's
+    image equals the view rendered alone, and the batched gradients
+    (d_mean2d_abs included) equal the sum over the views of the single-view
+    backward passes, which the tests above pin to the oracle."""
+    _need_gpu()
+    sc = scenes.cluster_scene(4000, 16, seed=23, sh_degree=3)
+    cams = [scenes.ring_camera(2 * math.pi * v / 40, 40 + 7 * (v % 3), 30 + 3 * (v % 5)) for v in range(40)]
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, cams)
+    gen = torch.Generator(device="cuda").manual_seed(5)
+    dL = torch.randn(fr.outs["image"].shape, generator=gen, device="cuda")
+    batched = raster.backward(g, fr, dL)
+    total = raster.alloc_grads(g)
+    for v, cam in enumerate(cams):
+        one = raster.forward(g, [cam])
+        off, h, w = raster.view_slice(fr.plan, v)
+        assert torch.equal(one.outs["image"], fr.outs["image"][3 * off: 3 * (off + h * w)]), v
+        for k, t in raster.backward(g, one, dL[3 * off: 3 * (off + h * w)]).items():
+            total[k] += t
+    torch.cuda.synchronize()
+    late = fr.outs["image"][3 * int(fr.plan.pixel_base[32]):]
+    assert late.abs().max().item() > 0.1          # the views past the first 32 see the scene
+    # the per-item 2-D gradients are summed with float atomics: equal up to rounding
+    for k in total:
+        tol = 1e-5 * (1e-3 + total[k].abs().max().item())
+        assert torch.allclose(batched[k], total[k], rtol=1e-4, atol=tol), k
+
+
 # ---------------------------------------------------------------- failure detection
 def test_bounded_wait_reports_timeout_and_context_survives():
     """A look-back wait whose predecessor never publishes gives up after its
