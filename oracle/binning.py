@@ -1,9 +1,9 @@
 """Step B of the oracle: tile lists, their depth order and tile ranges (test infrastructure).
 
-The paper's rasterizer (Sec. 3.1, and the 3DGS frustum culling recalled in
-Sec. 5.2 that "preserves Gaussians associated with touched tiles") splits the
-image into 16x16 tiles and gives every tile the depth-ordered list of the
-Gaussians that touch it.  The reading adopted here:
+The paper's rasterizer (Sec. 3.1; Sec. 5.2 recalls that the 3DGS
+preprocessing culls every Gaussian that reaches no tile) splits the image into
+16x16 tiles and gives every tile the depth-ordered list of the Gaussians that
+touch it.  The reading adopted here:
 
   * Gaussian i touches pixel x iff o_i G_i(x) >= alpha_min, i.e.
     q(x) = d^T conic d <= tau_i = 2 ln(o_i / alpha_min), d = x - mean2d;

@@ -8,9 +8,9 @@ check and the benchmark's CPU-baseline leg use it.
                               the number of pixels whose i_max is i.
   intersected(S)              G^int = {i : i is the i_max of some pixel}
                               (intersection preserving, Sec. 4.3), S_i > 0.
-  keep_quantile(values, q)    The paper sets thresholds "via the quantile
-                              function" with a keep quantile of 0.99
-                              (Sec. 5.1, 5.2) without defining it further.
+  keep_quantile(values, q)    Sec. 5.1 and 5.2 derive their thresholds
+                              from a quantile of the values with a keep
+                              quantile of 0.99, and define it no further.
                               Reading: of the M positive values, keep the
                               ceil(q M) largest, ties towards the lower index
                               (the rule of the importance pruning); q is the
