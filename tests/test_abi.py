@@ -120,3 +120,33 @@ def test_host_side_argument_checks(L):
     assert L.gs_bin_sort(C.byref(plan), fake, fake, 1 << 30, None) == 1
     assert L.gs_loss_l1(None, fake, 10, fake, fake, None) == 1
     assert L.gs_status_string(2) == b"workspace too small"
+
+
+def _paper_constants():
+    out = {}
+    for line in open(os.path.join(ROOT, "tests", "golden", "paper_constants.txt")):
+        line = line.split("#", 1)[0].strip()
+        if line:
+            name, value = line.split()[:2]
+            out[name] = float(value)
+    return out
+
+
+def test_identify_defaults_are_the_papers_constants(L):
+    """The identification defaults of the library and of the oracle are the
+    values the paper prints (Sec. 4.1 theta_blur, Sec. 5.1 and 5.2 keep
+    quantiles; tests/golden/paper_constants.txt)."""
+    import inspect
+
+    import numpy as np
+
+    from oracle import identify as OI
+    from paper_2411_12788_gb300 import _lib
+    paper = _paper_constants()
+    assert set(paper) == {"theta_blur", "keep_critical", "keep_visible"}
+    cfg = _lib.ConfigIdentify()
+    L.gs_config_identify_default(C.byref(cfg))
+    for name in paper:
+        assert getattr(cfg, name) == np.float32(paper[name]), name
+    assert inspect.signature(OI.blur_split).parameters["theta"].default == paper["theta_blur"]
+    assert inspect.signature(OI.visible).parameters["q"].default == paper["keep_visible"]
