@@ -38,16 +38,38 @@ struct PreParams {
   ItemState st;
 };
 
-// Stage the first K coefficients (3 floats each) of this block's SH rows into
-// shared memory with row stride 3K+1 (odd: conflict-free per-thread reads).
+// A thread's SH row in shared memory: the first K coefficients (3 floats
+// each) in an odd number of float4, so the row is read and written with
+// 128-bit accesses and the 8 lanes of each quarter-warp phase of such an
+// access fall on distinct banks.
+template <int K>
+__host__ __device__ constexpr int sh_row_floats() { return 4 * (((3 * K + 3) / 4) | 1); }
+
+// Stage this block's SH rows into shared memory (row stride sh_row_floats).
 template <int K, int THREADS>
 __device__ __forceinline__ void stage_sh(const float* __restrict__ sh, int sh_coeffs, int64_t i0, int64_t n,
                                          float* s_sh) {
-  constexpr int per = 3 * K, row = 3 * K + 1;
+  constexpr int per = 3 * K, row = sh_row_floats<K>();
   const int64_t rows = (n - i0 < THREADS) ? (n - i0) : (int64_t)THREADS;
   for (int f = threadIdx.x; f < rows * per; f += THREADS) {
     const int g = f / per, c = f - g * per;
     s_sh[g * row + c] = sh[(i0 + g) * (int64_t)sh_coeffs * 3 + c];
+  }
+}
+
+// acc[c] += sum_k Y_k sh[k][c] over a shared row (entry e = 3k + c), read a
+// float4 at a time.
+template <int K>
+__device__ __forceinline__ void sh_dot_rows(const float* row, const float* Y, float* acc) {
+#pragma unroll
+  for (int j = 0; j < (3 * K + 3) / 4; ++j) {
+    const float4 q = reinterpret_cast<const float4*>(row)[j];
+    const float qv[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+    for (int t = 0; t < 4; ++t) {
+      const int e = 4 * j + t;
+      if (e < 3 * K) acc[e % 3] += Y[e / 3] * qv[t];
+    }
   }
 }
 
@@ -60,8 +82,8 @@ __device__ __forceinline__ void cull(const ItemState& st, int64_t item) {
 template <int DEG, bool THREE_SIGMA>
 __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  constexpr int row = 3 * K + 1;
-  __shared__ float s_sh[kPreThreads * row];
+  constexpr int row = sh_row_floats<K>();
+  __shared__ __align__(16) float s_sh[kPreThreads * row];
   const int64_t i0 = (int64_t)blockIdx.x * kPreThreads;
   const int64_t i = i0 + threadIdx.x;
   stage_sh<K, kPreThreads>(P.sh, P.sh_coeffs, i0, P.n, s_sh);
@@ -195,14 +217,9 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
     dz *= il;
     float Y[16];
     sh_eval(DEG, dx, dy, dz, Y);
-    float r = 0.5f, g = 0.5f, bl = 0.5f;
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      r += Y[k] * shc[3 * k];
-      g += Y[k] * shc[3 * k + 1];
-      bl += Y[k] * shc[3 * k + 2];
-    }
-    P.st.rgb[item] = make_float4(fmaxf(r, 0.f), fmaxf(g, 0.f), fmaxf(bl, 0.f), 
+    float raw[3] = {0.5f, 0.5f, 0.5f};
+    sh_dot_rows<K>(shc, Y, raw);
+    P.st.rgb[item] = make_float4(fmaxf(raw[0], 0.f), fmaxf(raw[1], 0.f), fmaxf(raw[2], 0.f), 
                                  pack_extent(support_extent(rx_sup, cxx, kappa), support_extent(h_sup, cyy, kappa)));
 
     // midpoint-depth frame: W = diag(1/s) (R Rq)^T maps camera offsets to the
@@ -258,14 +275,15 @@ struct PreBwdParams {
 constexpr int kPreBwdThreads = 64;
 
 // One thread per Gaussian; its SH row and the row's gradient live in shared
-// memory (per-thread rows, odd stride) rather than in registers: at degree 3
-// the kernel takes 128 registers and 25 KB of shared memory, 8 blocks per SM.
+// memory (per-thread rows, see sh_row_floats) rather than in registers: at
+// degree 3 the kernel takes 128 registers and 26 KB of shared memory, 8 blocks
+// per SM.
 template <int DEG>
 __global__ void __launch_bounds__(kPreBwdThreads) preprocess_backward_kernel(PreBwdParams P) {
   constexpr int K = (DEG + 1) * (DEG + 1);
-  constexpr int row = 3 * K + 1;
-  __shared__ float s_sh[kPreBwdThreads * row];
-  __shared__ float s_dsh[kPreBwdThreads * row];
+  constexpr int row = sh_row_floats<K>();
+  __shared__ __align__(16) float s_sh[kPreBwdThreads * row];
+  __shared__ __align__(16) float s_dsh[kPreBwdThreads * row];
   const int64_t i0 = (int64_t)blockIdx.x * kPreBwdThreads;
   const int64_t i = i0 + threadIdx.x;
   stage_sh<K, kPreBwdThreads>(P.sh, P.sh_coeffs, i0, P.n, s_sh);
@@ -432,21 +450,29 @@ __global__ void __launch_bounds__(kPreBwdThreads) preprocess_backward_kernel(Pre
     float Y[16];
     sh_eval(DEG, dx, dy, dz, Y);
     float raw[3] = {0.5f, 0.5f, 0.5f};
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-      raw[0] += Y[k] * shc[3 * k];
-      raw[1] += Y[k] * shc[3 * k + 1];
-      raw[2] += Y[k] * shc[3 * k + 2];
-    }
+    sh_dot_rows<K>(shc, Y, raw);
     const float dr[3] = {raw[0] >= 0.f ? drgb[0] : 0.f, raw[1] >= 0.f ? drgb[1] : 0.f,
                          raw[2] >= 0.f ? drgb[2] : 0.f};
+    // dL/dsh[k][c] += Y_k dr_c and cdot_k = sum_c sh[k][c] dr_c, a float4 of
+    // the row (entry e = 3k + c) at a time
     float cdot[16];
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-      dsh[3 * k] += Y[k] * dr[0];
-      dsh[3 * k + 1] += Y[k] * dr[1];
-      dsh[3 * k + 2] += Y[k] * dr[2];
-      cdot[k] = shc[3 * k] * dr[0] + shc[3 * k + 1] * dr[1] + shc[3 * k + 2] * dr[2];
+    for (int k = 0; k < K; ++k) cdot[k] = 0.f;
+#pragma unroll
+    for (int j = 0; j < (3 * K + 3) / 4; ++j) {
+      const float4 q = reinterpret_cast<const float4*>(shc)[j];
+      float4 d = reinterpret_cast<float4*>(dsh)[j];
+      const float qv[4] = {q.x, q.y, q.z, q.w};
+      float dv[4] = {d.x, d.y, d.z, d.w};
+#pragma unroll
+      for (int t = 0; t < 4; ++t) {
+        const int e = 4 * j + t;
+        if (e < 3 * K) {
+          dv[t] += Y[e / 3] * dr[e % 3];
+          cdot[e / 3] += qv[t] * dr[e % 3];
+        }
+      }
+      reinterpret_cast<float4*>(dsh)[j] = make_float4(dv[0], dv[1], dv[2], dv[3]);
     }
     if (DEG > 0) {
       float gdir[3] = {0.f, 0.f, 0.f};
