@@ -475,7 +475,10 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
   const int64_t tiles = sort_tiles(n);
   cudaError_t e = cudaMemsetAsync(scratch, 0, radix_scratch_bytes(n, bits), stream);
   if (e != cudaSuccess) return e;
-  int hist_blocks = (int)std::min<int64_t>(4 * 152, (n + 256 * kHistKeys - 1) / (256 * kHistKeys));
+  // 8 blocks per SM keep more key loads in flight, but every block ends by
+  // adding passes x 256 counters to the global histogram: sorts of 3 or 4
+  // passes keep 4 blocks per SM
+  int hist_blocks = (int)std::min<int64_t>((passes <= 2 ? 8 : 4) * 152, (n + 256 * kHistKeys - 1) / (256 * kHistKeys));
   const bool depth = tag && tag[0] == 'd';
   GS_TIMED(depth ? "depth_sort_histogram" : "tile_sort_histogram", stream,
            (radix_histogram_kernel<<<hist_blocks, 256, 0, stream>>>(keys, n, passes, s.hist)));
