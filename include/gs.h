@@ -177,6 +177,7 @@ typedef struct gs_grads {
 } gs_grads;
 
 /* ---- plan and sizes (host only) ------------------------------------- */
+/* Host-side bookkeeping with no counterpart in the paper. */
 void gs_config_default(gs_config* cfg);
 
 /* Fills `plan` for n Gaussians seen by n_views cameras (host array).
@@ -215,14 +216,16 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
                         const uint8_t* mask, void* pre_ws, size_t pre_ws_bytes,
                         void* stream);
 
-/* Packs a byte mask (device [n_views * n], non-zero = keep) into the bit
- * mask GS_FLAG_MASK_BITS reads: bits, device [n_views][ceil(n / 32)] 32-bit
+/* Packs a per-view visibility mask (the culling mask of Sec. 5.2) given as
+ * bytes (device [n_views * n], non-zero = keep) into the bit mask
+ * GS_FLAG_MASK_BITS reads: bits, device [n_views][ceil(n / 32)] 32-bit
  * words, 4-byte aligned, OVERWRITTEN (padding bits zero).  Asynchronous;
  * GS_ERR_INVALID_ARG for bad sizes or pointers. */
 gs_status gs_pack_mask(const uint8_t* mask, int64_t n, int32_t n_views, uint32_t* bits, void* stream);
 
-/* Emits one (global tile id, item) entry per touched tile in depth order,
- * radix-sorts the entries by tile id (stable, so each tile's list stays in
+/* The tile binning of the rasterizer (Sec. 3.1): emits one (global tile id,
+ * item) entry per touched tile in depth order, radix-sorts the entries by
+ * tile id (stable, so each tile's list stays in
  * (depth, item) order) and computes each tile's [start, end) range.
  * Errors: GS_ERR_CAPACITY if sort_ws_bytes < gs_bin_sort_workspace_size. */
 gs_status gs_bin_sort(const gs_plan* plan, void* pre_ws, void* sort_ws,
@@ -300,7 +303,8 @@ gs_status gs_prune_select(const float* importance, int64_t n, int64_t k, uint32_
                           void* ws, size_t ws_bytes, void* stream);
 
 /* dst rows r = 0..k-1 <- src rows idx[r] of every attribute array (the
- * compaction before the re-render).  dst->n >= k, equal sh_coeffs. */
+ * compaction of the pruned scene before the re-render, Sec. 6.1).
+ * dst->n >= k, equal sh_coeffs. */
 gs_status gs_gather_scene(const gs_scene* src, const uint32_t* idx, int64_t k,
                           const gs_scene_buf* dst, void* stream);
 
@@ -430,6 +434,7 @@ gs_status gs_loss_l1_ssim(const gs_plan* plan, const float* image, const float* 
 gs_status gs_selftest_wait_timeout(void* scratch, size_t scratch_bytes, void* stream);
 
 /* ---- inspection --------------------------------------------------------- */
+/* Test and tooling access with no counterpart in the paper. */
 
 /* Device pointers into a preprocess workspace after gs_preprocess, for tests
  * and tools (read-only use).  Entries of culled items (tiles == 0) are not
@@ -454,6 +459,7 @@ typedef struct gs_sort_view {
 gs_status gs_inspect_sort(const gs_plan* plan, const void* sort_ws, gs_sort_view* out);
 
 /* ---- timing --------------------------------------------------------------- */
+/* Measurement support with no counterpart in the paper. */
 
 /* Opt-in per-kernel timing: while enabled, every kernel launch of the library
  * is bracketed by CUDA events recorded on its launch stream (events come from
@@ -470,6 +476,7 @@ gs_status gs_timing_enable(int on);
 int gs_timing_collect(gs_kernel_time* out, int max_out);
 
 /* ---- status ------------------------------------------------------------ */
+/* Failure reporting with no counterpart in the paper. */
 
 /* Reads (and clears) the device status word of a preprocess workspace;
  * synchronises `stream`.  Returns GS_OK, GS_ERR_TIMEOUT or GS_ERR_DEVICE_CHECK.
