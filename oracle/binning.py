@@ -37,7 +37,8 @@ def rect_min_q(A, B, C, mx, my, x0, x1, y0, y1):
     over the rectangle [x0, x1] x [y0, y1], for a positive-definite [[A,B],[B,C]].
 
     0 if the centre is inside; otherwise the minimum lies on an edge, and on
-    each edge q is a 1-D convex quadratic minimised by clamping its vertex."""
+    each edge q is a 1-D convex quadratic minimised by clamping its vertex.
+    The tile test of Sec. 3.1 under the exact-support reading."""
     A, B, C, mx, my, x0, x1, y0, y1 = np.broadcast_arrays(
         *(np.asarray(a, np.float64) for a in (A, B, C, mx, my, x0, x1, y0, y1)))
     inside = (mx >= x0) & (mx <= x1) & (my >= y0) & (my <= y1)
@@ -55,20 +56,22 @@ def rect_min_q(A, B, C, mx, my, x0, x1, y0, y1):
 
 def lambda_max(sxx, syy, sxy):
     """Larger eigenvalue of the symmetric 2x2 matrix [[sxx, sxy], [sxy, syy]]:
-    the mean of the diagonal plus the half-difference's hypotenuse with sxy."""
+    the mean of the diagonal plus the half-difference's hypotenuse with sxy.
+    Used by the 3-sigma extent of the 3DGS rasterizer recalled in Sec. 3.1."""
     sxx, syy, sxy = (np.asarray(a, np.float64) for a in (sxx, syy, sxy))
     return 0.5 * (sxx + syy) + np.hypot(0.5 * (sxx - syy), sxy)
 
 
 def three_sigma_radius(sxx, syy, sxy):
-    """r = ceil(3 sqrt(lambda_max)) of a 2-D covariance (the 3-sigma extent)."""
+    """r = ceil(3 sqrt(lambda_max)) of a 2-D covariance (the 3-sigma extent).
+    The 3-sigma extent of the 3DGS rasterizer recalled in Sec. 3.1."""
     return np.ceil(3.0 * np.sqrt(lambda_max(sxx, syy, sxy)))
 
 
 def square_tile_range(m, r, n_tiles, tile=16):
     """First and last tile index t (clipped to [0, n_tiles - 1]) whose pixel
     centres [tile t + 0.5, tile t + tile - 0.5] meet [m - r, m + r]; last <
-    first when none does."""
+    first when none does.  Tile range of the 3-sigma square (Sec. 3.1, 3-sigma extent)."""
     m, r = np.asarray(m, np.float64), np.asarray(r, np.float64)
     lo = np.ceil((m - r - (tile - 0.5)) / tile)
     hi = np.floor((m + r - 0.5) / tile)
@@ -123,7 +126,7 @@ def tile_lists(mean2d, conic, opacity, valid, width, height, alpha_min=1.0 / 255
     decision is within eps (relative to tau) of the boundary, and a second
     array of near-boundary *rejected* candidates (gauss, tiles) for the
     same tolerance.  extent="3sigma" gives the lists of the 3-sigma square
-    instead (see the module docstring)."""
+    instead (see the module docstring).  The per-tile binning of Sec. 3.1."""
     mean2d = np.asarray(mean2d, np.float64)
     conic = np.asarray(conic, np.float64)
     opacity = np.asarray(opacity, np.float64)
@@ -180,25 +183,28 @@ def sort_entries(tile_id, z32, gauss):
     """Stable order of (tile, z) keys: ascending global tile id, then
     ascending float32 bit pattern of z (equal to ascending z for z > 0), then
     input order.  Inputs are listed in (view, Gaussian, tile row-major) order.
-    Returns the permutation."""
+    Returns the permutation.  Sec. 3.1: every tile lists its Gaussians in depth order."""
     zb = np.asarray(z32, np.float32).view(np.uint32).astype(np.uint64)
     key = (np.asarray(tile_id, np.uint64) << np.uint64(32)) | zb
     return np.argsort(key, kind="stable")
 
 
 def tile_ranges(sorted_tile_ids, total_tiles):
-    """[start, end) of every global tile in the sorted entry list."""
+    """[start, end) of every global tile in the sorted entry list.
+    Sec. 3.1: each tile reads its own run of the sorted list."""
     t = np.asarray(sorted_tile_ids, np.int64)
     ids = np.arange(total_tiles)
     return np.stack([np.searchsorted(t, ids, "left"), np.searchsorted(t, ids, "right")], 1)
 
 
 def tile_grid(width, height, tile=16):
+    """Tiles across and down one view (16x16-pixel tiles, Sec. 3.1)."""
     return (width + tile - 1) // tile, (height + tile - 1) // tile
 
 
 def view_tile_bases(sizes, tile=16):
-    """Global tile-id base of every view when views are concatenated."""
+    """Global tile-id base of every view when views are concatenated.
+    Batching of several views into one list: no counterpart in the paper."""
     bases, acc = [], 0
     for (w, h) in sizes:
         bases.append(acc)
@@ -208,10 +214,12 @@ def view_tile_bases(sizes, tile=16):
 
 
 def exclusive_scan(counts):
-    """Offsets of a concatenation: out[k] = sum_{j<k} counts[j]."""
+    """Offsets of a concatenation: out[k] = sum_{j<k} counts[j].
+    The entry offsets of the binning of Sec. 3.1."""
     c = np.asarray(counts, np.int64)
     return np.concatenate([[0], np.cumsum(c)[:-1]]) if len(c) else c
 
 
 def ceil_log2(n: int) -> int:
+    """Bits of the global tile id, the sort key of Sec. 3.1."""
     return max(0, math.ceil(math.log2(max(n, 1))))

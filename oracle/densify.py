@@ -15,10 +15,12 @@ import numpy as np
 
 
 def clone_opacity(o):
+    """Opacity of each clone, o' = 1 - sqrt(1 - o) (aggressive clone, Sec. 5.1)."""
     return 1.0 - np.sqrt(1.0 - np.asarray(o, np.float64))
 
 
 def clone_scale_factor(o):
+    """Scale factor of each clone, o / (2 o' - o'^2 / sqrt 2) (aggressive clone, Sec. 5.1)."""
     o = np.asarray(o, np.float64)
     on = clone_opacity(o)
     return o / (2.0 * on - on * on / np.sqrt(2.0))

@@ -39,6 +39,7 @@ def intersected(S) -> np.ndarray:
 
 
 def keep_count(M: int, q: float) -> int:
+    """Number of values a keep quantile q of M values keeps (the reading of Sec. 5.1, 5.2)."""
     return min(M, math.ceil(float(np.float32(q)) * M))
 
 

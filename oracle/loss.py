@@ -13,7 +13,8 @@ import torch
 
 
 def l1(images, targets):
-    """Mean |image - target| over every element of every view (float64)."""
+    """Mean |image - target| over every element of every view (float64).
+    The L1 term of the 3DGS objective the paper trains with (Sec. 6.2)."""
     num = sum(torch.abs(a.to(torch.float64) - b.to(torch.float64)).sum()
               for a, b in zip(images, targets))
     den = sum(a.numel() for a in images)
@@ -29,6 +30,7 @@ SSIM_C2 = 0.03 ** 2
 
 
 def gaussian_window(size: int = 11, sigma: float = 1.5) -> torch.Tensor:
+    """The 11x11 SSIM window (sigma 1.5, normalised) of the D-SSIM term (Sec. 6.2 reading)."""
     r = size // 2
     g = torch.exp(-torch.arange(-r, r + 1, dtype=torch.float64) ** 2 / (2 * sigma * sigma))
     g = g / g.sum()
@@ -36,7 +38,8 @@ def gaussian_window(size: int = 11, sigma: float = 1.5) -> torch.Tensor:
 
 
 def ssim_map(x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
-    """SSIM map of planar [C, H, W] images (float64, zero padding)."""
+    """SSIM map of planar [C, H, W] images (float64, zero padding).
+    The SSIM of the D-SSIM term (Sec. 6.2 reading)."""
     x = x.to(torch.float64)[:, None]
     y = y.to(torch.float64)[:, None]
     w = gaussian_window()[None, None]
@@ -51,7 +54,8 @@ def ssim_map(x: torch.Tensor, y: torch.Tensor) -> torch.Tensor:
 
 def l1_ssim(images, targets, lam: float = 0.2):
     """(1 - lam) L1 + lam (1 - SSIM), both means over every element of every
-    view (the views' maps concatenated), float64."""
+    view (the views' maps concatenated), float64.
+    The photometric objective of the training step (Sec. 6.2 reading)."""
     den = sum(a.numel() for a in images)
     l1v = sum(torch.abs(a.to(torch.float64) - b.to(torch.float64)).sum() for a, b in zip(images, targets)) / den
     ss = sum(ssim_map(a, b).sum() for a, b in zip(images, targets)) / den

@@ -48,7 +48,7 @@ def rotation_matrix(q: torch.Tensor) -> torch.Tensor:
     """R(q) for (possibly unnormalised) quaternions q [..., 4] -> [..., 3, 3].
 
     Column k of R is the rotation of the basis vector e_k, computed as the
-    sandwich product q_hat e_k q_hat^*."""
+    sandwich product q_hat e_k q_hat^*.  The rotation of the covariance R(q) diag(s^2) R(q)^T (Sec. 3.1)."""
     qh = q / torch.linalg.norm(q, dim=-1, keepdim=True)
     conj = qh * torch.tensor([1.0, -1.0, -1.0, -1.0], dtype=qh.dtype)
     cols = []
@@ -79,7 +79,8 @@ def sh_basis(degree: int, dirs: torch.Tensor) -> torch.Tensor:
       Y_l(+m)  = sqrt2 K_lm (-1)^m Re((x+iy)^m) P_l^(m)(z)   (m > 0)
       Y_l(-m)  = sqrt2 K_lm (-1)^m Im((x+iy)^m) P_l^(m)(z)
     K_lm = sqrt((2l+1)/(4 pi) (l-m)!/(l+m)!), P_l^(m) the m-th derivative of
-    the Legendre polynomial; the (-1)^m is the Condon-Shortley phase."""
+    the Legendre polynomial; the (-1)^m is the Condon-Shortley phase.
+    The spherical-harmonic colour basis (Sec. 3.1)."""
     x, y, z = dirs.unbind(-1)
     out = []
     # powers of (x + i y): re/im parts by repeated complex multiplication

@@ -14,7 +14,8 @@ import numpy as np
 
 
 def keep_top_k(weight_sum, k: int) -> np.ndarray:
-    """The k largest weights, ties towards the lower index, ascending indices."""
+    """The k largest weights, ties towards the lower index, ascending indices.
+    Importance-based pruning of MSv2-D (Sec. 6.1)."""
     w = np.asarray(weight_sum, np.float64)
     n = len(w)
     order = np.lexsort((np.arange(n), -w))      # descending weight, then index
@@ -22,5 +23,6 @@ def keep_top_k(weight_sum, k: int) -> np.ndarray:
 
 
 def keep_top(weight_sum, frac: float) -> np.ndarray:
+    """Importance-based pruning of MSv2-D (Sec. 6.1): the top fraction f."""
     n = len(weight_sum)
     return keep_top_k(weight_sum, min(n, math.ceil(frac * n)))

@@ -43,7 +43,7 @@ def composite(alpha_raw: torch.Tensor, cfg: OracleConfig):
 
     alpha_raw [P, M] holds o*G for the M candidate Gaussians of every pixel,
     already in compositing order.  Returns (w [P, M], T_final [P],
-    blended [P, M] bool)."""
+    blended [P, M] bool).  Eq. 1 with the side outputs of Sec. 3.2 and 4.1."""
     alpha = torch.clamp(alpha_raw, max=cfg.alpha_max)
     keep = alpha >= cfg.alpha_min
     a = torch.where(keep, alpha, torch.zeros_like(alpha))
@@ -241,7 +241,8 @@ def _flags(alpha_raw, w, blended, zs, cfg, eps=None):
 
 def render(scene, cams, cfg: OracleConfig | None = None, masks=None, pix=None,
            want_depth=True) -> list[dict]:
-    """Render every camera in `cams` from a Scene (float64, no grad)."""
+    """Render every camera in `cams` from a Scene (float64, no grad).
+    Eq. 1 and 2 with the side outputs of Sec. 3.2 and 4.1."""
     cfg = cfg or OracleConfig()
     outs = []
     with torch.no_grad():
@@ -255,14 +256,16 @@ def render(scene, cams, cfg: OracleConfig | None = None, masks=None, pix=None,
 
 
 def planar(colour: torch.Tensor, cam) -> torch.Tensor:
-    """[H*W, 3] row-major pixel colours -> planar [3, H, W]."""
+    """[H*W, 3] row-major pixel colours -> planar [3, H, W].
+    Output layout only: no counterpart in the paper."""
     return colour.reshape(cam.height, cam.width, 3).permute(2, 0, 1)
 
 
 def contributors(proj: dict, pix, alpha_min: float, slack: float = 1e-3) -> np.ndarray:
     """Indices of the Gaussians whose o*G reaches (1 - slack) * alpha_min at
     any of the given (u, v) pixels (no depth order, no termination): a
-    superset of the Gaussians that can influence those pixels."""
+    superset of the Gaussians that can influence those pixels.
+    Test helper for the alpha_min skip rule of Eq. 1."""
     pix = np.asarray(pix).reshape(-1, 2)
     if len(pix) == 0:
         return np.zeros(0, np.int64)

@@ -40,7 +40,8 @@ def weighted_sample(I, E, k: int) -> np.ndarray:
 
 
 def reproject(depth, pix, cam) -> np.ndarray:
-    """World points of view-local pixels pix (y W + x) at depths depth[pix]."""
+    """World points of view-local pixels pix (y W + x) at depths depth[pix].
+    The reprojection of the depth map to world space (Sec. 4.2)."""
     pix = np.asarray(pix, np.int64)
     x, y = pix % cam.width, pix // cam.width
     d = np.asarray(depth, np.float64)[pix]
