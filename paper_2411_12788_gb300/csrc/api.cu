@@ -3,6 +3,9 @@
 // gs_render_bwd.  Every device buffer is the caller's; the only allocation is
 // one pinned, mapped 16-byte host word per host thread (first use, kept for
 // the process) through which gs_preprocess reads its status and entry count.
+// The calls sequence the steps of the paper's rasterizer (projection and SH
+// colour, binning and sort, Sec. 3.1; blending, Eq. 1; the outputs of Sec. 3.2,
+// 3.3 and 4.1); the plans, layouts and checks here have no counterpart in it.
 #include <math.h>
 #include <string.h>
 

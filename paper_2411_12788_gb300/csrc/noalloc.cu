@@ -1,5 +1,6 @@
-// gs_bin_sort_noalloc: the binning and tile sort of gs_bin_sort for callers
-// that cannot allocate device memory.
+// gs_bin_sort_noalloc: the binning and tile sort of gs_bin_sort (Sec. 3.1) for
+// callers that cannot allocate device memory; the variant itself has no
+// counterpart in the paper.
 //
 // Some callers cannot call cudaMalloc (or any allocating routine) at the
 // point where they render: a renderer embedded in a host that owns all GPU

@@ -1,7 +1,8 @@
 // Opt-in per-kernel timing with CUDA events recorded on each kernel's launch
 // stream.  Disabled by default; when enabled, every kernel launch of the
 // library is bracketed by two events from a fixed pool created at enable
-// time (no allocation while timing).  Single-threaded use.
+// time (no allocation while timing).  Single-threaded use.  Measurement
+// support with no counterpart in the paper.
 #include <string.h>
 
 #include <vector>
