@@ -181,8 +181,14 @@ __device__ __forceinline__ bool tile_rows(const BinParams& b, int tiles_y, int* 
 // lost most of its digits near the support edge anyway).  The term
 // 2e-3 sqrt(Sxx) covers the absolute part (q error up to 4e-6) and 0.5 px more
 // the rounding of the box ends.  The result is rounded up to half precision,
-// so the box contains every pixel whose exponent test can pass.
+// so the box contains every pixel whose exponent test can pass.  Beyond
+// kappa = 2e5 (or for a kappa that is not a finite number) the argument does
+// not hold, and the extent is infinite: the box then meets every block and
+// only the exact exponent test of the backward (block_may_blend) culls.
+constexpr float kSupportKappaMax = 2e5f;
+
 __device__ __forceinline__ float support_extent(float r, float s_diag, float kappa) {
+  if (!(kappa <= kSupportKappaMax)) return INFINITY;
   return fmaf(fmaf(4e-6f, kappa, 1.02f), r, fmaf(2e-3f, sqrtf(s_diag), 0.5f));
 }
 

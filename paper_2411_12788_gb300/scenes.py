@@ -131,23 +131,45 @@ def box_scene(n: int = 1024, seed: int = 0, sh_degree: int = 0) -> Scene:
                    {"kind": "box", "seed": seed})
 
 
-def needle_scene(n: int = 4000, seed: int = 0) -> Scene:
+def needle_scene(n: int = 4000, seed: int = 0, long_range=(0.02, 0.5), faint_frac: float = 0.5) -> Scene:
     """Adversarial scene for the support-box margins: means uniform in
-    [-1.5,1.5]^2 x [2,8], long axis log-uniform in [0.02, 0.5], the other two
-    shorter by a log-uniform ratio in [1, 1000] (x U[0.5, 2] for the third),
-    uniform unit quaternions, half the opacities just above 1/255
-    ((1 + U[1e-4, 1e-2]) / 255) and half U[0.05, 0.99], DC colour U[0,1]."""
+    [-1.5,1.5]^2 x [2,8], long axis log-uniform in `long_range` (default
+    [0.02, 0.5]), the other two shorter by a log-uniform ratio in [1, 1000]
+    (x U[0.5, 2] for the third), uniform unit quaternions, a fraction
+    `faint_frac` (default half) of the opacities just above 1/255
+    ((1 + U[1e-4, 1e-2]) / 255) and the rest U[0.05, 0.99], DC colour U[0,1]."""
     rng = np.random.default_rng(seed)
     means = np.stack([rng.uniform(-1.5, 1.5, n), rng.uniform(-1.5, 1.5, n),
                       rng.uniform(2, 8, n)], axis=1)
-    long = np.exp(rng.uniform(np.log(0.02), np.log(0.5), n))
+    long = np.exp(rng.uniform(np.log(long_range[0]), np.log(long_range[1]), n))
     short = long / np.exp(rng.uniform(0.0, np.log(1e3), n))
     scales = np.stack([long, short, short * rng.uniform(0.5, 2.0, n)], axis=1)
     quats = _unit_quaternions(rng, n)
-    faint = rng.uniform(size=n) < 0.5
+    faint = rng.uniform(size=n) < faint_frac
     opac = np.where(faint, (1.0 + rng.uniform(1e-4, 1e-2, n)) / 255.0, rng.uniform(0.05, 0.99, n))
     sh = _sh_from_colour(rng, n, 0, 0.05)
     return _finish(means, scales, quats, opac, sh, 0, {"kind": "needles", "seed": seed})
+
+
+def crossing_needles_scene(n: int = 200, seed: int = 0) -> Scene:
+    """Long, extremely thin needles lying nearly in the image plane of a
+    camera at the origin looking down +z, all passing close to the optical
+    axis (so that they cross the image and one another): means
+    U([-0.3,0.3]^2 x [3,5]), long axis log-uniform in [0.5, 2], the other two
+    1e-4 of it, rotations about the viewing axis by a uniform angle (tilted
+    by N(0, 0.05) quaternion components), opacity U[0.3, 0.9], DC colour
+    U[0,1].  Seen at focal lengths near 1000 px their projected
+    covariances have condition numbers from 1e4 to above 1e6."""
+    rng = np.random.default_rng(seed)
+    means = np.stack([rng.uniform(-0.3, 0.3, n), rng.uniform(-0.3, 0.3, n), rng.uniform(3, 5, n)], axis=1)
+    long = np.exp(rng.uniform(np.log(0.5), np.log(2.0), n))
+    scales = np.stack([long, 1e-4 * long, 1e-4 * long], axis=1)
+    th = rng.uniform(0.0, 2 * np.pi, n)
+    quats = np.stack([np.cos(th / 2), rng.normal(0, 0.05, n), rng.normal(0, 0.05, n), np.sin(th / 2)], axis=1)
+    quats /= np.linalg.norm(quats, axis=1, keepdims=True)
+    opac = rng.uniform(0.3, 0.9, n)
+    sh = _sh_from_colour(rng, n, 0, 0.05)
+    return _finish(means, scales, quats, opac, sh, 0, {"kind": "crossing-needles", "seed": seed})
 
 
 def cluster_scene(n: int, n_clusters: int = 64, seed: int = 0,

@@ -86,3 +86,40 @@ def test_backward_culling_drops_no_blended_pair(seed):
     b = fr.outs["weight_sum"].double().cpu()
     assert (b > 0).sum() > 2000
     assert torch.all((a - b).abs() <= 2e-6 + 1e-5 * b.abs())
+
+
+def test_culling_past_the_validated_condition_number():
+    """The box margin is argued only up to a 2-D condition number of 2e5.
+    Long, extremely thin needles crossing the view (condition numbers from
+    4e4 to above 1e6) must get unbounded boxes past the bound (the culling
+    then rests on the exact exponent test alone) and finite ones below it,
+    and the backward must still replay every pair the forward blended: its
+    collected I_i equals the forward's, also for the Gaussians past the bound."""
+    _need_gpu()
+    sc = scenes.crossing_needles_scene(200, seed=0)
+    cams = [scenes.origin_camera(512, 512, 1024.0)]
+    g = raster.GaussianTensors.from_scene(sc)
+    fr = raster.forward(g, cams)
+    st = raster.inspect_preprocess(fr)
+    co = st["conic_o"].numpy().astype(np.float64)
+    vis = st["tiles"].numpy() > 0
+    A, B, C = co[:, 0], co[:, 1], co[:, 2]
+    disc = np.sqrt(((A - C) / 2) ** 2 + B ** 2)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        kappa = ((A + C) / 2 + disc) / ((A + C) / 2 - disc)
+    ex, ey = _unpack_extents(st["rgb"].numpy()[:, 3])
+    past = vis & (kappa > 2.1e5)
+    within = vis & (kappa < 1.9e5)
+    assert past.sum() >= 50 and within.sum() >= 50, (past.sum(), within.sum())
+    assert np.isinf(ex[past]).all() and np.isinf(ey[past]).all()
+    assert np.isfinite(ex[within]).all() and np.isfinite(ey[within]).all()
+    grads = raster.alloc_grads(g)
+    grads["weight_sum"] = torch.zeros(int(fr.plan.n_items), device="cuda")
+    dL = torch.rand_like(fr.outs["image"]) - 0.5
+    raster.render_bwd(fr.plan, g.struct(), fr.cfg, fr.pre_ws, fr.sort_ws, dL, fr.outs["image"],
+                      fr.outs["n_contrib"], grads)
+    torch.cuda.synchronize()
+    a = grads["weight_sum"].double().cpu().numpy()
+    b = fr.outs["weight_sum"].double().cpu().numpy()
+    assert np.all(np.abs(a - b) <= 2e-6 + 1e-5 * np.abs(b))
+    assert (b[past] > 1.0).sum() >= 50, (b[past] > 1.0).sum()
