@@ -186,6 +186,17 @@ void preprocess_parts(const gs_plan* plan, void* pre_ws, const ViewDev** views, 
   *status = at<uint32_t>(pre_ws, L.status);
 }
 
+int device_sm_count() {
+  static std::atomic<int> cache[64];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 1;
+  int v = cache[dev].load(std::memory_order_relaxed);
+  if (v > 0) return v;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) return 1;
+  cache[dev].store(v, std::memory_order_relaxed);
+  return v;
+}
+
 }  // namespace gs
 
 using namespace gs;

@@ -262,7 +262,7 @@ cudaError_t launch_loss_l1(const float* image, const float* target, int64_t coun
   cudaError_t e = cudaMemsetAsync(loss, 0, sizeof(float), stream);
   if (e != cudaSuccess) return e;
   if (count > 0) {
-    const int blocks = (int)std::min<int64_t>(ceil_div(count, 256), 152 * 8);
+    const int blocks = (int)std::min<int64_t>(ceil_div(count, 256), (int64_t)8 * device_sm_count());
     GS_TIMED("loss_l1", stream, (l1_kernel<<<blocks, 256, 0, stream>>>(image, target, count, loss, dL)));
   }
   return cudaGetLastError();

@@ -128,6 +128,11 @@ cudaError_t once_per_device(std::atomic<uint64_t>& done, F&& init) {
   return e;
 }
 
+// Streaming multiprocessors of the current device, queried once per device
+// (api.cu); grid-stride launch shapes are sized in multiples of it.  1 if the
+// query fails (every such launch is still correct, only narrower).
+int device_sm_count();
+
 // ---- onesweep radix sort sizing (sort.cu) ----------------------------------
 constexpr int kRadixBits = 8;
 constexpr int kRadix = 1 << kRadixBits;

@@ -337,7 +337,7 @@ cudaError_t select_threshold(const uint32_t* keys, int64_t n, const SelectBufs& 
   cudaError_t e = cudaMemsetAsync(B.hist, 0, 256 * 4, stream);
   if (e != cudaSuccess) return e;
   const int blocks = ceil_div(n, 256);
-  const int hb = std::min(blocks, 4 * 152);
+  const int hb = std::min(blocks, 4 * device_sm_count());
   for (int pass = 0; pass < 4; ++pass) {
     const int shift = 24 - 8 * pass;
     GS_TIMED("select_hist", stream, (select_hist_kernel<<<hb, kSelThreads, 0, stream>>>(keys, n, shift, B.st, B.hist)));
@@ -366,7 +366,7 @@ cudaError_t select_init_count(const uint32_t* keys, int64_t n, int64_t k, const 
   cudaError_t e = cudaMemsetAsync(B.count, 0, 4, stream);
   if (e != cudaSuccess) return e;
   GS_TIMED("select_count", stream,
-           (count_positive_kernel<<<std::max(1, std::min(ceil_div(n, 256), 4 * 152)), 256, 0, stream>>>(keys, n,
+           (count_positive_kernel<<<std::max(1, std::min(ceil_div(n, 256), 4 * device_sm_count())), 256, 0, stream>>>(keys, n,
                                                                                                         B.count)));
   GS_TIMED("select_init", stream, (select_init_count_kernel<<<1, 1, 0, stream>>>(B.st, B.count, k, B.k_dev)));
   return cudaGetLastError();
@@ -377,7 +377,7 @@ cudaError_t select_init_quantile(const uint32_t* keys, int64_t n, float q, const
   cudaError_t e = cudaMemsetAsync(B.count, 0, 4, stream);
   if (e != cudaSuccess) return e;
   GS_TIMED("select_count", stream,
-           (count_positive_kernel<<<std::max(1, std::min(ceil_div(n, 256), 4 * 152)), 256, 0, stream>>>(keys, n,
+           (count_positive_kernel<<<std::max(1, std::min(ceil_div(n, 256), 4 * device_sm_count())), 256, 0, stream>>>(keys, n,
                                                                                                         B.count)));
   GS_TIMED("select_init", stream, (select_init_kernel<<<1, 1, 0, stream>>>(B.st, B.count, q)));
   return cudaGetLastError();

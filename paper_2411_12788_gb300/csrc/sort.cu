@@ -478,7 +478,8 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
   // 8 blocks per SM keep more key loads in flight, but every block ends by
   // adding passes x 256 counters to the global histogram: sorts of 3 or 4
   // passes keep 4 blocks per SM
-  int hist_blocks = (int)std::min<int64_t>((passes <= 2 ? 8 : 4) * 152, (n + 256 * kHistKeys - 1) / (256 * kHistKeys));
+  int hist_blocks = (int)std::min<int64_t>((int64_t)(passes <= 2 ? 8 : 4) * device_sm_count(),
+                                          (n + 256 * kHistKeys - 1) / (256 * kHistKeys));
   const bool depth = tag && tag[0] == 'd';
   GS_TIMED(depth ? "depth_sort_histogram" : "tile_sort_histogram", stream,
            (radix_histogram_kernel<<<hist_blocks, 256, 0, stream>>>(keys, n, passes, s.hist)));
@@ -494,11 +495,13 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
+  cudaError_t el = cudaGetLastError();
+  if (el != cudaSuccess) return el;
   if (kin != keys) {   // odd number of passes: the result sits in the alt buffers
-    cudaMemcpyAsync(keys, kin, n * 4, cudaMemcpyDeviceToDevice, stream);
-    cudaMemcpyAsync(vals, vin, n * 4, cudaMemcpyDeviceToDevice, stream);
+    el = cudaMemcpyAsync(keys, kin, n * 4, cudaMemcpyDeviceToDevice, stream);
+    if (el == cudaSuccess) el = cudaMemcpyAsync(vals, vin, n * 4, cudaMemcpyDeviceToDevice, stream);
   }
-  return cudaGetLastError();
+  return el;
 }
 
 cudaError_t lookback_timeout_probe(uint32_t* scratch, uint32_t* status, cudaStream_t stream) {
