@@ -154,6 +154,9 @@ typedef struct gs_fwd_outputs {
                                the atomic adds (bit-reproducible, unlike weight_sum) */
   float* depth_center;      /* [total_pixels] d^center = camera z of i_max's centre (the
                                alternative depth of Sec. 4.1), 0 if none */
+  uint32_t* n_blended;      /* [total_pixels] nullable: number of entries blended at the pixel
+                               (Eq. 1's terms with alpha >= alpha_min before the stop); the
+                               positions before n_contrib that are not blended were skipped */
 } gs_fwd_outputs;
 
 /* Gradients, device, ACCUMULATED (+=) over views, same layouts as gs_scene;

@@ -67,7 +67,7 @@ class FwdOutputs(C.Structure):
     _fields_ = [("image", C.c_void_p), ("final_T", C.c_void_p), ("n_contrib", C.c_void_p),
                 ("imax", C.c_void_p), ("wmax", C.c_void_p), ("depth", C.c_void_p),
                 ("depth_blend", C.c_void_p), ("weight_sum", C.c_void_p), ("max_area", C.c_void_p),
-                ("weight_sum_fixed", C.c_void_p), ("depth_center", C.c_void_p)]
+                ("weight_sum_fixed", C.c_void_p), ("depth_center", C.c_void_p), ("n_blended", C.c_void_p)]
 
 
 class Grads(C.Structure):

@@ -77,6 +77,7 @@ struct FwdOut {
   uint32_t* max_area;
   uint64_t* weight_sum_fixed;   // I_i in units of 2^-24 (integer sums: order-independent)
   float* depth_center;          // camera z of i_max's centre
+  uint32_t* n_blended;          // entries blended per pixel
 };
 
 // Exponent form of an entry's 2-D Gaussian (identical in both kernels).
@@ -147,6 +148,7 @@ struct FwdPix {
   float T, cr, cg, cb, dblend, wmax;
   int imax_pos;                 // list position of the argmax, -1 if none
   uint32_t last;                // one past the last blended position
+  uint32_t nbl;                 // blended entries (counted when asked for)
   bool done;
 };
 
@@ -157,11 +159,13 @@ __device__ __forceinline__ void fwd_pix_init(FwdPix& q, int px, int py, bool ins
   q.cr = q.cg = q.cb = q.dblend = q.wmax = 0.f;
   q.imax_pos = -1;
   q.last = 0;
+  q.nbl = 0;
   q.done = !inside;
 }
 
 // Blends the entry at list position `pos`, with exponent e at this pixel, into
 // the pixel; returns its weight.
+template <bool kCount>
 __device__ __forceinline__ float fwd_pix_blend(FwdPix& q, float e, const float4* s_rgbz, int j, int pos,
                                                float alpha_max, float e_min, float t_min) {
   if (q.done) return 0.f;
@@ -184,6 +188,7 @@ __device__ __forceinline__ float fwd_pix_blend(FwdPix& q, float e, const float4*
   }
   q.T = Tn;
   q.last = pos + 1;
+  if (kCount) ++q.nbl;
   return w;
 }
 
@@ -198,6 +203,7 @@ __device__ __forceinline__ void fwd_pix_store(const FwdPix& q, const RenderParam
   img[2 * hw] = q.cb + q.T * P.bg[2];
   O.final_T[pix] = q.T;
   O.n_contrib[pix] = q.last;
+  if (O.n_blended) O.n_blended[pix] = q.nbl;
   if (O.imax) O.imax[pix] = imax_item >= 0 ? (int32_t)(imax_item - (int64_t)view * P.n) : -1;
   if (O.wmax) O.wmax[pix] = q.wmax;
   if (O.depth_blend) O.depth_blend[pix] = q.dblend;
@@ -293,7 +299,7 @@ __device__ __forceinline__ void fwd_pixel_of(const ViewDev& V, int tile, int t, 
 // Blends a staged batch of nb entries into the thread's two pixels (same
 // row, so they share the exponent's row part); the warp stops once all
 // its pixels have (checked every 8 entries: a stopped pixel ignores the rest).
-template <bool kWantW>
+template <bool kWantW, bool kCount>
 __device__ __forceinline__ void fwd_batch(FwdPix& q0, FwdPix& q1, int nb, int pos0, const float2* s_xy,
                                           const float4* s_ex, const float4* s_rgbz, uint32_t* s_wsum,
                                           const RenderParams& P, int lane) {
@@ -308,8 +314,8 @@ __device__ __forceinline__ void fwd_batch(FwdPix& q0, FwdPix& q1, int nb, int po
       const float2 row = expo_row(ex, q0.fy - m.y);
       const float e0 = expo_pix(ex, row, q0.fx - m.x);
       const float e1 = expo_pix(ex, row, q1.fx - m.x);
-      const float w0 = fwd_pix_blend(q0, e0, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
-      const float w1 = fwd_pix_blend(q1, e1, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
+      const float w0 = fwd_pix_blend<kCount>(q0, e0, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
+      const float w1 = fwd_pix_blend<kCount>(q1, e1, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
       if (kWantW && __any_sync(0xffffffffu, w0 > 0.f || w1 > 0.f)) {
         const uint32_t s = __reduce_add_sync(0xffffffffu, __float2uint_rn(w0 * 16777216.f) +
                                                               __float2uint_rn(w1 * 16777216.f));
@@ -319,7 +325,7 @@ __device__ __forceinline__ void fwd_batch(FwdPix& q0, FwdPix& q1, int nb, int po
   }
 }
 
-template <bool kWantW>
+template <bool kWantW, bool kCount>
 __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P, FwdOut O) {
   constexpr int kBatch = kTilePixels;
   __shared__ int s_view;
@@ -365,7 +371,7 @@ __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P,
     __syncthreads();
     const int nb = (int)min(range.y - bstart, (uint32_t)kBatch);
     const int pos0 = (int)(bstart - range.x);
-    fwd_batch<kWantW>(q0, q1, nb, pos0, s_xy, s_ex, s_rgbz, s_wsum, P, lane);
+    fwd_batch<kWantW, kCount>(q0, q1, nb, pos0, s_xy, s_ex, s_rgbz, s_wsum, P, lane);
     __syncthreads();
     if (kWantW) {
 #pragma unroll
@@ -702,12 +708,18 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
                               const gs_fwd_outputs& out, cudaStream_t stream) {
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
   FwdOut O{out.image, out.final_T, out.n_contrib, out.imax, out.wmax, out.depth, out.depth_blend,
-           out.weight_sum, out.max_area, out.weight_sum_fixed, out.depth_center};
-  if (total_tiles > 0)
-    GS_TIMED("render_fwd", stream,
-             (O.weight_sum || O.weight_sum_fixed
-                  ? render_fwd_kernel<true><<<total_tiles, kFwdThreads, 0, stream>>>(P, O)
-                  : render_fwd_kernel<false><<<total_tiles, kFwdThreads, 0, stream>>>(P, O)));
+           out.weight_sum, out.max_area, out.weight_sum_fixed, out.depth_center, out.n_blended};
+  if (total_tiles > 0) {
+    const bool w = O.weight_sum || O.weight_sum_fixed;
+    if (O.n_blended)
+      GS_TIMED("render_fwd", stream,
+               (w ? render_fwd_kernel<true, true><<<total_tiles, kFwdThreads, 0, stream>>>(P, O)
+                  : render_fwd_kernel<false, true><<<total_tiles, kFwdThreads, 0, stream>>>(P, O)));
+    else
+      GS_TIMED("render_fwd", stream,
+               (w ? render_fwd_kernel<true, false><<<total_tiles, kFwdThreads, 0, stream>>>(P, O)
+                  : render_fwd_kernel<false, false><<<total_tiles, kFwdThreads, 0, stream>>>(P, O)));
+  }
   return cudaGetLastError();
 }
 

@@ -315,7 +315,7 @@ def inspect_sort(fr: "Frame") -> dict:
 
 # ---------------------------------------------------------------- outputs
 FWD_OUTPUTS = ("image", "final_T", "n_contrib", "imax", "wmax", "depth", "depth_blend",
-               "weight_sum", "max_area", "depth_center")
+               "weight_sum", "max_area", "depth_center", "n_blended")
 
 
 def alloc_outputs(plan, device="cuda", want=FWD_OUTPUTS) -> dict:
@@ -326,7 +326,7 @@ def alloc_outputs(plan, device="cuda", want=FWD_OUTPUTS) -> dict:
     spec = {"image": (3 * P, f32), "final_T": (P, f32), "n_contrib": (P, i32), "imax": (P, i32),
             "wmax": (P, f32), "depth": (P, f32), "depth_blend": (P, f32),
             "weight_sum": (I, f32), "max_area": (I, i32), "weight_sum_fixed": (I, torch.int64),
-            "depth_center": (P, f32)}
+            "depth_center": (P, f32), "n_blended": (P, i32)}
     out = {}
     for k in spec:
         if k in want or k in ("image", "final_T", "n_contrib"):

@@ -5,7 +5,8 @@ Stage by stage: projection (tolerance), binning / sort order / tile ranges
 outputs (tolerance, near-threshold pixels excluded and counted) and gradients
 (relative tolerance).  Tolerances, derived from FP32 arithmetic:
   colour, T, w_max            max-abs 1e-4
-  depth (d^mid, d^blend)      1e-4 * max(1, |d|)   (values reach ~30)
+  depth d^mid, d^center        max-abs 1e-4  (values reach ~35)
+  depth d^blend               1e-4 + 1e-5 |d^blend|  (FP32 transmittance, see _depth_tol)
   I_i (summed weights)        1e-4 + 1e-5 * I      (sums of up to ~1e4 terms)
   gradients                   |g - g_ref| <= 1e-3 max(|g_ref|, 1e-2 ||g_ref||_inf)
 """
@@ -149,8 +150,23 @@ def test_binning_sort_ranges_bit_exact(case):
 
 
 # ---------------------------------------------------------------- stage R
+def _depth_tol(name, ref):
+    """d^mid (Eq. 2) and d^center: max-abs 1e-4.  d^blend = sum_i w_i z_i:
+    1e-4 + 1e-5 |d^blend|.  Its weights carry the FP32 transmittance, whose
+    relative error grows by alpha / (1 - alpha) (up to 99 at the 0.99
+    clamp) times the 2^-24 rounding of each alpha in front; times depths up
+    to ~35 that alone can exceed 1e-4, so the blended depth is held to a
+    relative bar on top of the absolute one."""
+    if name == "depth_blend":
+        return 1e-4 + 1e-5 * np.abs(ref)
+    return 1e-4
+
+
 def _check_render(sc, cams, fr, max_flag_frac=2e-3, cfg=None):
+    """Render outputs of every view against the oracle; returns the largest
+    depth errors seen (d^mid, d^center, d^blend)."""
     n = sc.n
+    worst = {}
     for v, cam in enumerate(cams):
         pr, out = _oracle_view(sc, cam, cfg=cfg)
         ok = out["flags"].numpy() == 0
@@ -164,15 +180,17 @@ def _check_render(sc, cams, fr, max_flag_frac=2e-3, cfg=None):
         assert np.abs(wmax - out["wmax"].numpy())[ok].max() <= 1e-4
         imax = _gpu_pixels(fr, v, "imax").numpy()
         np.testing.assert_array_equal(imax[ok], out["imax"].numpy()[ok])
-        d = _gpu_pixels(fr, v, "depth").double().numpy()
-        dref = out["depth"].numpy()
-        assert np.all(np.abs(d - dref)[ok] <= 1e-4 * np.maximum(1.0, np.abs(dref[ok])))
-        dc = _gpu_pixels(fr, v, "depth_center").double().numpy()
-        dcr = out["depth_center"].numpy()
-        assert np.all(np.abs(dc - dcr)[ok] <= 1e-5 * np.maximum(1.0, np.abs(dcr[ok])))
-        db = _gpu_pixels(fr, v, "depth_blend").double().numpy()
-        dbr = out["depth_blend"].numpy()
-        assert np.all(np.abs(db - dbr)[ok] <= 1e-4 * np.maximum(1.0, np.abs(dbr[ok])))
+        if "n_blended" in fr.outs:
+            nbl = _gpu_pixels(fr, v, "n_blended").numpy()
+            np.testing.assert_array_equal(nbl[ok], out["n_blended"].numpy()[ok])
+        # depths (values reach ~35): d^mid and d^center max-abs 1e-4; d^blend
+        # max-abs 1e-4 + 1e-5 |d^blend| (FP32 transmittances: see _DEPTH_TOL)
+        for name in ("depth", "depth_center", "depth_blend"):
+            d = _gpu_pixels(fr, v, name).double().numpy()
+            ref = out[name].numpy()
+            err = np.abs(d - ref)[ok]
+            worst[name] = max(worst.get(name, 0.0), float(err.max()) if err.size else 0.0)
+            assert np.all(err <= _depth_tol(name, ref[ok])), (name, err.max())
         # n_contrib points at the last blended Gaussian in the tile's list
         nc = _gpu_pixels(fr, v, "n_contrib").numpy().astype(np.int64)
         last = out["last"].numpy()
@@ -196,6 +214,8 @@ def _check_render(sc, cams, fr, max_flag_frac=2e-3, cfg=None):
         assert np.all(np.abs(ws - wr)[keep] <= 1e-4 + 1e-5 * np.abs(wr[keep]))
         ma = fr.outs["max_area"][v * n:(v + 1) * n].cpu().numpy()
         np.testing.assert_array_equal(ma[keep], out["max_area"].numpy()[keep])
+    print(f"largest depth errors: {worst}")
+    return worst
 
 
 @pytest.mark.parametrize("case", list(SCENES))
@@ -483,9 +503,13 @@ def test_training_scale_sampled_pixels():
     lin = pix[:, 1] * cam.width + pix[:, 0]
     col = _gpu_colour(fr, 0).numpy()[lin]
     assert np.abs(col - out["colour"].numpy())[ok].max() <= 1e-4
-    d = _gpu_pixels(fr, 0, "depth").double().numpy()[lin]
-    dref = out["depth"].numpy()
-    assert np.all(np.abs(d - dref)[ok] <= 1e-4 * np.maximum(1, np.abs(dref[ok])))
+    for name in ("depth", "depth_center", "depth_blend"):
+        d = _gpu_pixels(fr, 0, name).double().numpy()[lin]
+        ref = out[name].numpy()
+        err = np.abs(d - ref)[ok]
+        k = int(np.argmax(err))
+        print(f"{name}: largest error {err.max():.3e} (at depth {ref[ok][k]:.2f}) over {ok.sum()} sampled pixels")
+        assert np.all(err <= _depth_tol(name, ref[ok])), (name, err.max())
     np.testing.assert_array_equal(_gpu_pixels(fr, 0, "imax").numpy()[lin][ok], out["imax"].numpy()[ok])
     so = raster.inspect_sort(fr)
     st = raster.inspect_preprocess(fr)
