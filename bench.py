@@ -243,30 +243,28 @@ def roofline(kt: dict, st: "Step", steps: int, peaks: dict, clocks: dict, name: 
     ms = kt[name]["ms"] / max(1, kt[name]["launches"])
     E = int(st.plan.n_entries)
     torch = st.torch
-    if name == "render_bwd":
-        # units: (pixel, entry) evaluations = sum of n_contrib; ALU-bound
-        evals = float(st.outs["n_contrib"].to(torch.int64).sum().item())
-        flops = evals * BWD_FLOPS_PER_EVAL
+    if name in ("render_bwd", "render_fwd"):
+        # ALU-bound.  Units: the (pixel, entry) pairs the sequential per-pixel
+        # algorithm evaluates up to the last blended entry (sum of n_contrib);
+        # the blended ones cost the full per-pair figure, the skipped ones
+        # (alpha < 1/255) only the offsets and the exponent
+        pc = pair_counts(st)
+        full = BWD_FLOPS_PER_BLEND if name == "render_bwd" else FWD_FLOPS_PER_BLEND
+        flops = pc["blended"] * full + pc["skipped"] * FLOPS_PER_SKIP
+        sms = st.torch.cuda.get_device_properties(st.torch.cuda.current_device()).multi_processor_count
         sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
+        peak = sms * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
         ach = flops / (ms * 1e-3) / 1e12
         traffic = profiled_traffic(name, E)
         return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": traffic,
                 "traffic_note": (f"DRAM bytes per launch from ncu ({PROFILED_TRAFFIC[name]['profile']}); "
                                  f"algorithmic {flops / traffic:.0f} flop per byte moved") if traffic else None,
-                "units": {"evaluations_per_launch": evals, "flops_per_evaluation": BWD_FLOPS_PER_EVAL},
-                "peak_note": f"FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled)"}
-    if name == "render_fwd":
-        evals = float(st.outs["n_contrib"].to(torch.int64).sum().item())
-        flops = evals * FWD_FLOPS_PER_EVAL
-        sm_mhz = clocks.get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
-        peak = FP32_LANES * 2 * sm_mhz * 1e6 / 1e12
-        ach = flops / (ms * 1e-3) / 1e12
-        return {"kernel": name, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
-                "frac": ach / peak, "traffic": None,
-                "units": {"evaluations_per_launch": evals, "flops_per_evaluation": FWD_FLOPS_PER_EVAL},
-                "peak_note": f"FP32 FMA issue: 152 SMs x 128 lanes x 2 flop x {sm_mhz:.0f} MHz (median sampled)"}
+                "units": {"blended_pairs_per_launch": pc["blended"], "skipped_pairs_per_launch": pc["skipped"],
+                          "flops_per_blended_pair": full, "flops_per_skipped_pair": FLOPS_PER_SKIP,
+                          "flops_per_launch": flops},
+                "peak_note": f"FP32 FMA issue: {sms} SMs (device query) x {FP32_LANES_PER_SM} lanes x 2 flop x "
+                             f"{sm_mhz:.0f} MHz (median sampled)"}
     # HBM-bound kernels: algorithmic bytes per launch.  V = items with a tile
     # (the rest are culled and write only their count and depth key).
     I = int(st.plan.n_items)
@@ -287,17 +285,38 @@ def roofline(kt: dict, st: "Step", steps: int, peaks: dict, clocks: dict, name: 
             "frac": ach / peak, "traffic": None}
 
 
-FP32_LANES = 152 * 128
-# Algorithmic FP32 operations (an FMA counts 2) per (pixel, entry)
-# evaluation of a blended entry, counted for the plain sequential per-pixel
-# algorithm (no scan or other parallelisation overhead): forward: offsets 2,
-# exponent 8, alpha 2, transmittance 2, weight 1, colour 6, blended depth 2,
-# argmax 1 = 24; backward: offsets 2, exponent 8, alpha 2, transmittance 2,
-# weight 1, c.g 5, running colour sum 2, colour gradient 6, dL/dalpha 4,
-# dL/de 2, conic and centre terms 17, I_i 1 = 52.  MUFU work (ex2, rcp) is not
-# counted.
-FWD_FLOPS_PER_EVAL = 24
-BWD_FLOPS_PER_EVAL = 52
+FP32_LANES_PER_SM = 128
+# Algorithmic FP32 operations (an FMA counts 2) per (pixel, entry) pair,
+# counted for the plain sequential per-pixel algorithm (no scan or other
+# parallelisation overhead).  A blended pair: forward: offsets 2, exponent 8,
+# alpha 2, transmittance 2, weight 1, colour 6, blended depth 2, argmax 1 =
+# 24; backward: offsets 2, exponent 8, alpha 2, transmittance 2, weight 1,
+# c.g 5, running colour sum 2, colour gradient 6, dL/dalpha 4, dL/de 2, conic
+# and centre terms 17, I_i 1 = 52.  A pair skipped at alpha < 1/255: offsets
+# 2 and exponent 8 = 10.  The forward's evaluations past the last blended
+# entry (the stopping entry, or the rest of a list that never stops) are not
+# counted, so the figure is a lower bound of the forward's work.  MUFU work
+# (ex2, rcp) is not counted.
+FWD_FLOPS_PER_BLEND = 24
+BWD_FLOPS_PER_BLEND = 52
+FLOPS_PER_SKIP = 10
+
+
+def pair_counts(st: "Step") -> dict:
+    """Pairs of the step's last forward: blended (sum of n_blended) and
+    skipped before the last blended entry (sum of n_contrib - n_blended).
+    One extra forward launch with the n_blended output, outside any timed
+    region, on the step's current workspaces."""
+    if getattr(st, "_pairs", None) is not None:
+        return st._pairs
+    torch = st.torch
+    outs = dict(st.outs)
+    outs["n_blended"] = torch.empty_like(st.outs["n_contrib"])
+    st.raster.render_fwd(st.plan, st.cfg, st.pre_ws, st.sort_ws, outs)
+    blended = int(outs["n_blended"].to(torch.int64).sum().item())
+    evals = int(st.outs["n_contrib"].to(torch.int64).sum().item())
+    st._pairs = {"blended": blended, "skipped": evals - blended, "evaluated": evals}
+    return st._pairs
 
 
 def run_ours(args, rank, world):
@@ -700,35 +719,125 @@ def run_dense(args, iters: int = 3) -> dict:
 
 
 # ---------------------------------------------------------------- oracle arm
-def oracle_sample_step(scene, cam, pix):
-    """fwd+bwd of the float64 oracle for the listed pixels of one view."""
+def oracle_view_setup(scene, cam) -> dict:
+    """The oracle's per-view work that does not depend on the pixels: the
+    projection of every Gaussian (no gradient) and the tile lists (exact
+    support, oracle.binning.tile_lists).  Timed."""
+    import torch
+    from oracle import binning as OB, project as OP
+    t0 = time.perf_counter()
+    with torch.no_grad():
+        pr = OP.project(scene.means, scene.scales, scene.rotations, scene.opacities, scene.sh,
+                        scene.sh_degree, cam)
+    gg, tt, _, _, _ = OB.tile_lists(pr["mean2d"].numpy(), pr["conic"].numpy(), pr["opacity"].numpy(),
+                                     pr["valid"].numpy(), cam.width, cam.height)
+    tx, ty = OB.tile_grid(cam.width, cam.height)
+    order = np.argsort(tt, kind="stable")
+    starts = np.searchsorted(tt[order], np.arange(tx * ty + 1))
+    return {"gauss": gg[order], "starts": starts, "tiles": tx * ty, "tiles_x": tx,
+            "seconds": time.perf_counter() - t0}
+
+
+def oracle_tiles_step(scene, cam, setup: dict, tiles) -> tuple[int, float]:
+    """float64 oracle fwd+bwd (colour, d^mid, I_i, S_i and the gradients of
+    a loss on the colour) of every pixel of the given tiles of one view,
+    each tile composited over the Gaussians its list holds.  Returns
+    (pixels, seconds)."""
     import torch
     from oracle import project as OP, render as OR
-    params = [torch.tensor(np.asarray(a, np.float64), requires_grad=True)
+    t0 = time.perf_counter()
+    lists = [setup["gauss"][setup["starts"][k]: setup["starts"][k + 1]] for k in tiles]
+    sel = np.unique(np.concatenate(lists)) if lists else np.zeros(0, np.int64)
+    params = [torch.tensor(np.asarray(a[sel], np.float64), requires_grad=True)
               for a in (scene.means, scene.scales, scene.rotations, scene.opacities, scene.sh)]
     pr = OP.project(*params, scene.sh_degree, cam)
-    out = OR.render_view(pr, cam, pix=pix, want_depth=True)
-    out["colour"].sum().backward()
-    return len(pix)
+    loss, pixels = 0.0, 0
+    for k, lst in zip(tiles, lists):
+        ty, tx = divmod(int(k), setup["tiles_x"])
+        uu, vv = np.meshgrid(np.arange(16 * tx, min(16 * tx + 16, cam.width)),
+                             np.arange(16 * ty, min(16 * ty + 16, cam.height)))
+        pix = np.stack([uu.reshape(-1), vv.reshape(-1)], 1)
+        view = dict(pr)
+        view["valid"] = pr["valid"] & torch.as_tensor(np.isin(sel, lst))
+        out = OR.render_view(view, cam, pix=pix, want_depth=True)
+        loss = loss + out["colour"].sum()
+        pixels += len(pix)
+    if pixels and isinstance(loss, torch.Tensor) and loss.requires_grad:
+        loss.backward()
+    return pixels, time.perf_counter() - t0
 
 
-def cpu_baseline(scene, cams, pixels_per_view=4, views=(0,)) -> dict:
-    import torch
-    rng = np.random.default_rng(11)
-    t0 = time.perf_counter()
-    done = 0
+def oracle_sample(scene, cams, views, tiles_per_view: int, seed: int) -> dict:
+    """Oracle fwd+bwd throughput on a tile sample of the batched workload:
+    per view, the projection and binning of all Gaussians, then
+    `tiles_per_view` tiles drawn uniformly (seeded).  The per-view work is
+    charged by the sampled share of the view's tiles, so the rate is that of
+    the oracle rendering whole views."""
+    rng = np.random.default_rng(seed)
+    pixels, charged, wall0 = 0, 0.0, time.perf_counter()
     for v in views:
         cam = cams[v]
-        pix = np.stack([rng.integers(0, cam.width, pixels_per_view),
-                        rng.integers(0, cam.height, pixels_per_view)], 1)
-        done += oracle_sample_step(scene, cam, pix)
-    sec = time.perf_counter() - t0
-    return {"value": done / sec / 1e6, "unit": "Mpix/s", "cores": torch.get_num_threads(), "kind": "oracle",
-            "sample": f"float64 oracle fwd+bwd of {done} random pixels of view {list(views)} over all "
-                      f"{scene.n} Gaussians (projection of every Gaussian included), {sec:.1f} s"}
+        su = oracle_view_setup(scene, cam)
+        tiles = rng.choice(su["tiles"], size=min(tiles_per_view, su["tiles"]), replace=False)
+        p, sec = oracle_tiles_step(scene, cam, su, tiles)
+        pixels += p
+        charged += sec + su["seconds"] * len(tiles) / su["tiles"]
+    return {"pixels": pixels, "charged_seconds": charged, "wall_seconds": time.perf_counter() - wall0}
+
+
+def oracle_full_frame(threads: int | None, backward: bool) -> float:
+    """Seconds of the oracle on one full frame of the 1,024-Gaussian 128x128
+    scene (SH 0), forward (colour, d^mid, I_i, S_i) or forward + backward,
+    on `threads` host threads (None: torch's default)."""
+    import torch
+    from oracle import project as OP, render as OR
+    from paper_2411_12788_gb300 import scenes
+    sc = scenes.box_scene(1024, seed=0, sh_degree=0)
+    cam = scenes.origin_camera()
+    old = torch.get_num_threads()
+    if threads:
+        torch.set_num_threads(threads)
+    try:
+        t0 = time.perf_counter()
+        params = [torch.tensor(np.asarray(a, np.float64), requires_grad=backward)
+                  for a in (sc.means, sc.scales, sc.rotations, sc.opacities, sc.sh)]
+        with torch.set_grad_enabled(backward):
+            pr = OP.project(*params, sc.sh_degree, cam)
+            out = OR.render_view(pr, cam, want_depth=True)
+            if backward:
+                out["colour"].sum().backward()
+        return time.perf_counter() - t0
+    finally:
+        torch.set_num_threads(old)
+
+
+def cpu_baseline(scene, cams, tiles_per_view: int = 16, views=(0,)) -> dict:
+    """The float64 oracle, as it stands, on the host cores: fwd+bwd Mpix/s on
+    a tile sample of the batched workload (the line's metric), plus full
+    frames of the small 1,024-Gaussian scene (forward and fwd+bwd on all
+    threads, forward on one thread)."""
+    import torch
+    s = oracle_sample(scene, cams, views, tiles_per_view, seed=11)
+    px0 = 128 * 128
+    f_all = oracle_full_frame(None, False)
+    fb_all = oracle_full_frame(None, True)
+    f_one = oracle_full_frame(1, False)
+    return {"value": s["pixels"] / s["charged_seconds"] / 1e6, "unit": "Mpix/s", "cores": torch.get_num_threads(),
+            "kind": "oracle",
+            "sample": (f"float64 oracle fwd+bwd of {tiles_per_view} random 16x16 tiles of view(s) {list(views)} of "
+                       f"the {scene.n}-Gaussian 8-view workload ({s['pixels']} pixels, each tile over its list); the "
+                       f"per-view projection and binning of all Gaussians charged by the sampled share of the "
+                       f"view's tiles; {s['wall_seconds']:.1f} s wall"),
+            "full_frame_1024_gaussians_128x128": {
+                "fwd_mpix_s_all_threads": px0 / f_all / 1e6, "fwd_bwd_mpix_s_all_threads": px0 / fb_all / 1e6,
+                "fwd_mpix_s_one_thread": px0 / f_one / 1e6, "threads": torch.get_num_threads()}}
 
 
 def run_reference(args, rank, world):
+    """The oracle on the line's workload: each step is fwd+bwd of 8 random
+    tiles of one view (round robin over the 8 views), each view's projection
+    and binning computed once and charged by the sampled share of its
+    tiles."""
     from paper_2411_12788_gb300 import scenes
     if rank != 0:
         return None
@@ -736,25 +845,34 @@ def run_reference(args, rank, world):
     scene = scenes.cluster_scene(args.n, 64, seed=0, sh_degree=3)
     cams = scenes.multiview_cameras()
     rng = np.random.default_rng(11)
-    per_step = 2
+    per_step = 8
+    setups = {}
 
     def one(k):
-        cam = cams[k % len(cams)]
-        pix = np.stack([rng.integers(0, cam.width, per_step), rng.integers(0, cam.height, per_step)], 1)
-        return oracle_sample_step(scene, cam, pix)
+        v = k % len(cams)
+        if v not in setups:
+            setups[v] = oracle_view_setup(scene, cams[v])
+        su = setups[v]
+        tiles = rng.choice(su["tiles"], size=per_step, replace=False)
+        p, sec = oracle_tiles_step(scene, cams[v], su, tiles)
+        return p, sec + su["seconds"] * per_step / su["tiles"]
     for k in range(args.warmup):
         one(k)
+    done, charged = 0, 0.0
     t0 = time.perf_counter()
-    done = 0
     for k in range(args.steps):
-        done += one(k)
-    sec = time.perf_counter() - t0
-    value = done / sec / 1e6
+        p, sec = one(args.warmup + k)
+        done += p
+        charged += sec
+    wall = time.perf_counter() - t0
+    value = done / charged / 1e6
     cpu = {"value": value, "unit": "Mpix/s", "cores": torch.get_num_threads(), "kind": "oracle",
-           "sample": f"each step: float64 oracle fwd+bwd of {per_step} random pixels of one view (round robin "
-                     f"over the 8 views) over all {args.n} Gaussians"}
+           "sample": f"each step: float64 oracle fwd+bwd of {per_step} random 16x16 tiles of one view (round robin "
+                     f"over the 8 views) of the {args.n}-Gaussian workload, each tile over its list; each view's "
+                     f"projection and binning of all Gaussians (once per view) charged by the sampled share of "
+                     f"its tiles; {wall:.1f} s wall for the timed steps"}
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3 / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": charged * 1e3 / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": WORKLOAD, "gaussians": args.n},
             "cpu_baseline": cpu,
