@@ -432,7 +432,11 @@ struct BwdEntry {
   float mx, my;        // centre
   float4 ex;           // exponent form
   float3 col;
-  float acc[9];        // d(centre x, y), d(a2, b2, c2), d log2 o, d colour
+  // sums over the pixels, with de = dL/de / ln 2 (the factor is applied at
+  // the flush): de dx, de dy (the centre's gradient follows from them and
+  // the entry's a2, b2, c2), de dx^2, de dx dy, de dy^2 (d a2, b2, c2), de
+  // (d log2 o), w dL/dI (d colour)
+  float acc[9];
   float wsum;          // blending weight over the warp's pixels (I_i)
   uint32_t wfix;       // the same, each pixel's weight rounded to a multiple of 2^-24
 };
@@ -464,24 +468,32 @@ __device__ __forceinline__ void bwd_entry_accumulate(BwdEntry& E, const float4& 
   E.acc[8] = fmaf(w, pg.z, E.acc[8]);
   if (araw <= alpha_max) {
     const float dal = fmaf(Tl, cg, -(pg.w - Fl) * rcp_approx(1.f - a));
-    const float de = dal * a * kLn2;          // dL/de
+    const float de = dal * a;                 // dL/de / ln 2
     const float dedx = de * dx, dedy = de * dy;
-    E.acc[5] += de;                           // d log2 o
-    E.acc[2] = fmaf(dedx, dx, E.acc[2]);      // d a2
-    E.acc[3] = fmaf(dedx, dy, E.acc[3]);      // d b2
-    E.acc[4] = fmaf(dedy, dy, E.acc[4]);      // d c2
-    // d = pixel - centre: de/dcentre = -(2 a2 dx + b2 dy, b2 dx + 2 c2 dy)
-    E.acc[0] = fmaf(-2.f * E.ex.x, dedx, fmaf(-E.ex.y, dedy, E.acc[0]));
-    E.acc[1] = fmaf(-E.ex.y, dedx, fmaf(-2.f * E.ex.z, dedy, E.acc[1]));
+    E.acc[5] += de;                           // log2 o
+    E.acc[2] = fmaf(dedx, dx, E.acc[2]);      // a2
+    E.acc[3] = fmaf(dedx, dy, E.acc[3]);      // b2
+    E.acc[4] = fmaf(dedy, dy, E.acc[4]);      // c2
+    E.acc[0] += dedx;                         // centre, via the flush
+    E.acc[1] += dedy;
   }
 }
 
 template <bool kFix>
 __device__ __forceinline__ void bwd_entry_flush(const BwdEntry& E, float (*s_g)[kRenderThreads], float* s_wsum,
                                                 uint32_t* s_wfix, int idx, bool want_w) {
+  // d = pixel - centre, so de/dcentre = -(2 a2 dx + b2 dy, b2 dx + 2 c2 dy);
+  // every exponent term carries the factor ln 2 left out per pixel
+  float g[9];
+  g[0] = -kLn2 * fmaf(2.f * E.ex.x, E.acc[0], E.ex.y * E.acc[1]);
+  g[1] = -kLn2 * fmaf(E.ex.y, E.acc[0], 2.f * E.ex.z * E.acc[1]);
+#pragma unroll
+  for (int k = 2; k < 6; ++k) g[k] = kLn2 * E.acc[k];
+#pragma unroll
+  for (int k = 6; k < 9; ++k) g[k] = E.acc[k];
 #pragma unroll
   for (int k = 0; k < 9; ++k)
-    if (E.acc[k] != 0.f) atomicAdd(&s_g[k][idx], E.acc[k]);
+    if (g[k] != 0.f) atomicAdd(&s_g[k][idx], g[k]);
   if (want_w && E.wsum != 0.f) atomicAdd(&s_wsum[idx], E.wsum);
   if (kFix && E.wfix) atomicAdd(&s_wfix[idx], E.wfix);
 }
