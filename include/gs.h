@@ -129,7 +129,8 @@ typedef struct gs_plan {
   int32_t n_views;
   int32_t total_tiles;
   int32_t sort_bits;        /* bits of the global tile id */
-  int32_t reserved;
+  int32_t n_pairs;          /* set by gs_preprocess: (item, tile row) pairs of the visible items'
+                               row bands (sizes the tile-list builder of gs_bin_sort) */
   gs_camera cams[GS_MAX_VIEWS];
   int32_t tile_base[GS_MAX_VIEWS + 1];
   int64_t pixel_base[GS_MAX_VIEWS + 1];
@@ -449,13 +450,19 @@ typedef struct gs_preprocess_view {
   const uint32_t* tiles;        /* [n_items] touched-tile count, 0 if culled */
   const uint32_t* rect;         /* [n_items][2] (tx0 | ty0 << 16, tx1 | ty1 << 16) */
   const uint32_t* sorted_items; /* [n_items] items in (float32 z, item) order, culled last */
-  const uint32_t* offsets;      /* [n_items] exclusive scan of tiles in that order */
+  const uint32_t* offsets;      /* [n_items] exclusive scan of tiles in that order (written when
+                                   gs_bin_sort sorts the entries by tile id, and by
+                                   gs_bin_sort_noalloc) */
+  const uint32_t* pair_offsets; /* [n_items] exclusive scan of the band sizes (tile rows ty1 - ty0
+                                   + 1 of the visible items) in that order (written when
+                                   gs_bin_sort builds the lists from (item, tile row) pairs) */
 } gs_preprocess_view;
 gs_status gs_inspect_preprocess(const gs_plan* plan, const void* pre_ws, gs_preprocess_view* out);
 
 /* Device pointers into a sort workspace after gs_bin_sort. */
 typedef struct gs_sort_view {
-  const uint32_t* tile_ids;     /* [n_entries] global tile id, ascending */
+  const uint32_t* tile_ids;     /* [n_entries] global tile id, ascending; NULL when the lists were
+                                   built from (item, tile row) pairs (the ranges give the tiles) */
   const uint32_t* items;        /* [n_entries] item of each entry */
   const uint32_t* ranges;       /* [total_tiles][2] [start, end) of each tile */
 } gs_sort_view;

@@ -52,7 +52,7 @@ class Scene(C.Structure):
 class Plan(C.Structure):
     _fields_ = [("n", C.c_int64), ("n_items", C.c_int64), ("total_pixels", C.c_int64),
                 ("n_entries", C.c_int64), ("n_views", C.c_int32), ("total_tiles", C.c_int32),
-                ("sort_bits", C.c_int32), ("reserved", C.c_int32),
+                ("sort_bits", C.c_int32), ("n_pairs", C.c_int32),
                 ("cams", Camera * GS_MAX_VIEWS), ("tile_base", C.c_int32 * (GS_MAX_VIEWS + 1)),
                 ("pixel_base", C.c_int64 * (GS_MAX_VIEWS + 1))]
 
@@ -79,7 +79,7 @@ class Grads(C.Structure):
 class PreprocessView(C.Structure):
     _fields_ = [("xy_tau_z", C.c_void_p), ("conic_o", C.c_void_p), ("rgb", C.c_void_p),
                 ("tiles", C.c_void_p), ("rect", C.c_void_p), ("sorted_items", C.c_void_p),
-                ("offsets", C.c_void_p)]
+                ("offsets", C.c_void_p), ("pair_offsets", C.c_void_p)]
 
 
 class SortView(C.Structure):

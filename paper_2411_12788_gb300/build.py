@@ -26,7 +26,8 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libgs.so")
 BUILD_CHECKED = os.path.join(HERE, "_build_checked")
 LIB_CHECKED = os.path.join(HERE, "libgs_checked.so")
-SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "binning.cu", "render.cu", "timing.cu", "noalloc.cu", "select.cu", "ssim.cu"]
+SOURCES = ["api.cu", "preprocess.cu", "sort.cu", "binning.cu", "lists.cu", "render.cu", "timing.cu", "noalloc.cu",
+           "select.cu", "ssim.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "-I", os.path.join(ROOT, "include")]

@@ -28,13 +28,14 @@ __global__ void set_views_kernel(const ViewTable t, int n_views, ViewDev* __rest
                                  uint32_t* __restrict__ status) {
   const int i = threadIdx.x;
   if (i < n_views) dst[i] = t.v[i];
-  if (i < 4) status[i] = 0u;
+  if (i < 8) status[i] = 0u;
 }
 
-// Copies the status word and the entry count (16 bytes) into mapped host
-// memory: the read-back then needs only the stream synchronisation.
+// Copies the status word, the entry count and the pair count (24 bytes) into
+// mapped host memory: the read-back then needs only the stream
+// synchronisation.
 __global__ void copy_head_kernel(const uint64_t* __restrict__ src, volatile uint64_t* dst) {
-  if (threadIdx.x < 2) dst[threadIdx.x] = src[threadIdx.x];
+  if (threadIdx.x < 3) dst[threadIdx.x] = src[threadIdx.x];
 }
 
 // bits[v][g / 32] bit g % 32 = (mask[v * n + g] != 0); one ballot per 32
@@ -58,7 +59,7 @@ cudaError_t host_head(HostHead** out) {
   thread_local HostHead hh;
   if (!hh.host) {
     void* p = nullptr;
-    cudaError_t e = cudaHostAlloc(&p, 16, cudaHostAllocMapped | cudaHostAllocPortable);
+    cudaError_t e = cudaHostAlloc(&p, 32, cudaHostAllocMapped | cudaHostAllocPortable);
     if (e != cudaSuccess) return e;
     void* dp = nullptr;
     e = cudaHostGetDevicePointer(&dp, p, 0);
@@ -83,7 +84,7 @@ PreLayout pre_layout(const gs_plan& p) {
     return at;
   };
   L.views = take(sizeof(ViewDev) * GS_MAX_VIEWS);
-  L.status = take(16);          // status word (u32) then n_entries (u64) at +8
+  L.status = take(32);          // status word (u32), n_entries (u64) at +8, n_pairs (u64) at +16
   L.n_entries = L.status + 8;
   L.xy_tau_z = take(16 * m);
   L.conic_o = take(16 * m);
@@ -92,12 +93,14 @@ PreLayout pre_layout(const gs_plan& p) {
   L.rect = take(8 * m);
   L.bin = take(32 * m);
   L.tiles = take(4 * m);
+  L.band_rows = take(4 * m);
   L.depth_key = take(4 * m);
   L.sort_keys_alt = take(4 * m);
   L.sort_vals = take(4 * m);
   L.sort_vals_alt = take(4 * m);
   L.sorted_items = L.sort_vals;
   L.offsets = take(4 * m);
+  L.pair_offsets = take(4 * m);
   L.scan_blocks = take(scan_block_bytes((int64_t)m));
   L.radix_scratch = take(radix_scratch_bytes((int64_t)m, 32));
   L.grad2d = take(48 * m);
@@ -105,8 +108,29 @@ PreLayout pre_layout(const gs_plan& p) {
   return L;
 }
 
+// Global tile rows of the plan and the widest view (tiles across).
+void plan_rows(const gs_plan& p, int* rows, int* max_tx) {
+  int64_t r = 0;
+  int mx = 0;
+  for (int v = 0; v < p.n_views; ++v) {
+    r += ceil_div(p.cams[v].height, kTile);
+    mx = std::max(mx, ceil_div(p.cams[v].width, kTile));
+  }
+  *rows = (int)std::min<int64_t>(r, INT32_MAX);
+  *max_tx = mx;
+}
+
+// Whether gs_bin_sort builds the tile lists by the pair sort (lists.cu):
+// the global tile rows and the tiles across every view fit the pair key.
+bool lists_path(const gs_plan& p) {
+  int rows = 0, max_tx = 0;
+  plan_rows(p, &rows, &max_tx);
+  return rows <= kListRowsMax && max_tx <= kListTxMax;
+}
+
 SortLayout sort_layout(const gs_plan& p) {
   SortLayout L;
+  memset(&L, 0, sizeof(L));
   const size_t e = (size_t)std::max<int64_t>(p.n_entries, 1);
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -114,12 +138,35 @@ SortLayout sort_layout(const gs_plan& p) {
     o = align_up(o + bytes);
     return at;
   };
-  L.keys = take(4 * e);
-  L.keys_alt = take(4 * e);
+  int rows = 0, max_tx = 0;
+  plan_rows(p, &rows, &max_tx);
+  L.lists = lists_path(p);
   L.vals = take(4 * e);
-  L.vals_alt = take(4 * e);
   L.ranges = take(8 * (size_t)std::max(p.total_tiles, 1));
-  L.radix_scratch = take(radix_scratch_bytes((int64_t)e, std::max(p.sort_bits, 1)));
+  if (L.lists) {
+    const size_t np = (size_t)std::max<int32_t>(p.n_pairs, 1);
+    L.rows = rows;
+    L.counts2_n = (int64_t)((np + kListPairsPerChunk - 1) / kListPairsPerChunk) * max_tx + std::max(p.total_tiles, 1);
+    L.pkey = take(4 * np);
+    L.pkey_alt = take(4 * np);
+    L.pval = take(4 * np);
+    L.pval_alt = take(4 * np);
+    L.pair_radix = take(list_pair_radix_bytes((int64_t)np));
+    L.row_T = take(4 * ((size_t)rows + 1));
+    L.row_start = take(4 * ((size_t)rows + 1));
+    L.c2_start = take(4 * ((size_t)rows + 1));
+    L.cnt2_off = take(4 * ((size_t)rows + 1));
+    L.counts2 = take(4 * (size_t)L.counts2_n);
+    L.prefix2 = take(4 * (size_t)L.counts2_n);
+    L.tile_count = take(4 * (size_t)std::max(p.total_tiles, 1));
+    L.tile_start = take(4 * (size_t)std::max(p.total_tiles, 1));
+    L.scan_blocks = take(scan_block_bytes(std::max(p.total_tiles, 1)) + 8);
+  } else {
+    L.keys = take(4 * e);
+    L.keys_alt = take(4 * e);
+    L.vals_alt = take(4 * e);
+    L.radix_scratch = take(radix_scratch_bytes((int64_t)e, std::max(p.sort_bits, 1)));
+  }
   L.total = o;
   return L;
 }
@@ -146,6 +193,8 @@ ItemState item_state(void* ws, const PreLayout& L) {
   s.depth_val = at<uint32_t>(ws, L.sort_vals);
   s.status = at<uint32_t>(ws, L.status);
   s.n_entries = at<unsigned long long>(ws, L.n_entries);
+  s.entries_acc = at<unsigned long long>(ws, L.n_entries);
+  s.band_rows = at<uint32_t>(ws, L.band_rows);
   return s;
 }
 
@@ -177,13 +226,16 @@ bool valid_plan(const gs_plan* p) {
 
 // Pointers into a preprocess workspace for another translation unit.
 void preprocess_parts(const gs_plan* plan, void* pre_ws, const ViewDev** views, ItemState* st,
-                      const uint32_t** sorted_items, const uint32_t** offsets, uint32_t** status) {
+                      const uint32_t** sorted_items, uint32_t** offsets, uint32_t** status, uint64_t** scan_blocks,
+                      unsigned long long** n_entries) {
   const PreLayout L = pre_layout(*plan);
   *views = at<ViewDev>(pre_ws, L.views);
   *st = item_state(pre_ws, L);
   *sorted_items = at<uint32_t>(pre_ws, L.sorted_items);
   *offsets = at<uint32_t>(pre_ws, L.offsets);
   *status = at<uint32_t>(pre_ws, L.status);
+  *scan_blocks = at<uint64_t>(pre_ws, L.scan_blocks);
+  *n_entries = at<unsigned long long>(pre_ws, L.n_entries);
 }
 
 int device_sm_count() {
@@ -267,6 +319,7 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
   ViewTable table;
   memset(&table, 0, sizeof(table));
   ViewDev* views = table.v;
+  int32_t row_base = 0;
   for (int v = 0; v < plan->n_views; ++v) {
     const gs_camera& c = plan->cams[v];
     ViewDev& V = views[v];
@@ -284,6 +337,8 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
     V.tiles_x = ceil_div(c.width, kTile);
     V.tiles_y = ceil_div(c.height, kTile);
     V.tile_base = plan->tile_base[v];
+    V.row_base = row_base;
+    row_base += V.tiles_y;
     V.pixel_base = plan->pixel_base[v];
   }
   HostHead* head = nullptr;
@@ -296,6 +351,7 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
   if (e != cudaSuccess) return GS_ERR_CUDA;
   if (plan->n_items == 0) {
     plan->n_entries = 0;
+    plan->n_pairs = 0;
     return cuda_status(cudaStreamSynchronize(stream));
   }
   const ItemState st = item_state(pre_ws, L);
@@ -305,21 +361,32 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
     e = radix_sort_pairs(st.depth_key, at<uint32_t>(pre_ws, L.sort_keys_alt), at<uint32_t>(pre_ws, L.sort_vals),
                          at<uint32_t>(pre_ws, L.sort_vals_alt), plan->n_items, 32,
                          at<void>(pre_ws, L.radix_scratch), status, stream, "depth");
-  if (e == cudaSuccess)
-    e = gather_exclusive_scan(st.tiles, at<uint32_t>(pre_ws, L.sorted_items), at<uint32_t>(pre_ws, L.offsets),
-                              plan->n_items, at<uint64_t>(pre_ws, L.scan_blocks),
-                              at<unsigned long long>(pre_ws, L.n_entries), stream);
+  // the tile-list builder needs the band sizes scanned in depth order (pair
+  // offsets, total n_pairs; the entry total comes from the preprocess's
+  // sums); the radix path the tile counts (entry offsets and total)
+  if (e == cudaSuccess) {
+    if (lists_path(*plan))
+      e = gather_exclusive_scan(st.band_rows, at<uint32_t>(pre_ws, L.sorted_items), at<uint32_t>(pre_ws, L.pair_offsets),
+                                plan->n_items, at<uint64_t>(pre_ws, L.scan_blocks),
+                                at<unsigned long long>(pre_ws, L.status + 16), stream);
+    else
+      e = gather_exclusive_scan(st.tiles, at<uint32_t>(pre_ws, L.sorted_items), at<uint32_t>(pre_ws, L.offsets),
+                                plan->n_items, at<uint64_t>(pre_ws, L.scan_blocks),
+                                at<unsigned long long>(pre_ws, L.n_entries), stream);
+  }
   if (e != cudaSuccess) return GS_ERR_CUDA;
   GS_TIMED("preprocess_readback", stream,
            (copy_head_kernel<<<1, 32, 0, stream>>>(at<uint64_t>(pre_ws, L.status), head->dev)));
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
-  const uint64_t h0 = head->host[0], h1 = head->host[1];
+  const uint64_t h0 = head->host[0], h1 = head->host[1], h2 = head->host[2];
   const uint32_t st_word = (uint32_t)(h0 & 0xffffffffu);
   if (st_word & kStatusTimeout) return GS_ERR_TIMEOUT;
   if (h1 >= ((uint64_t)1 << 30)) return GS_ERR_CAPACITY;    // entries beyond the sort's range
+  if (h2 >= ((uint64_t)1 << 31)) return GS_ERR_CAPACITY;    // pairs beyond the lists' 32-bit indices
   plan->n_entries = (int64_t)h1;
+  plan->n_pairs = (int32_t)h2;
   return GS_OK;
 }
 
@@ -335,6 +402,44 @@ gs_status gs_bin_sort(const gs_plan* plan, void* pre_ws, void* sort_ws, size_t s
   uint32_t* keys = at<uint32_t>(sort_ws, S.keys);
   uint32_t* vals = at<uint32_t>(sort_ws, S.vals);
   cudaError_t e = cudaSuccess;
+  if (S.lists) {
+    // tile lists by counting placement (lists.cu)
+    ListArgs a;
+    a.views = at<ViewDev>(pre_ws, L.views);
+    a.n_views = plan->n_views;
+    a.n = plan->n;
+    a.n_items = plan->n_items;
+    a.n_entries = plan->n_entries;
+    a.n_pairs = plan->n_pairs;
+    a.rows = S.rows;
+    a.total_tiles = plan->total_tiles;
+    int rows = 0, max_tx = 0;
+    plan_rows(*plan, &rows, &max_tx);
+    a.max_tx = max_tx;
+    a.counts2_n = S.counts2_n;
+    a.sorted_items = at<uint32_t>(pre_ws, L.sorted_items);
+    a.pair_offsets = at<uint32_t>(pre_ws, L.pair_offsets);
+    a.st = st;
+    a.vals = vals;
+    a.ranges = at<uint2>(sort_ws, S.ranges);
+    a.pkey = at<uint32_t>(sort_ws, S.pkey);
+    a.pkey_alt = at<uint32_t>(sort_ws, S.pkey_alt);
+    a.pval = at<uint32_t>(sort_ws, S.pval);
+    a.pval_alt = at<uint32_t>(sort_ws, S.pval_alt);
+    a.pair_radix = at<void>(sort_ws, S.pair_radix);
+    a.counts2 = at<int32_t>(sort_ws, S.counts2);
+    a.prefix2 = at<uint32_t>(sort_ws, S.prefix2);
+    a.row_T = at<uint32_t>(sort_ws, S.row_T);
+    a.row_start = at<uint32_t>(sort_ws, S.row_start);
+    a.c2_start = at<uint32_t>(sort_ws, S.c2_start);
+    a.cnt2_off = at<uint32_t>(sort_ws, S.cnt2_off);
+    a.tile_count = at<uint32_t>(sort_ws, S.tile_count);
+    a.tile_start = at<uint32_t>(sort_ws, S.tile_start);
+    a.scan_blocks = at<uint64_t>(sort_ws, S.scan_blocks);
+    a.scan_total = at<unsigned long long>(sort_ws, S.scan_blocks + scan_block_bytes(std::max(plan->total_tiles, 1)));
+    a.status = status;
+    return cuda_status(launch_lists(a, stream));
+  }
   if (plan->n_entries > 0) {
     e = launch_duplicate(at<ViewDev>(pre_ws, L.views), plan->n_views, plan->n_items, plan->n,
                          at<uint32_t>(pre_ws, L.sorted_items), at<uint32_t>(pre_ws, L.offsets), st, keys, vals,
@@ -459,13 +564,14 @@ gs_status gs_inspect_preprocess(const gs_plan* plan, const void* pre_ws, gs_prep
   out->rect = at<uint32_t>(pre_ws, L.rect);
   out->sorted_items = at<uint32_t>(pre_ws, L.sorted_items);
   out->offsets = at<uint32_t>(pre_ws, L.offsets);
+  out->pair_offsets = at<uint32_t>(pre_ws, L.pair_offsets);
   return GS_OK;
 }
 
 gs_status gs_inspect_sort(const gs_plan* plan, const void* sort_ws, gs_sort_view* out) {
   if (!valid_plan(plan) || plan->n_entries < 0 || !sort_ws || !out) return GS_ERR_INVALID_ARG;
   const SortLayout S = sort_layout(*plan);
-  out->tile_ids = at<uint32_t>(sort_ws, S.keys);
+  out->tile_ids = S.lists ? nullptr : at<uint32_t>(sort_ws, S.keys);   // the lists path stores no tile ids
   out->items = at<uint32_t>(sort_ws, S.vals);
   out->ranges = at<uint32_t>(sort_ws, S.ranges);
   return GS_OK;

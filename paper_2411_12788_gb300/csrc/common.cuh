@@ -40,7 +40,7 @@ struct ViewDev {
   float campos[3];           // camera centre -R^T t
   int32_t width, height, tiles_x, tiles_y;
   int32_t tile_base;
-  int32_t pad0;
+  int32_t row_base;          // first global tile row of the view (rows of all views concatenated)
   int64_t pixel_base;
 };
 
@@ -56,23 +56,34 @@ struct ItemState {
   uint32_t* depth_key;       // float bits of z, kCulledKey if culled
   uint32_t* depth_val;       // the item's own index: the depth sort's values
   uint32_t* status;          // device status word (kStatus* bits)
-  const unsigned long long* n_entries;   // tile entries, written by the scan
+  const unsigned long long* n_entries;   // tile entries (sum of tiles)
+  unsigned long long* entries_acc;       // the same word, summed by the preprocess with atomics
+  uint32_t* band_rows;       // tile rows of the item's band (ty1 - ty0 + 1; 0 = culled)
 };
 
 // Offsets of the preprocess workspace regions (bytes), host-computed.
 struct PreLayout {
   size_t views, status, n_entries;
-  size_t xy_tau_z, conic_o, rgb, depth_frame, rect, bin, tiles, depth_key;
+  size_t xy_tau_z, conic_o, rgb, depth_frame, rect, bin, tiles, band_rows, depth_key;
   size_t sort_keys_alt, sort_vals, sort_vals_alt;   // depth sort buffers
-  size_t sorted_items, offsets;                      // after the depth sort
+  size_t sorted_items, offsets, pair_offsets;        // after the depth sort: scanned tiles / band sizes
   size_t scan_blocks;
   size_t radix_scratch;                              // histograms + look-back
   size_t grad2d;                                     // 3 x float4 per item
   size_t total;
 };
 
+// Sort workspace.  Two layouts: the counting-placement tile lists (lists.cu,
+// `lists` true: vals, ranges and the lists' scratch) and the radix path
+// (duplicate + onesweep sort by tile id: keys, alternates, radix scratch).
 struct SortLayout {
-  size_t keys, keys_alt, vals, vals_alt, ranges, radix_scratch, total;
+  bool lists;
+  size_t keys, keys_alt, vals, vals_alt, ranges, radix_scratch;
+  size_t pkey, pkey_alt, pval, pval_alt, pair_radix, row_T, row_start, c2_start, cnt2_off, counts2, prefix2,
+      tile_count, tile_start, scan_blocks;
+  int rows;
+  int64_t counts2_n;
+  size_t total;
 };
 
 inline size_t align_up(size_t x, size_t a = 256) { return (x + a - 1) / a * a; }
@@ -141,8 +152,9 @@ constexpr int kSortItemsPerThread = 15;
 constexpr int kSortTile = kSortThreads * kSortItemsPerThread;   // keys per CTA tile
 
 size_t radix_scratch_bytes(int64_t n, int bits);
-// Stable LSD sort of (key, value) pairs over bits [0, bits); the result ends
-// up in (keys, vals) (the alt buffers are scratch).  `status` receives
+// Stable LSD sort of (key, value) pairs over bits [0, bits) (higher key bits
+// are carried along, not sorted); the result ends up in (keys, vals) (the alt
+// buffers are scratch).  `status` receives
 // kStatusTimeout if a look-back spin ran out.
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                              int64_t n, int bits, void* scratch, uint32_t* status,
@@ -193,6 +205,34 @@ cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int 
                               const uint32_t* vals, const ItemState& st, const gs_config& cfg,
                               const float* dL_dimage, const float* image, const uint32_t* n_contrib,
                               float4* grad2d, float* weight_sum, uint64_t* weight_sum_fixed, cudaStream_t stream);
+// ---- tile lists by counting placement (lists.cu) ----------------------------
+constexpr int kListRowsMax = 4096;        // global tile rows (all views) the lists path handles
+constexpr int kListTxMax = 1023;          // tiles per row
+constexpr int kListPairsPerChunk = 1024;  // (item, row) pairs per second-level chunk
+constexpr uint32_t kListEmpty = 0xFFFFFFFFu;   // a pair whose row has no tile in the image
+struct ListArgs {
+  const ViewDev* views;     // device
+  int n_views;
+  int64_t n, n_items, n_entries, n_pairs;
+  int rows, total_tiles, max_tx;
+  int64_t counts2_n;        // second-level counters allocated
+  const uint32_t* sorted_items;
+  const uint32_t* pair_offsets;   // scanned band sizes in depth order (the preprocess's offsets array)
+  ItemState st;
+  uint32_t* vals;           // [n_entries] items in tile order (the output)
+  uint2* ranges;            // [total_tiles] (the output)
+  uint32_t *pkey, *pkey_alt, *pval, *pval_alt;   // pairs and the radix sort's alternates
+  void* pair_radix;         // radix scratch for n_pairs keys over the row bits
+  int32_t* counts2;         // per second-level chunk, entries per column
+  uint32_t* prefix2;        // the same, exclusive over the row's chunks
+  uint32_t *row_T, *row_start, *c2_start, *cnt2_off, *tile_count, *tile_start;
+  uint64_t* scan_blocks;
+  unsigned long long* scan_total;
+  uint32_t* status;
+};
+size_t list_pair_radix_bytes(int64_t pairs);
+cudaError_t launch_lists(const ListArgs& a, cudaStream_t stream);
+
 cudaError_t launch_loss_l1(const float* image, const float* target, int64_t count, float* loss, float* dL,
                            cudaStream_t stream);
 

@@ -28,7 +28,8 @@
 namespace gs {
 
 void preprocess_parts(const gs_plan* plan, void* pre_ws, const ViewDev** views, ItemState* st,
-                      const uint32_t** sorted_items, const uint32_t** offsets, uint32_t** status);
+                      const uint32_t** sorted_items, uint32_t** offsets, uint32_t** status, uint64_t** scan_blocks,
+                      unsigned long long** n_entries);
 
 namespace {
 
@@ -86,12 +87,18 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_plan* plan, void* pre_ws, uint
 
   const ViewDev* views;
   ItemState st;
-  const uint32_t *sorted_items, *offsets;
-  uint32_t* status;
-  preprocess_parts(plan, pre_ws, &views, &st, &sorted_items, &offsets, &status);
+  const uint32_t* sorted_items;
+  uint32_t *offsets, *status;
+  uint64_t* scan_blocks;
+  unsigned long long* n_entries;
+  preprocess_parts(plan, pre_ws, &views, &st, &sorted_items, &offsets, &status, &scan_blocks, &n_entries);
   cudaError_t e = cudaSuccess;
   if (plan->n_entries > 0) {
-    e = launch_duplicate(views, plan->n_views, plan->n_items, plan->n, sorted_items, offsets, st, tile_ids, items,
+    // the entry offsets of the depth order (the preprocess may have scanned
+    // the band sizes instead, for the tile-list builder of gs_bin_sort)
+    e = gather_exclusive_scan(st.tiles, sorted_items, offsets, plan->n_items, scan_blocks, n_entries, stream);
+    if (e == cudaSuccess)
+      e = launch_duplicate(views, plan->n_views, plan->n_items, plan->n, sorted_items, offsets, st, tile_ids, items,
                          status, stream);
     // radix_sort_pairs clears the histogram, counter and look-back region first
     if (e == cudaSuccess)

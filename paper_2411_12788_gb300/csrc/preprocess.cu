@@ -75,6 +75,7 @@ __device__ __forceinline__ void sh_dot_rows(const float* row, const float* Y, fl
 
 __device__ __forceinline__ void cull(const ItemState& st, int64_t item) {
   st.tiles[item] = 0u;
+  st.band_rows[item] = 0u;
   st.depth_key[item] = kCulledKey;
   st.depth_val[item] = (uint32_t)item;
 }
@@ -102,6 +103,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
   const float tau = 2.f * logf(o / P.alpha_min);
   const float* shc = s_sh + threadIdx.x * row;     // coefficient k, channel c at [3k + c]
   const float lp = P.lowpass;
+  uint32_t entries = 0;                            // touched tiles of this Gaussian's items
 
   for (int v = 0; v < P.n_views; ++v) {
     const ViewDev& V = P.views[v];
@@ -200,10 +202,12 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
     if (!THREE_SIGMA) lmax = eig_max();
     const float kappa = lmax * lmax / det;
     P.st.tiles[item] = count;
+    P.st.band_rows[item] = count ? (uint32_t)(ty1 - ty0 + 1) : 0u;
     P.st.depth_key[item] = count ? __float_as_uint(pc.z) : kCulledKey;
     P.st.depth_val[item] = (uint32_t)item;
     if (!count) continue;
     P.st.rect[item] = make_uint2((uint32_t)ty0 << 16, (uint32_t)(V.tiles_x - 1) | ((uint32_t)ty1 << 16));
+    entries += count;
     P.st.xy_tau_z[item] = make_float4(b.mx, b.my, b.tau, pc.z);
     P.st.conic_o[item] = make_float4(A, B, C, o);
     P.st.bin[2 * item] = make_float4(b.k, b.sc, b.isyy, b.h);
@@ -246,6 +250,10 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
     df[1] = make_float4(W[3], W[4], W[5], e1);
     df[2] = make_float4(W[6], W[7], W[8], e2);
   }
+  // the entry total, summed per warp
+  const uint32_t am = __activemask();
+  const uint32_t we = __reduce_add_sync(am, entries);
+  if ((int)(threadIdx.x & 31) == __ffs(am) - 1 && we) atomicAdd(P.st.entries_acc, (unsigned long long)we);
 }
 
 // ---- backward ------------------------------------------------------------

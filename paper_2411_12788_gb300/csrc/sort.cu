@@ -56,6 +56,12 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
+// Digit mask of the pass starting at bit `shift` of a sort over bits [0, bits):
+// the key bits above `bits` ride along unsorted.
+__host__ __device__ inline uint32_t digit_mask(int bits, int shift) {
+  return bits - shift >= kRadixBits ? (uint32_t)(kRadix - 1) : (1u << (bits - shift)) - 1u;
+}
+
 // Counts the digits of every pass in one read of the keys.  Each thread
 // takes 8 consecutive keys and adds runs of equal digits with one shared
 // atomic per run, which keeps nearly-sorted inputs (long runs of one high
@@ -63,7 +69,7 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
 constexpr int kHistKeys = 8;
 
 __global__ void __launch_bounds__(256) radix_histogram_kernel(const uint32_t* __restrict__ keys, int64_t n,
-                                                              int passes, uint32_t* __restrict__ hist) {
+                                                              int passes, int bits, uint32_t* __restrict__ hist) {
   __shared__ uint32_t sh[kMaxPasses * kRadix];
   for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) sh[i] = 0;
   __syncthreads();
@@ -81,11 +87,12 @@ __global__ void __launch_bounds__(256) radix_histogram_kernel(const uint32_t* __
     }
     for (int p = 0; p < passes; ++p) {
       const int sh_p = p * kRadixBits;
-      uint32_t cur = (k[0] >> sh_p) & (kRadix - 1), run = 1;
+      const uint32_t msk = digit_mask(bits, sh_p);
+      uint32_t cur = (k[0] >> sh_p) & msk, run = 1;
 #pragma unroll
       for (int j = 1; j < kHistKeys; ++j) {
         if (j >= cnt) break;
-        const uint32_t d = (k[j] >> sh_p) & (kRadix - 1);
+        const uint32_t d = (k[j] >> sh_p) & msk;
         if (d == cur) {
           ++run;
         } else {
@@ -178,7 +185,7 @@ constexpr long kCopyWaitLimit = 1L << 22;
 
 __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
-    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift,
+    uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift, uint32_t dmask,
     const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ counter,
     uint32_t* __restrict__ lookback, uint32_t* __restrict__ status) {
   extern __shared__ __align__(16) uint32_t s_dyn[];
@@ -248,7 +255,7 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
   for (int k = 0; k < kSortItemsPerThread; ++k) {
     const int i = warp_start + k * 32 + lane;
     const bool valid = i < count;
-    const uint32_t d = (key[k] >> shift) & (kRadix - 1);
+    const uint32_t d = (key[k] >> shift) & dmask;
     // diff: the lanes whose digit differs from this lane's (or that hold no
     // key); a bit's ballot XOR this lane's bit replicated marks them
     uint32_t diff = ~__ballot_sync(0xffffffffu, valid);
@@ -323,7 +330,7 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
   for (int k = 0; k < kSortItemsPerThread; ++k) {
     const int i = warp_start + k * 32 + lane;
     if (i < count) {
-      const uint32_t d = (key[k] >> shift) & (kRadix - 1);
+      const uint32_t d = (key[k] >> shift) & dmask;
       const uint32_t pos = s_cta_start[d] + s_warp_hist[warp][d] + rank[k];
       if (GS_IN_RANGE(pos, count, status)) {
         s_keys[pos] = key[k];
@@ -346,7 +353,7 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
   // 6. write out: runs of equal digits are contiguous in the output
   for (int i = tid; i < count; i += kSortThreads) {
     const uint32_t k = s_keys[i];
-    const uint32_t d = (k >> shift) & (kRadix - 1);
+    const uint32_t d = (k >> shift) & dmask;
     const uint32_t out = s_out_base[d] + (uint32_t)i;
     if (GS_IN_RANGE(out, n, status)) {
       keys_out[out] = k;
@@ -480,16 +487,16 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
   // passes keep 4 blocks per SM
   int hist_blocks = (int)std::min<int64_t>((int64_t)(passes <= 2 ? 8 : 4) * device_sm_count(),
                                           (n + 256 * kHistKeys - 1) / (256 * kHistKeys));
-  const bool depth = tag && tag[0] == 'd';
-  GS_TIMED(depth ? "depth_sort_histogram" : "tile_sort_histogram", stream,
-           (radix_histogram_kernel<<<hist_blocks, 256, 0, stream>>>(keys, n, passes, s.hist)));
-  GS_TIMED(depth ? "depth_sort_scan_hist" : "tile_sort_scan_hist", stream,
+  const bool depth = tag && tag[0] == 'd', pairs = tag && tag[0] == 'p';
+  GS_TIMED(depth ? "depth_sort_histogram" : pairs ? "pair_sort_histogram" : "tile_sort_histogram", stream,
+           (radix_histogram_kernel<<<hist_blocks, 256, 0, stream>>>(keys, n, passes, bits, s.hist)));
+  GS_TIMED(depth ? "depth_sort_scan_hist" : pairs ? "pair_sort_scan_hist" : "tile_sort_scan_hist", stream,
            (radix_scan_hist_kernel<<<passes, kRadix, 0, stream>>>(s.hist)));
   uint32_t *kin = keys, *kout = keys_alt, *vin = vals, *vout = vals_alt;
   for (int p = 0; p < passes; ++p) {
-    GS_TIMED(depth ? "depth_sort_onesweep" : "tile_sort_onesweep", stream,
+    GS_TIMED(depth ? "depth_sort_onesweep" : pairs ? "pair_sort_onesweep" : "tile_sort_onesweep", stream,
              (radix_onesweep_kernel<<<(unsigned)tiles, kSortThreads, kOnesweepDynSmem, stream>>>(
-                 kin, vin, kout, vout, n, p * kRadixBits,
+                 kin, vin, kout, vout, n, p * kRadixBits, digit_mask(bits, p * kRadixBits),
                  s.hist + p * kRadix, s.counters + p,
                  s.lookback + (size_t)p * tiles * kRadix, status)));
     std::swap(kin, kout);

@@ -297,7 +297,20 @@ def inspect_preprocess(fr: "Frame") -> dict:
             "tiles": sl(v.tiles, I, torch.int32),
             "rect": sl(v.rect, 2 * I, torch.int32).view(I, 2),
             "sorted_items": sl(v.sorted_items, I, torch.int32),
-            "offsets": sl(v.offsets, I, torch.int32)}
+            "offsets": sl(v.offsets, I, torch.int32),
+            "pair_offsets": sl(v.pair_offsets, I, torch.int32)}
+
+
+LIST_ROWS_MAX, LIST_TX_MAX = 4096, 1023
+
+
+def lists_path(plan) -> bool:
+    """Whether gs_bin_sort builds this plan's tile lists from (item, tile row)
+    pairs (all views' tile rows at most 4096, at most 1023 tiles across any
+    view) rather than by sorting the entries by tile id."""
+    rows = sum((int(plan.cams[v].height) + 15) // 16 for v in range(int(plan.n_views)))
+    tx = max((int(plan.cams[v].width) + 15) // 16 for v in range(int(plan.n_views)))
+    return rows <= LIST_ROWS_MAX and tx <= LIST_TX_MAX
 
 
 def inspect_sort(fr: "Frame") -> dict:
@@ -310,7 +323,15 @@ def inspect_sort(fr: "Frame") -> dict:
     def sl(ptr, count):
         off = ptr - base
         return fr.sort_ws[off: off + 4 * count].view(torch.int32).cpu()
-    return {"tile_ids": sl(v.tile_ids, E), "items": sl(v.items, E), "ranges": sl(v.ranges, 2 * K).view(K, 2)}
+    ranges = sl(v.ranges, 2 * K).view(K, 2)
+    if v.tile_ids:
+        tile_ids = sl(v.tile_ids, E)
+    else:
+        # the tile-list builder stores no tile id per entry: entry e belongs to
+        # the tile whose range holds it
+        lens = (ranges[:, 1] - ranges[:, 0]).to(torch.int64)
+        tile_ids = torch.repeat_interleave(torch.arange(K, dtype=torch.int32), lens)
+    return {"tile_ids": tile_ids, "items": sl(v.items, E), "ranges": ranges}
 
 
 # ---------------------------------------------------------------- outputs
@@ -441,3 +462,26 @@ class RasterSettings:
 
 def rasterize(means, scales, rotations, opacities, sh, settings: RasterSettings):
     return RasterizeGaussians.apply(means, scales, rotations, opacities, sh, settings)
+
+
+class L1Loss(torch.autograd.Function):
+    """mean |image - target| as a torch.autograd.Function over gs_loss_l1,
+    which computes the loss and its gradient in one kernel; the backward
+    scales the stored gradient by the incoming one."""
+
+    @staticmethod
+    def forward(ctx, image, target):
+        loss = torch.zeros(1, device=image.device)
+        dL = torch.empty_like(image)
+        loss_l1(image.detach().contiguous(), target.detach().contiguous(), loss, dL)
+        ctx.save_for_backward(dL)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (dL,) = ctx.saved_tensors
+        return dL * g, None
+
+
+def l1_loss(image, target):
+    return L1Loss.apply(image, target)
