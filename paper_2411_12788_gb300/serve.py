@@ -3,11 +3,15 @@
 Requests (a camera each, any resolution) arrive over time.  Whenever one of
 `streams` slots is free, the server takes the requests that have arrived, in
 arrival order, as long as they fit the memory budget for sort and tile
-buffers and the batch has at most `max_views` views, and renders them as one
-batch on that slot's CUDA stream: one gs_preprocess over all the batch's
-views, one shared gs_bin_sort (the view is part of the global tile id) and
-one gs_render_fwd launch over every tile of every view.  Batches on
-different slots overlap on the device.  Completion is stamped with a CUDA
+buffers and the batch has at most `max_views` views, and hands them to that
+slot's worker thread, which renders them as one batch on the slot's CUDA
+stream: one gs_preprocess over all the batch's views, one shared gs_bin_sort
+(the view is part of the global tile id) and one gs_render_fwd launch over
+every tile of every view.  The admission loop never waits for a launch: the
+preprocess's read-back of the entry count and the wait for completion block
+only the slot's worker (the library calls release the interpreter lock), so
+requests arriving meanwhile are admitted to the other slots at once.  Batches
+on different slots overlap on the device.  Completion is stamped with a CUDA
 event on the batch's stream, so latencies are device-accurate:
 latency = completion - arrival, queueing included.
 
@@ -29,6 +33,9 @@ from __future__ import annotations
 
 import gc
 import math
+import queue
+import sys
+import threading
 import time
 from dataclasses import dataclass, field
 
@@ -92,6 +99,7 @@ class RenderServer:
         self.peak_reserved = 0
         self.batches_run = 0
         self.views_run = 0
+        self._lock = threading.Lock()
 
     # -------------------------------------------------------------- memory
     @staticmethod
@@ -129,10 +137,9 @@ class RenderServer:
         return {name: buf[off: off + 4 * cnt].view(dt) for (name, cnt, dt), off in zip(layout, offs)}
 
     # -------------------------------------------------------------- one batch
-    def _launch(self, reqs: list, slot: int, bid: int) -> _Batch:
+    def _launch(self, reqs: list, slot: int, bid: int, est: int) -> _Batch:
         big = self.big_pixels is not None and sum(r.pixels for r in reqs) > self.big_pixels
         s = self.hi_streams[slot] if big else self.streams[slot]
-        est = sum(self._estimate(r.cam) for r in reqs)
         with torch.cuda.stream(s):
             cams = [r.cam for r in reqs]
             plan = raster.make_plan(self.g.n, cams)
@@ -149,75 +156,123 @@ class RenderServer:
             ev.record(s)
         actual = pre_ws.numel() + sort_ws.numel() + sum(t.numel() * t.element_size() for t in outs.values())
         tiles = sum(self._tiles(c) for c in cams)
-        if tiles:
-            self.ept = 0.8 * self.ept + 0.2 * (plan.n_entries / tiles)
-        self.reserved += actual - est               # correct the admission estimate
-        self.peak_reserved = max(self.peak_reserved, self.reserved)
+        with self._lock:
+            if tiles:
+                self.ept = 0.8 * self.ept + 0.2 * (plan.n_entries / tiles)
+            self.reserved += actual - est           # correct the admission estimate
+            self.peak_reserved = max(self.peak_reserved, self.reserved)
         return _Batch(bid, reqs, s, actual, ev, [])
 
     # -------------------------------------------------------------- the loop
     def serve(self, trace: list) -> list:
         """Serves `trace` (Requests sorted by arrival) in real time; returns it
         with `done` filled in.  Python's cyclic garbage collector is paused
-        for the duration (its sweeps stall the launch loop)."""
+        for the duration (its sweeps stall the launch loop), and the
+        interpreter's thread switch interval is shortened so that the slot
+        workers and the admission loop hand over quickly."""
         was = gc.isenabled()
+        interval = sys.getswitchinterval()
         gc.disable()
+        sys.setswitchinterval(2e-5)
         try:
             return self._serve(trace)
         finally:
+            sys.setswitchinterval(interval)
             if was:
                 gc.enable()
 
+    def _worker(self, slot: int, jobs: "queue.Queue", st: dict) -> None:
+        """One slot: launches each batch it is given (the preprocess's read-back
+        of the entry count blocks this thread only; the calls release the
+        interpreter lock), waits for the batch on the device, stamps its
+        requests and frees the slot."""
+        while True:
+            job = jobs.get()
+            if job is None:
+                return
+            reqs, bid, est = job
+            try:
+                b = self._launch(reqs, slot, bid, est)
+                b.event.synchronize()
+                done = st["t0_ev"].elapsed_time(b.event) / 1e3
+                for r in reqs:
+                    r.done = done
+                    r.batch = bid
+                with st["cv"]:
+                    self.reserved -= b.reserved
+                    st["free"].append(slot)
+                    st["inflight"] -= 1
+                    st["cv"].notify()
+            except BaseException as exc:         # handed to the admission loop
+                with st["cv"]:
+                    st["error"] = exc
+                    st["inflight"] -= 1
+                    st["free"].append(slot)
+                    st["cv"].notify()
+
     def _serve(self, trace: list) -> list:
         pending = list(trace)
-        queue: list = []
-        inflight: dict = {}
-        free_slots = list(range(self.n_slots))
+        queue_: list = []
+        cv = threading.Condition(self._lock)      # guards reserved, the free slots and the error
+        st = {"cv": cv, "free": list(range(self.n_slots)), "inflight": 0, "error": None}
+        jobs = [queue.Queue() for _ in range(self.n_slots)]
+        workers = [threading.Thread(target=self._worker, args=(k, jobs[k], st), daemon=True)
+                   for k in range(self.n_slots)]
+        for w in workers:
+            w.start()
         torch.cuda.synchronize()
-        t0_ev = torch.cuda.Event(enable_timing=True)
-        t0_ev.record(torch.cuda.current_stream())
+        st["t0_ev"] = torch.cuda.Event(enable_timing=True)
+        st["t0_ev"].record(torch.cuda.current_stream())
         t0 = time.perf_counter()
         bid = 0
-        while pending or queue or inflight:
-            now = time.perf_counter() - t0
-            while pending and pending[0].arrival <= now:
-                queue.append(pending.pop(0))
-            # retire finished batches
-            for slot, b in list(inflight.items()):
-                if b.event.query():
-                    done = t0_ev.elapsed_time(b.event) / 1e3
-                    for r in b.reqs:
-                        r.done = done
-                        r.batch = b.bid
-                    self.reserved -= b.reserved
-                    del inflight[slot]
-                    free_slots.append(slot)
-            # admit and launch while a slot is free
-            while queue and free_slots:
-                take, need = [], 0
-                while queue and len(take) < self.max_views:
-                    if queue[0].cancelled:
-                        queue.pop(0)
-                        continue
-                    est = self._estimate(queue[0].cam)
-                    if take and self.reserved + need + est > self.budget:
+        try:
+            while True:
+                with cv:
+                    if st["error"] is not None:
+                        raise st["error"]
+                    now = time.perf_counter() - t0
+                    while pending and pending[0].arrival <= now:
+                        queue_.append(pending.pop(0))
+                    # admit and hand batches to free slots
+                    while queue_ and st["free"]:
+                        take, need = [], 0
+                        while queue_ and len(take) < self.max_views:
+                            if queue_[0].cancelled:
+                                queue_.pop(0)
+                                continue
+                            est = self._estimate(queue_[0].cam)
+                            if take and self.reserved + need + est > self.budget:
+                                break
+                            if not take and self.reserved + est > self.budget and st["inflight"]:
+                                break
+                            take.append(queue_.pop(0))
+                            need += est
+                        if not take:
+                            break
+                        slot = st["free"].pop(0)
+                        self.reserved += need
+                        self.peak_reserved = max(self.peak_reserved, self.reserved)
+                        st["inflight"] += 1
+                        jobs[slot].put((take, bid, need))
+                        bid += 1
+                        self.batches_run += 1
+                        self.views_run += len(take)
+                    if not pending and not queue_ and st["inflight"] == 0:
                         break
-                    if not take and self.reserved + est > self.budget and inflight:
-                        break
-                    take.append(queue.pop(0))
-                    need += est
-                if not take:
-                    break
-                slot = free_slots.pop(0)
-                self.reserved += need
-                inflight[slot] = self._launch(take, slot, bid)
-                bid += 1
-                self.batches_run += 1
-                self.views_run += len(take)
-            if not queue and not inflight and pending:
-                wait = pending[0].arrival - (time.perf_counter() - t0)
-                if wait > 2e-4:
-                    time.sleep(wait - 1e-4)
+                    # sleep until just before the next arrival or until a slot
+                    # reports back; the last 0.2 ms are spun (a timed wait wakes
+                    # up too late for sub-millisecond latencies)
+                    wait = (pending[0].arrival - (time.perf_counter() - t0)) if pending else 0.05
+                    if queue_ and not st["free"]:
+                        wait = 0.05
+                    if wait > 3e-4:
+                        cv.wait(timeout=min(wait - 2e-4, 0.05))
+                time.sleep(0)                        # let the slot workers take the interpreter
+        finally:
+            for q in jobs:
+                q.put(None)
+            for w in workers:
+                w.join()
         torch.cuda.synchronize()
         return trace
 
