@@ -76,3 +76,17 @@ def test_rasterize_gradients_match_oracle(recompute):
         floor = 1e-2 * np.abs(ref).max()
         bad = np.abs(g - ref) > 1e-3 * np.maximum(np.abs(ref), floor)
         assert not bad.any(), (name, int(bad.sum()), g[bad][:4], ref[bad][:4])
+
+
+def test_l1_loss_function():
+    """raster.l1_loss (gs_loss_l1 behind a torch.autograd.Function): the
+    mean absolute difference and its gradient sign(image - target) / count,
+    scaled by the incoming gradient."""
+    _need_gpu()
+    rng = np.random.default_rng(1)
+    a = torch.tensor(rng.uniform(0, 1, 70001), dtype=torch.float32, device="cuda", requires_grad=True)
+    b = torch.tensor(rng.uniform(0, 1, 70001), dtype=torch.float32, device="cuda")
+    L = raster.l1_loss(a, b)
+    (3.0 * L).backward()
+    assert abs(L.item() - torch.abs(a.detach().double() - b.double()).mean().item()) <= 1e-6
+    assert torch.equal(a.grad, 3.0 * (torch.sign(a.detach() - b) / a.numel()))
