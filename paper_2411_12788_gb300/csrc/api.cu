@@ -161,6 +161,9 @@ SortLayout sort_layout(const gs_plan& p) {
     L.tile_count = take(4 * (size_t)std::max(p.total_tiles, 1));
     L.tile_start = take(4 * (size_t)std::max(p.total_tiles, 1));
     L.scan_blocks = take(scan_block_bytes(std::max(p.total_tiles, 1)) + 8);
+    const size_t c2 = np / kListPairsPerChunk + (size_t)rows + 1;   // second-level chunks, at most
+    L.chunks = take(16 * c2);
+    L.chunk_cnt = take(4 * c2);
   } else {
     L.keys = take(4 * e);
     L.keys_alt = take(4 * e);
@@ -436,6 +439,8 @@ gs_status gs_bin_sort(const gs_plan* plan, void* pre_ws, void* sort_ws, size_t s
     a.tile_count = at<uint32_t>(sort_ws, S.tile_count);
     a.tile_start = at<uint32_t>(sort_ws, S.tile_start);
     a.scan_blocks = at<uint64_t>(sort_ws, S.scan_blocks);
+    a.chunks = at<int4>(sort_ws, S.chunks);
+    a.chunk_cnt = at<uint32_t>(sort_ws, S.chunk_cnt);
     a.scan_total = at<unsigned long long>(sort_ws, S.scan_blocks + scan_block_bytes(std::max(plan->total_tiles, 1)));
     a.status = status;
     return cuda_status(launch_lists(a, stream));

@@ -51,7 +51,7 @@ struct ItemState {
   float4* rgb;               // (r, g, b, support half-extents as two halves; see pack_extent)
   float4* depth_frame;       // 3 x float4 per item: rows of W = diag(1/s) (R Rq)^T, then e = W p_c
   uint2* rect;               // (tx0 | ty0 << 16, tx1 | ty1 << 16), inclusive bounding box
-  float4* bin;               // 2 x float4 per item: (k, sc, 1/Syy, h), (rx, ys, 0, 0); see BinParams
+  float4* bin;               // 2 x float4 per item: (k, sc, 1/Syy, h), (rx, ys, ty0 as int bits, 0); see BinParams
   uint32_t* tiles;           // exact touched-tile count (0 = culled)
   uint32_t* depth_key;       // float bits of z, kCulledKey if culled
   uint32_t* depth_val;       // the item's own index: the depth sort's values
@@ -80,7 +80,7 @@ struct SortLayout {
   bool lists;
   size_t keys, keys_alt, vals, vals_alt, ranges, radix_scratch;
   size_t pkey, pkey_alt, pval, pval_alt, pair_radix, row_T, row_start, c2_start, cnt2_off, counts2, prefix2,
-      tile_count, tile_start, scan_blocks;
+      tile_count, tile_start, scan_blocks, chunks, chunk_cnt;
   int rows;
   int64_t counts2_n;
   size_t total;
@@ -208,7 +208,7 @@ cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int 
 // ---- tile lists by counting placement (lists.cu) ----------------------------
 constexpr int kListRowsMax = 4096;        // global tile rows (all views) the lists path handles
 constexpr int kListTxMax = 1023;          // tiles per row
-constexpr int kListPairsPerChunk = 1024;  // (item, row) pairs per second-level chunk
+constexpr int kListPairsPerChunk = 256;   // (item, row) pairs per second-level chunk
 constexpr uint32_t kListEmpty = 0xFFFFFFFFu;   // a pair whose row has no tile in the image
 struct ListArgs {
   const ViewDev* views;     // device
@@ -226,6 +226,8 @@ struct ListArgs {
   int32_t* counts2;         // per second-level chunk, entries per column
   uint32_t* prefix2;        // the same, exclusive over the row's chunks
   uint32_t *row_T, *row_start, *c2_start, *cnt2_off, *tile_count, *tile_start;
+  int4* chunks;             // per second-level chunk: tiles across, first tile, pairs [p0, p1)
+  uint32_t* chunk_cnt;      // per second-level chunk: offset of its counters
   uint64_t* scan_blocks;
   unsigned long long* scan_total;
   uint32_t* status;

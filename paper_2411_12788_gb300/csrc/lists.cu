@@ -19,7 +19,7 @@
 //            column scan over the row's chunks and an exclusive scan over all
 //            tiles give every chunk its offset in each tile's list; each chunk
 //            then places its entries in shared memory, grouped by column and
-//            in pair order (ranks among 32 pairs from one coverage word per
+//            in pair order (ranks among 32 entries from one coverage word per
 //            column), and writes every column's run out contiguously.
 //
 // Every placement is a prefix count in the order of the input, so a tile's
@@ -37,7 +37,8 @@ namespace gs {
 namespace {
 
 constexpr int kL2Warps = 4;
-constexpr int kStageCap = 2048;            // entries a chunk stages in shared memory
+constexpr int kL2EmitWarps = 4;
+constexpr int kStageCap = 1024;            // entries a second-level chunk stages in shared memory
 constexpr int kRowBits = 12;               // kListRowsMax == 1 << kRowBits
 constexpr uint32_t kRowMask = (1u << kRowBits) - 1u;
 static_assert(kListRowsMax <= (1 << kRowBits), "row ids must fit the key's row bits");
@@ -91,49 +92,35 @@ __device__ __forceinline__ int run_owner(uint32_t start, uint32_t len, uint32_t 
 // finds its pair's item (run_owner), evaluates that row's columns with
 // row_tiles (the same arithmetic the preprocess counted with) and writes the
 // pair at the run's start + its index: consecutive lanes, consecutive slots.
-struct PairItem {
-  BinParams b;
-  uint32_t item;
-  int ty0, row_base, tiles_x;
-};
 constexpr int kPairWarps = 8;
 
 __global__ void __launch_bounds__(32 * kPairWarps) pairs_kernel(ListArgs A) {
-  __shared__ PairItem s_it[kPairWarps][32];
+  // each lane's item record as three float4 (one 128-bit shared access each):
+  // (mx, my, tau, k), (sc, 1/Syy, h, rx), (ys, item, ty0, row_base | tiles_x << 16)
+  __shared__ float4 s_it[kPairWarps][3][32];
   __shared__ uint8_t s_nz[kPairWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t k0 = ((int64_t)blockIdx.x * kPairWarps + warp) * 32;
   if (k0 >= A.n_items) return;                               // warp-uniform
   const int64_t k = k0 + lane;
   uint32_t nrows = 0;
-  {
-    PairItem d;
-    d.item = 0;
-    d.ty0 = d.row_base = d.tiles_x = 0;
-    if (k < A.n_items) {
+  if (k < A.n_items) {
+    // band size from the scanned offsets (coalesced), so that only visible
+    // items are gathered
+    const uint32_t o0 = A.pair_offsets[k];
+    const uint32_t o1 = k + 1 < A.n_items ? A.pair_offsets[k + 1] : (uint32_t)A.n_pairs;
+    nrows = o1 - o0;
+    if (nrows) {
       uint32_t item = A.sorted_items[k];
       if (!GS_IN_RANGE(item, A.n_items, A.status)) item = 0;
-      nrows = A.st.band_rows[item];
-      if (nrows) {
-        const ViewDev& V = A.views[item / A.n];
-        const float4 a = A.st.xy_tau_z[item];
-        const float4 b0 = A.st.bin[2 * item], b1 = A.st.bin[2 * item + 1];
-        d.b.mx = a.x;
-        d.b.my = a.y;
-        d.b.tau = a.z;
-        d.b.k = b0.x;
-        d.b.sc = b0.y;
-        d.b.isyy = b0.z;
-        d.b.h = b0.w;
-        d.b.rx = b1.x;
-        d.b.ys = b1.y;
-        d.item = item;
-        d.ty0 = (int)(A.st.rect[item].x >> 16);
-        d.row_base = V.row_base;
-        d.tiles_x = V.tiles_x;
-      }
+      const ViewDev& V = A.views[item / A.n];
+      const float4 a = A.st.xy_tau_z[item];
+      const float4 b0 = A.st.bin[2 * item], b1 = A.st.bin[2 * item + 1];
+      s_it[warp][0][lane] = make_float4(a.x, a.y, a.z, b0.x);
+      s_it[warp][1][lane] = make_float4(b0.y, b0.z, b0.w, b1.x);
+      s_it[warp][2][lane] = make_float4(b1.y, __uint_as_float(item), b1.z,
+                                        __uint_as_float((uint32_t)V.row_base | ((uint32_t)V.tiles_x << 16)));
     }
-    s_it[warp][lane] = d;
   }
   const uint32_t nzmask = __ballot_sync(0xffffffffu, nrows > 0);
   if (!nzmask) return;                                       // warp-uniform
@@ -148,15 +135,27 @@ __global__ void __launch_bounds__(32 * kPairWarps) pairs_kernel(ListArgs A) {
     const uint32_t u = u0 + lane;
     const uint32_t r = u - __shfl_sync(0xffffffffu, rstart, j);
     if (u < R) {
-      const PairItem& d = s_it[warp][j];
-      const int ty = d.ty0 + (int)r;
+      const float4 q0 = s_it[warp][0][j], q1 = s_it[warp][1][j], q2 = s_it[warp][2][j];
+      BinParams b;
+      b.mx = q0.x;
+      b.my = q0.y;
+      b.tau = q0.z;
+      b.k = q0.w;
+      b.sc = q1.x;
+      b.isyy = q1.y;
+      b.h = q1.z;
+      b.rx = q1.w;
+      b.ys = q2.x;
+      const uint32_t rb = __float_as_uint(q2.w);
+      const int row_base = (int)(rb & 0xFFFFu), tiles_x = (int)(rb >> 16);
+      const int ty = __float_as_int(q2.z) + (int)r;
       int ta, tb;
-      const uint32_t key = row_tiles(d.b, ty, d.tiles_x, &ta, &tb) ? pair_key(d.row_base + ty, ta, tb)
-                                                                   : ((uint32_t)(d.row_base + ty) | kEmptyAB);
+      const uint32_t key = row_tiles(b, ty, tiles_x, &ta, &tb) ? pair_key(row_base + ty, ta, tb)
+                                                              : ((uint32_t)(row_base + ty) | kEmptyAB);
       const uint64_t pos = (uint64_t)base + u;
       if (pos < (uint64_t)A.n_pairs) {
         A.pkey[pos] = key;
-        A.pval[pos] = d.item;
+        A.pval[pos] = __float_as_uint(q2.y);
       } else {
         atomicOr(A.status, kStatusEntryMismatch);            // more pairs than the scan counted
       }
@@ -230,33 +229,43 @@ __global__ void __launch_bounds__(1024) rows_kernel(ListArgs A) {
 
 // ---- level 2 ---------------------------------------------------------------
 struct Chunk2 {
-  int row, tx_n, tb;            // row, tiles across its view, global id of the row's first tile
-  uint32_t j, p0, p1;           // chunk index in the row, its pairs [p0, p1)
+  int tx_n, tb;                 // tiles across the row's view, global id of the row's first tile
+  uint32_t p0, p1;              // the chunk's pairs [p0, p1)
   uint32_t cnt;                 // offset of its counters
 };
 
-// The second-level chunk c: its row by binary search in the chunk table.
-__device__ __forceinline__ bool chunk2(const ListArgs& A, uint32_t c, Chunk2* k) {
-  if (c >= A.c2_start[A.rows]) return false;
+// The table of second-level chunks: thread per chunk (its row by binary
+// search in the chunk table), so that the chunk kernels read one record.
+__global__ void chunk_table_kernel(ListArgs A) {
+  const uint32_t c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= A.c2_start[A.rows]) return;
   int lo = 0, hi = A.rows - 1;                  // last row with c2_start <= c
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
     if (A.c2_start[mid] <= c) lo = mid;
     else hi = mid - 1;
   }
-  k->row = lo;
   const ViewDev& V = A.views[view_of_row(A.views, A.n_views, lo)];
-  k->tx_n = V.tiles_x;
-  k->tb = V.tile_base + (lo - V.row_base) * V.tiles_x;
-  k->j = c - A.c2_start[lo];
+  const uint32_t j = c - A.c2_start[lo];
   const uint32_t rs = A.row_start[lo], re = A.row_start[lo] + A.row_T[lo];
-  k->p0 = rs + k->j * (uint32_t)kListPairsPerChunk;
-  k->p1 = min(k->p0 + (uint32_t)kListPairsPerChunk, re);
-  k->cnt = A.cnt2_off[lo] + k->j * (uint32_t)k->tx_n;
-  // pairs and counters stay inside their arrays even if the counts disagree
-  // with the preprocess's (the disagreement itself is flagged by the totals)
-  if (k->p1 > (uint32_t)A.n_pairs || (int64_t)k->cnt + k->tx_n > A.counts2_n) return false;
-  return true;
+  const uint32_t p0 = rs + j * (uint32_t)kListPairsPerChunk;
+  A.chunks[c] = make_int4(V.tiles_x, V.tile_base + (lo - V.row_base) * V.tiles_x, (int)p0,
+                          (int)min(p0 + (uint32_t)kListPairsPerChunk, re));
+  A.chunk_cnt[c] = A.cnt2_off[lo] + j * (uint32_t)V.tiles_x;
+}
+
+// The second-level chunk c from the table; false past the last chunk or if
+// its pairs or counters would leave their arrays (counts that disagree with
+// the preprocess's are flagged by the totals).
+__device__ __forceinline__ bool chunk2(const ListArgs& A, uint32_t c, Chunk2* k) {
+  if (c >= A.c2_start[A.rows]) return false;
+  const int4 r = A.chunks[c];
+  k->tx_n = r.x;
+  k->tb = r.y;
+  k->p0 = (uint32_t)r.z;
+  k->p1 = (uint32_t)r.w;
+  k->cnt = A.chunk_cnt[c];
+  return k->p1 <= (uint32_t)A.n_pairs && (int64_t)k->cnt + k->tx_n <= A.counts2_n;
 }
 
 // Entries per tile column of every second-level chunk (warp per chunk).
@@ -287,34 +296,37 @@ __global__ void __launch_bounds__(32 * kL2Warps) l2_count_kernel(ListArgs A) {
 }
 
 // Per row: exclusive scan of each column's counts over the row's chunks
-// (into prefix2), and the tile totals.  One block per row.
-__global__ void __launch_bounds__(128) l2_tile_kernel(ListArgs A) {
+// (into prefix2), and the tile totals.  Block per (row, 32 columns); its
+// warps split the row's chunks, sum their share, and then scan it from the
+// sums of the warps before them.
+constexpr int kTileScanWarps = 8;
+
+__global__ void __launch_bounds__(32 * kTileScanWarps) l2_tile_kernel(ListArgs A) {
+  __shared__ uint32_t s_part[kTileScanWarps][32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int r = blockIdx.x;
   const ViewDev& V = A.views[view_of_row(A.views, A.n_views, r)];
   const int tx_n = V.tiles_x;
+  const int t = blockIdx.y * 32 + lane;
+  if (blockIdx.y * 32 >= tx_n) return;                       // block-uniform
   const uint32_t nch = A.c2_start[r + 1] - A.c2_start[r];
-  const int tb = V.tile_base + (r - V.row_base) * tx_n;
   const int64_t off = A.cnt2_off[r];
-  for (int t = threadIdx.x; t < tx_n; t += blockDim.x) {
-    uint32_t run = 0;
-    uint32_t j = 0;
-    for (; j + 4 <= nch; j += 4) {               // four independent loads at a time
-      const int64_t i = off + (int64_t)j * tx_n + t;
-      const uint32_t c0 = (uint32_t)A.counts2[i], c1 = (uint32_t)A.counts2[i + tx_n],
-                     c2 = (uint32_t)A.counts2[i + 2 * tx_n], c3 = (uint32_t)A.counts2[i + 3 * tx_n];
-      A.prefix2[i] = run;
-      A.prefix2[i + tx_n] = run + c0;
-      A.prefix2[i + 2 * tx_n] = run + c0 + c1;
-      A.prefix2[i + 3 * tx_n] = run + c0 + c1 + c2;
-      run += c0 + c1 + c2 + c3;
-    }
-    for (; j < nch; ++j) {
-      const int64_t i = off + (int64_t)j * tx_n + t;
-      A.prefix2[i] = run;
-      run += (uint32_t)A.counts2[i];
-    }
-    A.tile_count[tb + t] = run;
+  const uint32_t per = (nch + kTileScanWarps - 1) / kTileScanWarps;
+  const uint32_t j0 = min(warp * per, nch), j1 = min(j0 + per, nch);
+  uint32_t sum = 0;
+  if (t < tx_n)
+    for (uint32_t j = j0; j < j1; ++j) sum += (uint32_t)A.counts2[off + (int64_t)j * tx_n + t];
+  s_part[warp][lane] = sum;
+  __syncthreads();
+  if (t >= tx_n) return;
+  uint32_t run = 0;
+  for (int w2 = 0; w2 < warp; ++w2) run += s_part[w2][lane];
+  for (uint32_t j = j0; j < j1; ++j) {
+    const int64_t i = off + (int64_t)j * tx_n + t;
+    A.prefix2[i] = run;
+    run += (uint32_t)A.counts2[i];
   }
+  if (warp == kTileScanWarps - 1) A.tile_count[V.tile_base + (r - V.row_base) * tx_n + t] = run;
 }
 
 // [start, end) of every tile; checks the entry total against the preprocess's.
@@ -330,30 +342,30 @@ __global__ void l2_ranges_kernel(ListArgs A) {
 // run_owner); an entry's rank at its column is the number of lower lanes with
 // the same column, read from a coverage word per column (bit l set by lane
 // l); the column's lowest lane then advances the column's next slot and
-// clears the word.  Entries go to shared memory, grouped by column, and are
-// written out in runs of one column (consecutive addresses); a chunk with
-// more than kStageCap entries writes them straight to their places instead.
-__global__ void __launch_bounds__(32 * kL2Warps) l2_emit_kernel(ListArgs A) {
+// clears the word.  The entries are staged in shared memory grouped by column
+// (the chunk's own counts give each column's local start) and then written
+// out column by column, each column's run to consecutive addresses of its
+// tile's list, so that stores coalesce.  A chunk with more than kStageCap
+// entries (very wide supports) writes its entries straight to their places.
+__global__ void __launch_bounds__(32 * kL2EmitWarps) l2_emit_kernel(ListArgs A) {
   extern __shared__ uint32_t s_dyn3[];
-  __shared__ uint8_t s_nz[kL2Warps][32];
+  __shared__ uint8_t s_nz[kL2EmitWarps][32];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int w = A.max_tx + 1;
-  uint32_t* s_next = s_dyn3 + warp * (3 * w + kStageCap);   // next slot of each column (local or global)
-  uint32_t* s_cov = s_next + w;                              // coverage words of the current group
-  uint32_t* s_gd = s_cov + w;                                // global position minus local position
-  uint32_t* s_stage = s_gd + w;                              // the chunk's entries, grouped by column
+  uint32_t* s_next = s_dyn3 + warp * (2 * w + kStageCap + kStageCap / 2);   // next slot of each column
+  uint32_t* s_cov = s_next + w;                              // coverage words of the current window
+  uint32_t* s_stage = s_cov + w;                             // the chunk's entries, grouped by column
+  uint16_t* s_tag = reinterpret_cast<uint16_t*>(s_stage + kStageCap);   // their columns
   Chunk2 k;
-  if (!chunk2(A, blockIdx.x * kL2Warps + warp, &k)) return;   // warp-uniform
+  if (!chunk2(A, blockIdx.x * kL2EmitWarps + warp, &k)) return;   // warp-uniform
   uint32_t carry = 0;
-  for (int t0 = 0; t0 < k.tx_n; t0 += 32) {
+  for (int t0 = 0; t0 < k.tx_n; t0 += 32) {                 // local starts: scan of the chunk's counts
     const int t = t0 + lane;
     const uint32_t own = t < k.tx_n ? (uint32_t)A.counts2[k.cnt + t] : 0u;
     const uint32_t incl = warp_incl_scan(own) + carry;
     if (t < k.tx_n) {
-      const uint32_t start = incl - own;
-      s_next[t] = start;
+      s_next[t] = incl - own;
       s_cov[t] = 0u;
-      s_gd[t] = A.tile_start[k.tb + t] + A.prefix2[k.cnt + t] - start;
     }
     carry = __shfl_sync(0xffffffffu, incl, 31);
   }
@@ -361,17 +373,22 @@ __global__ void __launch_bounds__(32 * kL2Warps) l2_emit_kernel(ListArgs A) {
   const bool direct = total > (uint32_t)kStageCap;
   __syncwarp();
   if (direct)
-    for (int t = lane; t < k.tx_n; t += 32) s_next[t] += s_gd[t];
+    for (int t = lane; t < k.tx_n; t += 32) s_next[t] = A.tile_start[k.tb + t] + A.prefix2[k.cnt + t];
   const uint32_t bit = 1u << lane, lt = bit - 1u;
   __syncwarp();
+  // the pairs of the next group are loaded while the current one is placed
+  uint32_t nkey = k.p0 + lane < k.p1 ? A.pkey[k.p0 + lane] : kEmptyAB;
+  uint32_t nval = k.p0 + lane < k.p1 ? A.pval[k.p0 + lane] : 0u;
   for (uint32_t pb = k.p0; pb < k.p1; pb += 32) {
-    const uint32_t p = pb + lane;
+    const uint32_t key = nkey, val = nval;
+    const uint32_t pn = pb + 32 + lane;
+    nkey = pn < k.p1 ? A.pkey[pn] : kEmptyAB;
+    nval = pn < k.p1 ? A.pval[pn] : 0u;
     uint32_t item = 0, a = 0, len = 0;
-    if (p < k.p1) {
-      const uint32_t key = A.pkey[p];
+    {
       const int ka = key_a(key), kb = key_b(key);
       if (ka <= kb) {
-        item = A.pval[p];
+        item = val;
         a = (uint32_t)ka;
         len = (uint32_t)(kb - ka + 1);
       }
@@ -382,9 +399,6 @@ __global__ void __launch_bounds__(32 * kL2Warps) l2_emit_kernel(ListArgs A) {
     const uint32_t T = __shfl_sync(0xffffffffu, es, 31);
     const uint32_t estart = es - len;
     __syncwarp();
-    // the group's entries 32 at a time: entry e belongs to pair run_owner(e),
-    // column a + (e - its start); a column's rank among the window's entries
-    // comes from its coverage word (one bit per lane)
     for (uint32_t e0 = 0; e0 < T; e0 += 32) {
       const int j = run_owner(estart, len, e0, s_nz[warp]);
       const uint32_t e = e0 + lane;
@@ -398,7 +412,10 @@ __global__ void __launch_bounds__(32 * kL2Warps) l2_emit_kernel(ListArgs A) {
         cov = s_cov[tx];
         const uint32_t pos = s_next[tx] + (uint32_t)__popc(cov & lt);
         if (!direct) {
-          if (pos < (uint32_t)kStageCap) s_stage[pos] = it;
+          if (pos < (uint32_t)kStageCap) {
+            s_stage[pos] = it;
+            s_tag[pos] = (uint16_t)tx;
+          }
         } else if (pos < (uint64_t)A.n_entries) {
           A.vals[pos] = it;
         } else {
@@ -414,16 +431,22 @@ __global__ void __launch_bounds__(32 * kL2Warps) l2_emit_kernel(ListArgs A) {
     }
   }
   if (direct) return;
-  // s_next now holds each column's local end: the column of staged entry i is
-  // the first whose end exceeds i
-  for (uint32_t i = lane; i < total; i += 32) {
-    int lo = 0, hi = k.tx_n - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi) >> 1;
-      if (s_next[mid] > i) hi = mid;
-      else lo = mid + 1;
+  // write-out: the coverage words (all zero again) take each column's global
+  // start minus its local start; staged entry i goes to that + i, so runs of
+  // one column go to consecutive addresses
+  {
+    uint32_t carry2 = 0;
+    for (int t0 = 0; t0 < k.tx_n; t0 += 32) {
+      const int t = t0 + lane;
+      const uint32_t own = t < k.tx_n ? (uint32_t)A.counts2[k.cnt + t] : 0u;
+      const uint32_t incl = warp_incl_scan(own) + carry2;
+      if (t < k.tx_n) s_cov[t] = A.tile_start[k.tb + t] + A.prefix2[k.cnt + t] - (incl - own);
+      carry2 = __shfl_sync(0xffffffffu, incl, 31);
     }
-    const uint32_t pos = s_gd[lo] + i;
+  }
+  __syncwarp();
+  for (uint32_t i = lane; i < total; i += 32) {
+    const uint32_t pos = s_cov[s_tag[i]] + i;
     if (pos < (uint64_t)A.n_entries) A.vals[pos] = s_stage[i];
     else atomicOr(A.status, kStatusEntryMismatch);
   }
@@ -445,12 +468,12 @@ cudaError_t launch_lists(const ListArgs& a, cudaStream_t stream) {
                                          kL2Warps * (kListTxMax + 1) * 4);
     if (r == cudaSuccess)
       r = cudaFuncSetAttribute(l2_emit_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               kL2Warps * (3 * (kListTxMax + 1) + kStageCap) * 4);
+                               kL2EmitWarps * (2 * (kListTxMax + 1) + kStageCap + kStageCap / 2) * 4);
     return r;
   });
   if (e != cudaSuccess) return e;
   const size_t smem2 = (size_t)kL2Warps * (a.max_tx + 1) * 4;
-  const size_t smem3 = (size_t)kL2Warps * (3 * (a.max_tx + 1) + kStageCap) * 4;
+  const size_t smem3 = (size_t)kL2EmitWarps * (2 * (a.max_tx + 1) + kStageCap + kStageCap / 2) * 4;
   // second-level chunks: at most one partial chunk per row
   const int64_t c2_max = a.n_pairs / kListPairsPerChunk + a.rows;
   const int l2_blocks = (int)((c2_max + kL2Warps - 1) / kL2Warps);
@@ -463,15 +486,19 @@ cudaError_t launch_lists(const ListArgs& a, cudaStream_t stream) {
   if (e != cudaSuccess) return e;
   GS_TIMED("lists_rows", stream, (row_ranges_kernel<<<ceil_div((int64_t)a.rows + 1, 256), 256, 0, stream>>>(a)));
   GS_TIMED("lists_rows", stream, (rows_kernel<<<1, 1024, 0, stream>>>(a)));
+  GS_TIMED("lists_rows", stream, (chunk_table_kernel<<<ceil_div(c2_max, 256), 256, 0, stream>>>(a)));
   GS_TIMED("lists_tile_count", stream, (l2_count_kernel<<<l2_blocks, 32 * kL2Warps, smem2, stream>>>(a)));
-  GS_TIMED("lists_tile_scan", stream, (l2_tile_kernel<<<a.rows, 128, 0, stream>>>(a)));
+  GS_TIMED("lists_tile_scan", stream,
+           (l2_tile_kernel<<<dim3(a.rows, (a.max_tx + 31) / 32), 32 * kTileScanWarps, 0, stream>>>(a)));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   e = gather_exclusive_scan(a.tile_count, nullptr, a.tile_start, a.total_tiles, a.scan_blocks, a.scan_total, stream);
   if (e != cudaSuccess) return e;
   GS_TIMED("lists_ranges", stream,
            (l2_ranges_kernel<<<ceil_div(a.total_tiles, 256), 256, 0, stream>>>(a)));
-  GS_TIMED("lists_entries", stream, (l2_emit_kernel<<<l2_blocks, 32 * kL2Warps, smem3, stream>>>(a)));
+  GS_TIMED("lists_entries", stream,
+           (l2_emit_kernel<<<(int)((c2_max + kL2EmitWarps - 1) / kL2EmitWarps), 32 * kL2EmitWarps, smem3, stream>>>(
+               a)));
   return cudaGetLastError();
 }
 

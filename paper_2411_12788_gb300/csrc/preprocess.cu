@@ -211,7 +211,7 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
     P.st.xy_tau_z[item] = make_float4(b.mx, b.my, b.tau, pc.z);
     P.st.conic_o[item] = make_float4(A, B, C, o);
     P.st.bin[2 * item] = make_float4(b.k, b.sc, b.isyy, b.h);
-    P.st.bin[2 * item + 1] = make_float4(b.rx, b.ys, 0.f, 0.f);
+    P.st.bin[2 * item + 1] = make_float4(b.rx, b.ys, __int_as_float(ty0), 0.f);   // + first band row
 
     // colour (Sec. 3.1): SH in the direction camera centre -> Gaussian
     float dx = p.x - V.campos[0], dy = p.y - V.campos[1], dz = p.z - V.campos[2];
