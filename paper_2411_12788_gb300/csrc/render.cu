@@ -103,6 +103,40 @@ __device__ __forceinline__ float ex2_approx(float x) {
   return y;
 }
 
+// Blackwell's packed FP32 instructions: two independent IEEE operations in
+// one instruction, each rounded exactly as its scalar form.  The backward
+// keeps a lane's two entries in the two halves.
+#define GS_PK3(op)                                                                                       \
+  asm("{\n\t.reg .b64 ra, rb, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t" op            \
+      " rd, ra, rb;\n\tmov.b64 {%0, %1}, rd;\n\t}"                                                      \
+      : "=f"(d.x), "=f"(d.y)                                                                             \
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y))
+__device__ __forceinline__ float2 pk_mul(float2 a, float2 b) {
+  float2 d;
+  GS_PK3("mul.rn.f32x2");
+  return d;
+}
+__device__ __forceinline__ float2 pk_add(float2 a, float2 b) {
+  float2 d;
+  GS_PK3("add.rn.f32x2");
+  return d;
+}
+__device__ __forceinline__ float2 pk_sub(float2 a, float2 b) {
+  float2 d;
+  GS_PK3("sub.rn.f32x2");
+  return d;
+}
+#undef GS_PK3
+__device__ __forceinline__ float2 pk_fma(float2 a, float2 b, float2 c) {
+  float2 d;
+  asm("{\n\t.reg .b64 ra, rb, rc, rd;\n\tmov.b64 ra, {%2, %3};\n\tmov.b64 rb, {%4, %5};\n\t"
+      "mov.b64 rc, {%6, %7};\n\tfma.rn.f32x2 rd, ra, rb, rc;\n\tmov.b64 {%0, %1}, rd;\n\t}"
+      : "=f"(d.x), "=f"(d.y)
+      : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+  return d;
+}
+__device__ __forceinline__ float2 pk_dup(float x) { return make_float2(x, x); }
+
 __device__ __forceinline__ float rcp_approx(float x) {
   float y;
   asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
@@ -432,13 +466,17 @@ struct BwdEntry {
   float mx, my;        // centre
   float4 ex;           // exponent form
   float3 col;
-  // sums over the pixels, with de = dL/de / ln 2 (the factor is applied at
-  // the flush): de dx, de dy (the centre's gradient follows from them and
-  // the entry's a2, b2, c2), de dx^2, de dx dy, de dy^2 (d a2, b2, c2), de
-  // (d log2 o), w dL/dI (d colour)
-  float acc[9];
-  float wsum;          // blending weight over the warp's pixels (I_i)
-  uint32_t wfix;       // the same, each pixel's weight rounded to a multiple of 2^-24
+};
+
+// A lane's sums over the pixels for its two entries (first entry in .x,
+// second in .y), with de = dL/de / ln 2 (the factor is applied at the
+// flush): de dx, de dy (the centre's gradient follows from them and the
+// entry's a2, b2, c2), de dx^2, de dx dy, de dy^2 (d a2, b2, c2), de
+// (d log2 o), w dL/dI (d colour).
+struct BwdSums {
+  float2 acc[9];
+  float2 wsum;         // blending weight over the warp's pixels (I_i)
+  uint32_t wfix_a, wfix_b;   // the same, each pixel's weight rounded to a multiple of 2^-24
 };
 
 __device__ __forceinline__ void bwd_entry_load(BwdEntry& E, bool valid, const float2* s_xy, const float4* s_ex,
@@ -450,52 +488,55 @@ __device__ __forceinline__ void bwd_entry_load(BwdEntry& E, bool valid, const fl
   E.ex = valid ? s_ex[idx] : make_float4(0.f, 0.f, 0.f, -1e30f);
   const float4 c = valid ? s_rgb[idx] : make_float4(0.f, 0.f, 0.f, 0.f);
   E.col = make_float3(c.x, c.y, c.z);
-#pragma unroll
-  for (int k = 0; k < 9; ++k) E.acc[k] = 0.f;
-  E.wsum = 0.f;
-  E.wfix = 0u;
 }
 
-// Adds one pixel's contribution to an active entry's gradient sums.
+// Adds one pixel's contribution to a lane's two entries' gradient sums, both
+// halves at once: a = (alpha_A, alpha_B) is zero for an entry that does not
+// take part at this pixel, and ad the same with zero also where the 0.99
+// clamp holds (no alpha gradient there), so such an entry adds nothing.
 template <bool kFix>
-__device__ __forceinline__ void bwd_entry_accumulate(BwdEntry& E, const float4& pg, float dx, float dy, float a,
-                                                     float araw, float Tl, float Fl, float cg, float alpha_max) {
-  const float w = a * Tl;
-  E.wsum += w;
-  if (kFix) E.wfix += __float2uint_rn(w * 16777216.f);
-  E.acc[6] = fmaf(w, pg.x, E.acc[6]);
-  E.acc[7] = fmaf(w, pg.y, E.acc[7]);
-  E.acc[8] = fmaf(w, pg.z, E.acc[8]);
-  if (araw <= alpha_max) {
-    const float dal = fmaf(Tl, cg, -(pg.w - Fl) * rcp_approx(1.f - a));
-    const float de = dal * a;                 // dL/de / ln 2
-    const float dedx = de * dx, dedy = de * dy;
-    E.acc[5] += de;                           // log2 o
-    E.acc[2] = fmaf(dedx, dx, E.acc[2]);      // a2
-    E.acc[3] = fmaf(dedx, dy, E.acc[3]);      // b2
-    E.acc[4] = fmaf(dedy, dy, E.acc[4]);      // c2
-    E.acc[0] += dedx;                         // centre, via the flush
-    E.acc[1] += dedy;
+__device__ __forceinline__ void bwd_pair_accumulate(BwdSums& S, const float4& pg, float2 dx, float2 dy, float2 a,
+                                                    float2 ad, float2 one_minus_a, float2 T, float2 F, float2 cg) {
+  const float2 w = pk_mul(a, T);
+  S.wsum = pk_add(S.wsum, w);
+  if (kFix) {
+    S.wfix_a += __float2uint_rn(w.x * 16777216.f);
+    S.wfix_b += __float2uint_rn(w.y * 16777216.f);
   }
+  S.acc[6] = pk_fma(w, pk_dup(pg.x), S.acc[6]);
+  S.acc[7] = pk_fma(w, pk_dup(pg.y), S.acc[7]);
+  S.acc[8] = pk_fma(w, pk_dup(pg.z), S.acc[8]);
+  // dL/dalpha = T (c.g) - (I - F) / (1 - alpha)
+  const float2 r = make_float2(rcp_approx(one_minus_a.x), rcp_approx(one_minus_a.y));
+  const float2 dal = pk_fma(pk_sub(F, pk_dup(pg.w)), r, pk_mul(T, cg));
+  const float2 de = pk_mul(dal, ad);                 // dL/de / ln 2
+  const float2 dedx = pk_mul(de, dx), dedy = pk_mul(de, dy);
+  S.acc[5] = pk_add(S.acc[5], de);                   // log2 o
+  S.acc[2] = pk_fma(dedx, dx, S.acc[2]);             // a2
+  S.acc[3] = pk_fma(dedx, dy, S.acc[3]);             // b2
+  S.acc[4] = pk_fma(dedy, dy, S.acc[4]);             // c2
+  S.acc[0] = pk_add(S.acc[0], dedx);                 // centre, via the flush
+  S.acc[1] = pk_add(S.acc[1], dedy);
 }
 
 template <bool kFix>
-__device__ __forceinline__ void bwd_entry_flush(const BwdEntry& E, float (*s_g)[kRenderThreads], float* s_wsum,
-                                                uint32_t* s_wfix, int idx, bool want_w) {
+__device__ __forceinline__ void bwd_entry_flush(const BwdEntry& E, const float* acc, float wsum, uint32_t wfix,
+                                                float (*s_g)[kRenderThreads], float* s_wsum, uint32_t* s_wfix, int idx,
+                                                bool want_w) {
   // d = pixel - centre, so de/dcentre = -(2 a2 dx + b2 dy, b2 dx + 2 c2 dy);
   // every exponent term carries the factor ln 2 left out per pixel
   float g[9];
-  g[0] = -kLn2 * fmaf(2.f * E.ex.x, E.acc[0], E.ex.y * E.acc[1]);
-  g[1] = -kLn2 * fmaf(E.ex.y, E.acc[0], 2.f * E.ex.z * E.acc[1]);
+  g[0] = -kLn2 * fmaf(2.f * E.ex.x, acc[0], E.ex.y * acc[1]);
+  g[1] = -kLn2 * fmaf(E.ex.y, acc[0], 2.f * E.ex.z * acc[1]);
 #pragma unroll
-  for (int k = 2; k < 6; ++k) g[k] = kLn2 * E.acc[k];
+  for (int k = 2; k < 6; ++k) g[k] = kLn2 * acc[k];
 #pragma unroll
-  for (int k = 6; k < 9; ++k) g[k] = E.acc[k];
+  for (int k = 6; k < 9; ++k) g[k] = acc[k];
 #pragma unroll
   for (int k = 0; k < 9; ++k)
     if (g[k] != 0.f) atomicAdd(&s_g[k][idx], g[k]);
-  if (want_w && E.wsum != 0.f) atomicAdd(&s_wsum[idx], E.wsum);
-  if (kFix && E.wfix) atomicAdd(&s_wfix[idx], E.wfix);
+  if (want_w && wsum != 0.f) atomicAdd(&s_wsum[idx], wsum);
+  if (kFix && wfix) atomicAdd(&s_wfix[idx], wfix);
 }
 
 template <bool kFix>
@@ -598,6 +639,17 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
       BwdEntry A, Bn;
       bwd_entry_load(A, va, s_xy, s_ex, s_rgb, ia);
       bwd_entry_load(Bn, vb, s_xy, s_ex, s_rgb, ib);
+      BwdSums S;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) S.acc[k] = make_float2(0.f, 0.f);
+      S.wsum = make_float2(0.f, 0.f);
+      S.wfix_a = S.wfix_b = 0u;
+      // the two entries side by side for the packed instructions
+      const float2 mx2 = make_float2(A.mx, Bn.mx), my2 = make_float2(A.my, Bn.my);
+      const float2 exx = make_float2(A.ex.x, Bn.ex.x), exy = make_float2(A.ex.y, Bn.ex.y);
+      const float2 exz = make_float2(A.ex.z, Bn.ex.z), exw = make_float2(A.ex.w, Bn.ex.w);
+      const float2 colx = make_float2(A.col.x, Bn.col.x), coly = make_float2(A.col.y, Bn.col.y);
+      const float2 colz = make_float2(A.col.z, Bn.col.z);
       const uint32_t posa = bstart + ia, posb = bstart + ib;   // list positions
       // pixels of this warp still blending at the chunk's first entry
       const uint32_t pmask = __ballot_sync(0xffffffffu, my_nc > bstart + s_list[warp][c]);
@@ -608,8 +660,8 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
       if (!((pmask >> (8 * r)) & 0xffu)) continue;
       // pixel centre minus entry centre, rounded exactly as in the forward
       const float fy = byf + (float)r;
-      const float dya = fy - A.my, dyb = fy - Bn.my;
-      const float2 rowa = expo_row(A.ex, dya), rowb = expo_row(Bn.ex, dyb);
+      const float2 dy = pk_sub(pk_dup(fy), my2);
+      const float2 rowx = pk_fma(pk_mul(exz, dy), dy, exw), rowy = pk_mul(exy, dy);   // expo_row, both entries
 #pragma unroll 4
       for (int cx = 0; cx < 8; ++cx) {
         const int p = 8 * r + cx;
@@ -618,23 +670,20 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
         const float4 st = s_st[pt];
         const uint32_t nc = __float_as_uint(st.z);
         const float fx = bxf + (float)cx;
-        const float dxa = fx - A.mx, dxb = fx - Bn.mx;
-        const float ea = expo_pix(A.ex, rowa, dxa);
-        const float eb = expo_pix(Bn.ex, rowb, dxb);
-        const bool acta = posa < nc && ea >= P.e_min;
-        const bool actb = posb < nc && eb >= P.e_min;
+        const float2 dx = pk_sub(pk_dup(fx), mx2);
+        const float2 e = pk_fma(pk_fma(exx, dx, rowy), dx, rowx);   // expo_pix, both entries
+        const bool acta = posa < nc && e.x >= P.e_min;
+        const bool actb = posb < nc && e.y >= P.e_min;
         if (!__any_sync(0xffffffffu, acta || actb)) continue;
         const float4 pg = s_pg[pt];
-        const float arawa = ex2_approx(ea), arawb = ex2_approx(eb);
-        const float aa = acta ? fminf(P.alpha_max, arawa) : 0.f;
-        const float ab = actb ? fminf(P.alpha_max, arawb) : 0.f;
-        const float cga = A.col.x * pg.x + A.col.y * pg.y + A.col.z * pg.z;
-        const float cgb = Bn.col.x * pg.x + Bn.col.y * pg.y + Bn.col.z * pg.z;
+        const float arawa = ex2_approx(e.x), arawb = ex2_approx(e.y);
+        const float2 a = make_float2(acta ? fminf(P.alpha_max, arawa) : 0.f, actb ? fminf(P.alpha_max, arawb) : 0.f);
+        const float2 cg = pk_fma(colz, pk_dup(pg.z), pk_fma(coly, pk_dup(pg.y), pk_mul(colx, pk_dup(pg.x))));
         // the lane's two maps composed, then one scan over the lanes: the
         // product of (1 - a) and sum a_k cg_k prod_{j<k} (1 - a_j)
-        const float ma = 1.f - aa, mb = 1.f - ab;
-        const float fa = aa * cga;
-        float m = ma * mb, f = fmaf(ma, ab * cgb, fa);
+        const float2 oma = pk_sub(make_float2(1.f, 1.f), a);
+        const float2 fab = pk_mul(a, cg);
+        float m = oma.x * oma.y, f = fmaf(oma.x, fab.y, fab.x);
         scan_affine(m, f);
         float mex = __shfl_up_sync(0xffffffffu, m, 1);     // exclusive over lanes
         float fex = __shfl_up_sync(0xffffffffu, f, 1);
@@ -644,21 +693,30 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
         }
         const float T0 = st.x, F0 = st.y;
         const float Ta = T0 * mex;                          // T in front of entry A
-        const float Fa = fmaf(Ta, fa, fmaf(T0, fex, F0));   // sum_{k<=A} w_k cg_k
-        const float Tb = Ta * ma;
-        const float Fb = fmaf(Tb * ab, cgb, Fa);
+        const float Fa = fmaf(Ta, fab.x, fmaf(T0, fex, F0));   // sum_{k<=A} w_k cg_k
+        const float Tb = Ta * oma.x;
+        const float Fb = fmaf(Tb * a.y, cg.y, Fa);
         // lane 31 holds the chunk's totals: carry the pixel's state forward
         __syncwarp();
         if (lane == 31) {
           float2* stp = reinterpret_cast<float2*>(&s_st[pt]);
           *stp = make_float2(T0 * m, fmaf(T0, f, F0));
         }
-        if (acta) bwd_entry_accumulate<kFix>(A, pg, dxa, dya, aa, arawa, Ta, Fa, cga, P.alpha_max);
-        if (actb) bwd_entry_accumulate<kFix>(Bn, pg, dxb, dyb, ab, arawb, Tb, Fb, cgb, P.alpha_max);
+        // alpha gradient only where the 0.99 clamp is not active
+        const float2 ad = make_float2(arawa <= P.alpha_max ? a.x : 0.f, arawb <= P.alpha_max ? a.y : 0.f);
+        bwd_pair_accumulate<kFix>(S, pg, dx, dy, a, ad, oma, make_float2(Ta, Tb), make_float2(Fa, Fb), cg);
       }
       }
-      if (va) bwd_entry_flush<kFix>(A, s_g, s_wsum, s_wfix, ia, want_w);
-      if (vb) bwd_entry_flush<kFix>(Bn, s_g, s_wsum, s_wfix, ib, want_w);
+      if (va) {
+        const float acc[9] = {S.acc[0].x, S.acc[1].x, S.acc[2].x, S.acc[3].x, S.acc[4].x,
+                              S.acc[5].x, S.acc[6].x, S.acc[7].x, S.acc[8].x};
+        bwd_entry_flush<kFix>(A, acc, S.wsum.x, S.wfix_a, s_g, s_wsum, s_wfix, ia, want_w);
+      }
+      if (vb) {
+        const float acc[9] = {S.acc[0].y, S.acc[1].y, S.acc[2].y, S.acc[3].y, S.acc[4].y,
+                              S.acc[5].y, S.acc[6].y, S.acc[7].y, S.acc[8].y};
+        bwd_entry_flush<kFix>(Bn, acc, S.wsum.y, S.wfix_b, s_g, s_wsum, s_wfix, ib, want_w);
+      }
     }
     __syncthreads();
     if (tid < nb) {
