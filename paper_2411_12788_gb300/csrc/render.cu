@@ -333,27 +333,59 @@ __device__ __forceinline__ void fwd_pixel_of(const ViewDev& V, int tile, int t, 
 // Blends a staged batch of nb entries into the thread's two pixels (same
 // row, so they share the exponent's row part); the warp stops once all
 // its pixels have (checked every 8 entries: a stopped pixel ignores the rest).
+// The staged batch as consecutive entry pairs, so that one 128-bit load gives
+// a quantity of both entries in an aligned register pair for the packed
+// instructions: s_m[j/2] = (mx_j, mx_j+1, my_j, my_j+1), s_ab[j/2] = (a2, a2',
+// b2, b2'), s_cl[j/2] = (c2, c2', log2 o, log2 o').
+__device__ __forceinline__ void stage_pair_slot(float4* s_m, float4* s_ab, float4* s_cl, int k, float2 m, float4 ex) {
+  float* fm = reinterpret_cast<float*>(s_m) + 4 * (k >> 1) + (k & 1);
+  float* fab = reinterpret_cast<float*>(s_ab) + 4 * (k >> 1) + (k & 1);
+  float* fcl = reinterpret_cast<float*>(s_cl) + 4 * (k >> 1) + (k & 1);
+  fm[0] = m.x;
+  fm[2] = m.y;
+  fab[0] = ex.x;
+  fab[2] = ex.y;
+  fcl[0] = ex.z;
+  fcl[2] = ex.w;
+}
+
+// Blends a staged batch of nb entries into the thread's two pixels (same
+// row, so they share the exponent's row part); the warp stops once all
+// its pixels have (checked every 8 entries: a stopped pixel ignores the rest).
+// The exponents of two consecutive entries are evaluated together with the
+// packed FP32x2 instructions (each half rounded exactly as expo_row/expo_pix,
+// so the decisions equal the backward's); blending stays entry by entry.
 template <bool kWantW, bool kCount>
-__device__ __forceinline__ void fwd_batch(FwdPix& q0, FwdPix& q1, int nb, int pos0, const float2* s_xy,
-                                          const float4* s_ex, const float4* s_rgbz, uint32_t* s_wsum,
-                                          const RenderParams& P, int lane) {
+__device__ __forceinline__ void fwd_batch(FwdPix& q0, FwdPix& q1, int nb, int pos0, const float4* s_m,
+                                          const float4* s_ab, const float4* s_cl, const float4* s_rgbz,
+                                          uint32_t* s_wsum, const RenderParams& P, int lane) {
+  const float2 fy = pk_dup(q0.fy), fx0 = pk_dup(q0.fx), fx1 = pk_dup(q1.fx);
   for (int j0 = 0; j0 < nb; j0 += 8) {
     if (__all_sync(0xffffffffu, q0.done && q1.done)) break;
 #pragma unroll
-    for (int u = 0; u < 8; ++u) {
+    for (int u = 0; u < 8; u += 2) {
       const int j = j0 + u;
       if (j >= nb) break;
-      const float2 m = s_xy[j];
-      const float4 ex = s_ex[j];
-      const float2 row = expo_row(ex, q0.fy - m.y);
-      const float e0 = expo_pix(ex, row, q0.fx - m.x);
-      const float e1 = expo_pix(ex, row, q1.fx - m.x);
-      const float w0 = fwd_pix_blend<kCount>(q0, e0, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
-      const float w1 = fwd_pix_blend<kCount>(q1, e1, s_rgbz, j, pos0 + j, P.alpha_max, P.e_min, P.t_min);
-      if (kWantW && __any_sync(0xffffffffu, w0 > 0.f || w1 > 0.f)) {
-        const uint32_t s = __reduce_add_sync(0xffffffffu, __float2uint_rn(w0 * 16777216.f) +
-                                                              __float2uint_rn(w1 * 16777216.f));
-        if (lane == 0) atomicAdd(&s_wsum[j], s);
+      const float4 m4 = s_m[j >> 1], ab4 = s_ab[j >> 1], cl4 = s_cl[j >> 1];
+      const float2 mx = make_float2(m4.x, m4.y), my = make_float2(m4.z, m4.w);
+      const float2 dy = pk_sub(fy, my);
+      const float2 rowx = pk_fma(pk_mul(make_float2(cl4.x, cl4.y), dy), dy, make_float2(cl4.z, cl4.w));
+      const float2 rowy = pk_mul(make_float2(ab4.z, ab4.w), dy);
+      const float2 a2 = make_float2(ab4.x, ab4.y);
+      const float2 e0 = pk_fma(pk_fma(a2, pk_sub(fx0, mx), rowy), pk_sub(fx0, mx), rowx);
+      const float2 e1 = pk_fma(pk_fma(a2, pk_sub(fx1, mx), rowy), pk_sub(fx1, mx), rowx);
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (j + h >= nb) break;
+        const float w0 = fwd_pix_blend<kCount>(q0, h ? e0.y : e0.x, s_rgbz, j + h, pos0 + j + h, P.alpha_max,
+                                               P.e_min, P.t_min);
+        const float w1 = fwd_pix_blend<kCount>(q1, h ? e1.y : e1.x, s_rgbz, j + h, pos0 + j + h, P.alpha_max,
+                                               P.e_min, P.t_min);
+        if (kWantW && __any_sync(0xffffffffu, w0 > 0.f || w1 > 0.f)) {
+          const uint32_t s = __reduce_add_sync(0xffffffffu, __float2uint_rn(w0 * 16777216.f) +
+                                                                __float2uint_rn(w1 * 16777216.f));
+          if (lane == 0) atomicAdd(&s_wsum[j + h], s);
+        }
       }
     }
   }
@@ -363,8 +395,9 @@ template <bool kWantW, bool kCount>
 __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P, FwdOut O) {
   constexpr int kBatch = kTilePixels;
   __shared__ int s_view;
-  __shared__ float2 s_xy[kBatch];
-  __shared__ float4 s_ex[kBatch];
+  __shared__ float4 s_m[kBatch / 2];     // entry pairs: centres
+  __shared__ float4 s_ab[kBatch / 2];    // entry pairs: a2, b2
+  __shared__ float4 s_cl[kBatch / 2];    // entry pairs: c2, log2 o
   __shared__ float4 s_rgbz[kBatch];
   __shared__ uint32_t s_item[kBatch];
   __shared__ uint32_t s_wsum[kBatch];    // 2^-24 fixed point
@@ -396,8 +429,7 @@ __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P,
         const uint32_t item = list_item(P, idx);
         s_item[k] = item;
         const float4 a = P.xy_tau_z[item];
-        s_xy[k] = make_float2(a.x, a.y);
-        s_ex[k] = exponent_form(P.conic_o[item]);
+        stage_pair_slot(s_m, s_ab, s_cl, k, make_float2(a.x, a.y), exponent_form(P.conic_o[item]));
         const float4 c = P.rgb[item];
         s_rgbz[k] = make_float4(c.x, c.y, c.z, a.w);
       }
@@ -405,7 +437,7 @@ __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P,
     __syncthreads();
     const int nb = (int)min(range.y - bstart, (uint32_t)kBatch);
     const int pos0 = (int)(bstart - range.x);
-    fwd_batch<kWantW, kCount>(q0, q1, nb, pos0, s_xy, s_ex, s_rgbz, s_wsum, P, lane);
+    fwd_batch<kWantW, kCount>(q0, q1, nb, pos0, s_m, s_ab, s_cl, s_rgbz, s_wsum, P, lane);
     __syncthreads();
     if (kWantW) {
 #pragma unroll
