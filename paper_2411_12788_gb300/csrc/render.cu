@@ -571,10 +571,161 @@ __device__ __forceinline__ void bwd_entry_flush(const BwdEntry& E, const float* 
   if (kFix && wfix) atomicAdd(&s_wfix[idx], wfix);
 }
 
+// The affine scan of scan_affine within segments of kL lanes (kL a power of
+// two): lane l ends with the composition over the lanes of its segment up to
+// and including l.  The shuffle's segment mask keeps sources in the segment.
+template <int kL>
+__device__ __forceinline__ void scan_affine_seg(float& m, float& f) {
+  constexpr uint32_t kSegMask = (uint32_t)(32 - kL) << 8;
+#pragma unroll
+  for (int off = 1; off < kL; off <<= 1)
+    asm("{\n\t.reg .f32 tm, tf;\n\t.reg .pred p;\n\t"
+        "shfl.sync.up.b32 tm|p, %0, %2, %3, 0xffffffff;\n\t"
+        "shfl.sync.up.b32 tf, %1, %2, %3, 0xffffffff;\n\t"
+        "@p fma.rn.f32 %1, tm, %1, tf;\n\t"
+        "@p mul.f32 %0, %0, tm;\n\t}"
+        : "+f"(m), "+f"(f)
+        : "r"(off), "n"(kSegMask));
+}
+
+// What a chunk walk reads and writes besides the list: the staged batch, the
+// per-pixel state and the per-entry gradient sums in shared memory.
+struct BwdShared {
+  const float2* xy;
+  const float4* ex;
+  const float4* rgb;
+  const float4* pg;
+  float4* st;
+  float (*g)[kRenderThreads];
+  float* wsum;
+  uint32_t* wfix;
+};
+
+// Walks one chunk of a warp's list over the warp's 8x4 block, kSeg pixels
+// per step.  The warp splits into kSeg segments of kL = 32 / kSeg lanes; lane
+// j of each segment holds list entries c + 2j and c + 2j + 1 (those before
+// cnt), and segment s takes pixel s of each run of kSeg pixels of a row.  A
+// chunk thus holds 64 / kSeg entries: a short list tail is walked with
+// several pixels per step instead of idle lanes.  The lane scans run within a
+// segment, and an entry's sums over the segments' pixels are added together
+// before the flush.
+template <bool kFix, int kSeg>
+__device__ __forceinline__ void bwd_walk_chunk(const RenderParams& P, const BwdShared& M, const uint8_t* list, int c,
+                                               int cnt, uint32_t bstart, uint32_t my_nc, int warp, int lane,
+                                               float bxf, float byf, bool want_w) {
+  constexpr int kL = 32 / kSeg;
+  const int j = lane & (kL - 1), seg = lane / kL;
+  __syncwarp();                                 // list stores; the state stores of the last chunk
+  const int ta = c + 2 * j, tb = ta + 1;        // my entries in the list
+  const bool va = ta < cnt, vb = tb < cnt;
+  const int ia = va ? list[ta] : 0, ib = vb ? list[tb] : 0;
+  BwdEntry A, Bn;
+  bwd_entry_load(A, va, M.xy, M.ex, M.rgb, ia);
+  bwd_entry_load(Bn, vb, M.xy, M.ex, M.rgb, ib);
+  BwdSums S;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) S.acc[k] = make_float2(0.f, 0.f);
+  S.wsum = make_float2(0.f, 0.f);
+  S.wfix_a = S.wfix_b = 0u;
+  // the two entries side by side for the packed instructions
+  const float2 mx2 = make_float2(A.mx, Bn.mx), my2 = make_float2(A.my, Bn.my);
+  const float2 exx = make_float2(A.ex.x, Bn.ex.x), exy = make_float2(A.ex.y, Bn.ex.y);
+  const float2 exz = make_float2(A.ex.z, Bn.ex.z), exw = make_float2(A.ex.w, Bn.ex.w);
+  const float2 colx = make_float2(A.col.x, Bn.col.x), coly = make_float2(A.col.y, Bn.col.y);
+  const float2 colz = make_float2(A.col.z, Bn.col.z);
+  const uint32_t posa = bstart + ia, posb = bstart + ib;   // list positions
+  // pixels of this warp still blending at the chunk's first entry
+  const uint32_t pmask = __ballot_sync(0xffffffffu, my_nc > bstart + list[c]);
+  // the block's 4 rows, 8 pixels each: the row part of each entry's
+  // exponent is computed once per row
+#pragma unroll 1
+  for (int r = 0; r < 4; ++r) {
+    if (!((pmask >> (8 * r)) & 0xffu)) continue;
+    // pixel centre minus entry centre, rounded exactly as in the forward
+    const float fy = byf + (float)r;
+    const float2 dy = pk_sub(pk_dup(fy), my2);
+    const float2 rowx = pk_fma(pk_mul(exz, dy), dy, exw), rowy = pk_mul(exy, dy);   // expo_row, both entries
+#pragma unroll 4
+    for (int cx0 = 0; cx0 < 8; cx0 += kSeg) {
+      if (!((pmask >> (8 * r + cx0)) & ((1u << kSeg) - 1u))) continue;
+      const int cx = cx0 + seg;
+      const int pt = warp * 32 + 8 * r + cx;        // the pixel's thread id
+      const float4 st = M.st[pt];
+      const uint32_t nc = __float_as_uint(st.z);
+      const float fx = bxf + (float)cx;
+      const float2 dx = pk_sub(pk_dup(fx), mx2);
+      const float2 e = pk_fma(pk_fma(exx, dx, rowy), dx, rowx);   // expo_pix, both entries
+      const bool acta = posa < nc && e.x >= P.e_min;
+      const bool actb = posb < nc && e.y >= P.e_min;
+      if (!__any_sync(0xffffffffu, acta || actb)) continue;
+      const float4 pg = M.pg[pt];
+      const float arawa = ex2_approx(e.x), arawb = ex2_approx(e.y);
+      const float2 a = make_float2(acta ? fminf(P.alpha_max, arawa) : 0.f, actb ? fminf(P.alpha_max, arawb) : 0.f);
+      const float2 cg = pk_fma(colz, pk_dup(pg.z), pk_fma(coly, pk_dup(pg.y), pk_mul(colx, pk_dup(pg.x))));
+      // the lane's two maps composed, then one scan over the segment's
+      // lanes: the product of (1 - a) and sum a_k cg_k prod_{j<k} (1 - a_j)
+      const float2 oma = pk_sub(make_float2(1.f, 1.f), a);
+      const float2 fab = pk_mul(a, cg);
+      float m = oma.x * oma.y, f = fmaf(oma.x, fab.y, fab.x);
+      scan_affine_seg<kL>(m, f);
+      float mex = __shfl_up_sync(0xffffffffu, m, 1, kL);   // exclusive over the segment's lanes
+      float fex = __shfl_up_sync(0xffffffffu, f, 1, kL);
+      if (j == 0) {
+        mex = 1.f;
+        fex = 0.f;
+      }
+      const float T0 = st.x, F0 = st.y;
+      const float Ta = T0 * mex;                            // T in front of entry A
+      const float Fa = fmaf(Ta, fab.x, fmaf(T0, fex, F0));   // sum_{k<=A} w_k cg_k
+      const float Tb = Ta * oma.x;
+      const float Fb = fmaf(Tb * a.y, cg.y, Fa);
+      // the segment's last lane holds the chunk's totals: carry the pixel's
+      // state forward
+      __syncwarp();
+      if (j == kL - 1) {
+        float2* stp = reinterpret_cast<float2*>(&M.st[pt]);
+        *stp = make_float2(T0 * m, fmaf(T0, f, F0));
+      }
+      // alpha gradient only where the 0.99 clamp is not active
+      const float2 ad = make_float2(arawa <= P.alpha_max ? a.x : 0.f, arawb <= P.alpha_max ? a.y : 0.f);
+      bwd_pair_accumulate<kFix>(S, pg, dx, dy, a, ad, oma, make_float2(Ta, Tb), make_float2(Fa, Fb), cg);
+    }
+  }
+  if (kSeg > 1) {
+    // the segments hold the same entries over different pixels
+#pragma unroll
+    for (int o = kL; o < 32; o <<= 1) {
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        S.acc[k].x += __shfl_xor_sync(0xffffffffu, S.acc[k].x, o);
+        S.acc[k].y += __shfl_xor_sync(0xffffffffu, S.acc[k].y, o);
+      }
+      if (want_w) {
+        S.wsum.x += __shfl_xor_sync(0xffffffffu, S.wsum.x, o);
+        S.wsum.y += __shfl_xor_sync(0xffffffffu, S.wsum.y, o);
+      }
+      if (kFix) {
+        S.wfix_a += __shfl_xor_sync(0xffffffffu, S.wfix_a, o);
+        S.wfix_b += __shfl_xor_sync(0xffffffffu, S.wfix_b, o);
+      }
+    }
+    if (seg != 0) return;
+  }
+  if (va) {
+    const float acc[9] = {S.acc[0].x, S.acc[1].x, S.acc[2].x, S.acc[3].x, S.acc[4].x,
+                          S.acc[5].x, S.acc[6].x, S.acc[7].x, S.acc[8].x};
+    bwd_entry_flush<kFix>(A, acc, S.wsum.x, S.wfix_a, M.g, M.wsum, M.wfix, ia, want_w);
+  }
+  if (vb) {
+    const float acc[9] = {S.acc[0].y, S.acc[1].y, S.acc[2].y, S.acc[3].y, S.acc[4].y,
+                          S.acc[5].y, S.acc[6].y, S.acc[7].y, S.acc[8].y};
+    bwd_entry_flush<kFix>(Bn, acc, S.wsum.y, S.wfix_b, M.g, M.wsum, M.wfix, ib, want_w);
+  }
+}
+
 template <bool kFix>
 __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderParams P, BwdIn B) {
   constexpr int kWarps = kRenderThreads / 32;
-  constexpr int kChunk = 64;                   // entries per warp step
   __shared__ int s_view;
   __shared__ uint32_t s_max_nc;
   __shared__ float2 s_xy[kRenderThreads];
@@ -663,91 +814,23 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
       if (hit) s_list[warp][cnt + __popc(bal & lt_mask)] = (uint8_t)k;
       cnt += __popc(bal);
     }
-    for (int c = 0; c < cnt; c += kChunk) {
-      __syncwarp();                                 // list stores; lane 31's state stores of the last chunk
-      const int ta = c + 2 * lane, tb = ta + 1;     // my entries in the list
-      const bool va = ta < cnt, vb = tb < cnt;
-      const int ia = va ? s_list[warp][ta] : 0, ib = vb ? s_list[warp][tb] : 0;
-      BwdEntry A, Bn;
-      bwd_entry_load(A, va, s_xy, s_ex, s_rgb, ia);
-      bwd_entry_load(Bn, vb, s_xy, s_ex, s_rgb, ib);
-      BwdSums S;
-#pragma unroll
-      for (int k = 0; k < 9; ++k) S.acc[k] = make_float2(0.f, 0.f);
-      S.wsum = make_float2(0.f, 0.f);
-      S.wfix_a = S.wfix_b = 0u;
-      // the two entries side by side for the packed instructions
-      const float2 mx2 = make_float2(A.mx, Bn.mx), my2 = make_float2(A.my, Bn.my);
-      const float2 exx = make_float2(A.ex.x, Bn.ex.x), exy = make_float2(A.ex.y, Bn.ex.y);
-      const float2 exz = make_float2(A.ex.z, Bn.ex.z), exw = make_float2(A.ex.w, Bn.ex.w);
-      const float2 colx = make_float2(A.col.x, Bn.col.x), coly = make_float2(A.col.y, Bn.col.y);
-      const float2 colz = make_float2(A.col.z, Bn.col.z);
-      const uint32_t posa = bstart + ia, posb = bstart + ib;   // list positions
-      // pixels of this warp still blending at the chunk's first entry
-      const uint32_t pmask = __ballot_sync(0xffffffffu, my_nc > bstart + s_list[warp][c]);
-      // the block's 4 rows, 8 pixels each: the row part of each entry's
-      // exponent is computed once per row
-#pragma unroll 1
-      for (int r = 0; r < 4; ++r) {
-      if (!((pmask >> (8 * r)) & 0xffu)) continue;
-      // pixel centre minus entry centre, rounded exactly as in the forward
-      const float fy = byf + (float)r;
-      const float2 dy = pk_sub(pk_dup(fy), my2);
-      const float2 rowx = pk_fma(pk_mul(exz, dy), dy, exw), rowy = pk_mul(exy, dy);   // expo_row, both entries
-#pragma unroll 4
-      for (int cx = 0; cx < 8; ++cx) {
-        const int p = 8 * r + cx;
-        if (!(pmask & (1u << p))) continue;
-        const int pt = warp * 32 + p;                 // the pixel's thread id
-        const float4 st = s_st[pt];
-        const uint32_t nc = __float_as_uint(st.z);
-        const float fx = bxf + (float)cx;
-        const float2 dx = pk_sub(pk_dup(fx), mx2);
-        const float2 e = pk_fma(pk_fma(exx, dx, rowy), dx, rowx);   // expo_pix, both entries
-        const bool acta = posa < nc && e.x >= P.e_min;
-        const bool actb = posb < nc && e.y >= P.e_min;
-        if (!__any_sync(0xffffffffu, acta || actb)) continue;
-        const float4 pg = s_pg[pt];
-        const float arawa = ex2_approx(e.x), arawb = ex2_approx(e.y);
-        const float2 a = make_float2(acta ? fminf(P.alpha_max, arawa) : 0.f, actb ? fminf(P.alpha_max, arawb) : 0.f);
-        const float2 cg = pk_fma(colz, pk_dup(pg.z), pk_fma(coly, pk_dup(pg.y), pk_mul(colx, pk_dup(pg.x))));
-        // the lane's two maps composed, then one scan over the lanes: the
-        // product of (1 - a) and sum a_k cg_k prod_{j<k} (1 - a_j)
-        const float2 oma = pk_sub(make_float2(1.f, 1.f), a);
-        const float2 fab = pk_mul(a, cg);
-        float m = oma.x * oma.y, f = fmaf(oma.x, fab.y, fab.x);
-        scan_affine(m, f);
-        float mex = __shfl_up_sync(0xffffffffu, m, 1);     // exclusive over lanes
-        float fex = __shfl_up_sync(0xffffffffu, f, 1);
-        if (lane == 0) {
-          mex = 1.f;
-          fex = 0.f;
-        }
-        const float T0 = st.x, F0 = st.y;
-        const float Ta = T0 * mex;                          // T in front of entry A
-        const float Fa = fmaf(Ta, fab.x, fmaf(T0, fex, F0));   // sum_{k<=A} w_k cg_k
-        const float Tb = Ta * oma.x;
-        const float Fb = fmaf(Tb * a.y, cg.y, Fa);
-        // lane 31 holds the chunk's totals: carry the pixel's state forward
-        __syncwarp();
-        if (lane == 31) {
-          float2* stp = reinterpret_cast<float2*>(&s_st[pt]);
-          *stp = make_float2(T0 * m, fmaf(T0, f, F0));
-        }
-        // alpha gradient only where the 0.99 clamp is not active
-        const float2 ad = make_float2(arawa <= P.alpha_max ? a.x : 0.f, arawb <= P.alpha_max ? a.y : 0.f);
-        bwd_pair_accumulate<kFix>(S, pg, dx, dy, a, ad, oma, make_float2(Ta, Tb), make_float2(Fa, Fb), cg);
-      }
-      }
-      if (va) {
-        const float acc[9] = {S.acc[0].x, S.acc[1].x, S.acc[2].x, S.acc[3].x, S.acc[4].x,
-                              S.acc[5].x, S.acc[6].x, S.acc[7].x, S.acc[8].x};
-        bwd_entry_flush<kFix>(A, acc, S.wsum.x, S.wfix_a, s_g, s_wsum, s_wfix, ia, want_w);
-      }
-      if (vb) {
-        const float acc[9] = {S.acc[0].y, S.acc[1].y, S.acc[2].y, S.acc[3].y, S.acc[4].y,
-                              S.acc[5].y, S.acc[6].y, S.acc[7].y, S.acc[8].y};
-        bwd_entry_flush<kFix>(Bn, acc, S.wsum.y, S.wfix_b, s_g, s_wsum, s_wfix, ib, want_w);
+    // chunks of 64 entries, one pixel per step; a tail of at most 32, 16 or
+    // 8 entries is walked 2, 4 or 8 pixels per step
+    const BwdShared M{s_xy, s_ex, s_rgb, s_pg, s_st, s_g, s_wsum, s_wfix};
+    for (int c = 0; c < cnt;) {
+      const int rest = cnt - c;
+      if (rest > 32) {
+        bwd_walk_chunk<kFix, 1>(P, M, s_list[warp], c, cnt, bstart, my_nc, warp, lane, bxf, byf, want_w);
+        c += 64;
+      } else if (rest > 16) {
+        bwd_walk_chunk<kFix, 2>(P, M, s_list[warp], c, cnt, bstart, my_nc, warp, lane, bxf, byf, want_w);
+        c += 32;
+      } else if (rest > 8) {
+        bwd_walk_chunk<kFix, 4>(P, M, s_list[warp], c, cnt, bstart, my_nc, warp, lane, bxf, byf, want_w);
+        c += 16;
+      } else {
+        bwd_walk_chunk<kFix, 8>(P, M, s_list[warp], c, cnt, bstart, my_nc, warp, lane, bxf, byf, want_w);
+        c += 8;
       }
     }
     __syncthreads();
