@@ -192,8 +192,8 @@ def kernel_times(collect=True) -> dict:
 # valid while the kernel's source file is the one profiled (its SHA-256) and the workload has the same number
 # of tile entries; otherwise the traffic is reported as null.
 PROFILED_TRAFFIC = {
-    "render_bwd": {"bytes": 590.12e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
-                   "sha256": "97634706ad11eba134b870f8a609f589e4c66070f20da2f1c349139e8ef3b9ed",
+    "render_bwd": {"bytes": 590.40e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
+                   "sha256": "88b4cff041030be110d840112923dc7992aa3ed259cf1c6406989851518c2a87",
                    "profile": "profiles/render_bwd_1M_8views.md"},
 }
 
@@ -274,8 +274,9 @@ def roofline(kt: dict, st: "Step", steps: int, peaks: dict, clocks: dict, name: 
     P = int(st.plan.n_pairs)
     per = {"tile_sort_onesweep": 16 * E, "depth_sort_onesweep": 16 * I, "tile_sort_histogram": 4 * E,
            "depth_sort_histogram": 4 * I, "pair_sort_onesweep": 16 * P, "pair_sort_histogram": 4 * P,
-           # tile lists: the item id and band size of every position, 60 B of state per visible item, 8 B per pair
-           "lists_pairs": 8 * I + 60 * V + 8 * P,
+           # tile lists: the item id and band size of every position, the 32 B binning record of every
+           # visible item, 8 B per pair
+           "lists_pairs": 8 * I + 32 * V + 8 * P,
            # the row-sorted pairs in, one item id per entry out
            "lists_entries": 8 * P + 4 * E,
            # item id, tile count and offset of every item; centre and row parameters of visible ones; entries

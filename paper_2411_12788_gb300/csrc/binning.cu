@@ -72,17 +72,7 @@ __global__ void __launch_bounds__(kDupThreads) duplicate_kernel(const ViewDev* _
       d.cnt = known ? st.tiles[d.item] : 0u;
       if (d.cnt) {
         d.off = offsets[k];
-        const float4 a = st.xy_tau_z[d.item];
-        const float4 b0 = st.bin[2 * d.item], b1 = st.bin[2 * d.item + 1];
-        d.b.mx = a.x;
-        d.b.my = a.y;
-        d.b.tau = a.z;
-        d.b.k = b0.x;
-        d.b.sc = b0.y;
-        d.b.isyy = b0.z;
-        d.b.h = b0.w;
-        d.b.rx = b1.x;
-        d.b.ys = b1.y;
+        d.b = bin_decode(st.bin[2 * d.item], st.bin[2 * d.item + 1]);
         const ViewDev& V = views[d.item / n];
         d.tiles_x = V.tiles_x;
         d.tile_base = V.tile_base;

@@ -51,7 +51,7 @@ struct ItemState {
   float4* rgb;               // (r, g, b, support half-extents as two halves; see pack_extent)
   float4* depth_frame;       // 3 x float4 per item: rows of W = diag(1/s) (R Rq)^T, then e = W p_c
   uint2* rect;               // (tx0 | ty0 << 16, tx1 | ty1 << 16), inclusive bounding box
-  float4* bin;               // 2 x float4 per item: (k, sc, 1/Syy, h), (rx, ys, ty0 as int bits, 0); see BinParams
+  float4* bin;               // 2 x float4 per item: the binning record of bin_decode (with the first band row)
   uint32_t* tiles;           // exact touched-tile count (0 = culled)
   uint32_t* depth_key;       // float bits of z, kCulledKey if culled
   uint32_t* depth_val;       // the item's own index: the depth sort's values

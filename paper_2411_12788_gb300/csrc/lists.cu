@@ -114,11 +114,12 @@ __global__ void __launch_bounds__(32 * kPairWarps) pairs_kernel(ListArgs A) {
       uint32_t item = A.sorted_items[k];
       if (!GS_IN_RANGE(item, A.n_items, A.status)) item = 0;
       const ViewDev& V = A.views[item / A.n];
-      const float4 a = A.st.xy_tau_z[item];
-      const float4 b0 = A.st.bin[2 * item], b1 = A.st.bin[2 * item + 1];
-      s_it[warp][0][lane] = make_float4(a.x, a.y, a.z, b0.x);
-      s_it[warp][1][lane] = make_float4(b0.y, b0.z, b0.w, b1.x);
-      s_it[warp][2][lane] = make_float4(b1.y, __uint_as_float(item), b1.z,
+      // one 32-byte record per item (the gathers follow the depth order)
+      const float4 r0 = A.st.bin[2 * item], r1 = A.st.bin[2 * item + 1];
+      const BinParams b = bin_decode(r0, r1);
+      s_it[warp][0][lane] = make_float4(b.mx, b.my, b.tau, b.k);
+      s_it[warp][1][lane] = make_float4(b.sc, b.isyy, b.h, b.rx);
+      s_it[warp][2][lane] = make_float4(b.ys, __uint_as_float(item), r1.w,
                                         __uint_as_float((uint32_t)V.row_base | ((uint32_t)V.tiles_x << 16)));
     }
   }

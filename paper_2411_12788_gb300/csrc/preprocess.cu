@@ -164,31 +164,14 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
       return 0.5f * (cxx + cyy) + sqrtf(hd * hd + cxy * cxy);
     };
     float lmax = 0.f;
-    BinParams b;
-    b.mx = V.fx * pc.x * iz + V.cx;
-    b.my = V.fy * pc.y * iz + V.cy;
+    const float mx = V.fx * pc.x * iz + V.cx, my = V.fy * pc.y * iz + V.cy;
+    float sq_r = 0.f;
     if (THREE_SIGMA) {
-      // the square of half-width r = ceil(3 sqrt(lambda_max)): with tau = 1,
-      // no slope, no y-dependence and the extreme points out of reach, the
-      // row functions return the square's rows and columns
+      // the square of half-width r = ceil(3 sqrt(lambda_max))
       lmax = eig_max();
-      const float r = ceilf(3.f * sqrtf(lmax));
-      b.tau = 1.f;
-      b.k = 0.f;
-      b.sc = r;
-      b.isyy = 0.f;
-      b.h = r;
-      b.rx = r;
-      b.ys = INFINITY;
-    } else {
-      b.tau = tau;
-      b.k = cxy / cyy;
-      b.sc = sqrtf(det / cyy);
-      b.isyy = 1.f / cyy;
-      b.h = h_sup;
-      b.rx = rx_sup;
-      b.ys = cxy * sqrtf(tau / cxx);
+      sq_r = ceilf(3.f * sqrtf(lmax));
     }
+    const BinParams b = THREE_SIGMA ? bin_params_square(mx, my, sq_r) : bin_params_exact(mx, my, tau, cxx, cyy, cxy, det);
     // exact tile count, row by row
     uint32_t count = 0;
     int ty0 = 0, ty1 = -1;
@@ -210,8 +193,10 @@ __global__ void __launch_bounds__(kPreThreads) preprocess_kernel(PreParams P) {
     entries += count;
     P.st.xy_tau_z[item] = make_float4(b.mx, b.my, b.tau, pc.z);
     P.st.conic_o[item] = make_float4(A, B, C, o);
-    P.st.bin[2 * item] = make_float4(b.k, b.sc, b.isyy, b.h);
-    P.st.bin[2 * item + 1] = make_float4(b.rx, b.ys, __int_as_float(ty0), 0.f);   // + first band row
+    // the binning record (see bin_decode) with the first band row
+    P.st.bin[2 * item] = THREE_SIGMA ? make_float4(mx, my, 1.f, sq_r) : make_float4(mx, my, tau, cxx);
+    P.st.bin[2 * item + 1] = THREE_SIGMA ? make_float4(0.f, 0.f, -1.f, __int_as_float(ty0))
+                                         : make_float4(cyy, cxy, det, __int_as_float(ty0));
 
     // colour (Sec. 3.1): SH in the direction camera centre -> Gaussian
     float dx = p.x - V.campos[0], dy = p.y - V.campos[1], dz = p.z - V.campos[2];

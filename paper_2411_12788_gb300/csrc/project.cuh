@@ -138,6 +138,52 @@ struct BinParams {
   float h, rx, ys;     // half-height sqrt(tau Syy), half-width, y of the rightmost point
 };
 
+// The row parameters of an exact support q(d) <= tau of the 2-D covariance
+// (Sxx, Syy, Sxy) with determinant det: x | y decomposition x = k y +- sc
+// sqrt(tau - y^2 / Syy), half-height sqrt(tau Syy), half-width sqrt(tau Sxx)
+// reached at y = ys.  Explicitly rounded operations, so that every kernel
+// that rebuilds them from the same inputs gets the same bits.
+__device__ __forceinline__ BinParams bin_params_exact(float mx, float my, float tau, float sxx, float syy, float sxy,
+                                                      float det) {
+  BinParams b;
+  b.mx = mx;
+  b.my = my;
+  b.tau = tau;
+  b.k = __fdiv_rn(sxy, syy);
+  b.sc = __fsqrt_rn(__fdiv_rn(det, syy));
+  b.isyy = __frcp_rn(syy);
+  b.h = __fsqrt_rn(__fmul_rn(tau, syy));
+  b.rx = __fsqrt_rn(__fmul_rn(tau, sxx));
+  b.ys = __fmul_rn(sxy, __fsqrt_rn(__fdiv_rn(tau, sxx)));
+  return b;
+}
+
+// The square of half-width r: with tau = 1, no slope, no y-dependence and
+// the extreme points out of reach, the row functions return the square's
+// rows and columns.
+__device__ __forceinline__ BinParams bin_params_square(float mx, float my, float r) {
+  BinParams b;
+  b.mx = mx;
+  b.my = my;
+  b.tau = 1.f;
+  b.k = 0.f;
+  b.sc = r;
+  b.isyy = 0.f;
+  b.h = r;
+  b.rx = r;
+  b.ys = INFINITY;
+  return b;
+}
+
+// An item's binning record, two float4 written by the preprocess: the inputs
+// of its row parameters, (mx, my, tau, Sxx), (Syy, Sxy, det, first band row)
+// for an exact support (det > 0) or (mx, my, 1, r), (0, 0, -1, first band
+// row) for a square of half-width r.  The consumers rebuild the parameters
+// with the functions above, so one 32-byte read per item serves them.
+__device__ __forceinline__ BinParams bin_decode(float4 r0, float4 r1) {
+  return r1.z > 0.f ? bin_params_exact(r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z) : bin_params_square(r0.x, r0.y, r0.w);
+}
+
 __device__ __forceinline__ bool row_tiles(const BinParams& b, int ty, int tiles_x, int* tx_a, int* tx_b) {
   const float lo = __fsub_rn((float)(ty * kTile) + 0.5f, b.my);
   const float hi = __fadd_rn(lo, (float)(kTile - 1));
