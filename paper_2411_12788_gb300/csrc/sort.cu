@@ -183,6 +183,9 @@ __global__ void lookback_timeout_probe_kernel(const uint32_t* __restrict__ lookb
 constexpr size_t kOnesweepDynSmem = 3 * (size_t)kSortTile * sizeof(uint32_t);
 constexpr long kCopyWaitLimit = 1L << 22;
 
+// kDigitBits: the widest digit the instance ranks (8, or 4 for the narrow
+// last pass of a sort whose bit count is not a multiple of 8).
+template <int kDigitBits>
 __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift, uint32_t dmask,
@@ -260,7 +263,7 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
     // key); a bit's ballot XOR this lane's bit replicated marks them
     uint32_t diff = ~__ballot_sync(0xffffffffu, valid);
 #pragma unroll
-    for (int b = 0; b < kRadixBits; ++b) {
+    for (int b = 0; b < kDigitBits; ++b) {      // digit bits past the pass's mask are zero
       const uint32_t bit = (d >> b) & 1u;
       diff |= __ballot_sync(0xffffffffu, bit) ^ (0u - bit);
     }
@@ -473,7 +476,10 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
     return cudaErrorMisalignedAddress;     // the bulk copies need 16-byte aligned rows
   static std::atomic<uint64_t> attr_done{0};
   cudaError_t ea = once_per_device(attr_done, [] {
-    return cudaFuncSetAttribute(radix_onesweep_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(radix_onesweep_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kOnesweepDynSmem);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(radix_onesweep_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)kOnesweepDynSmem);
   });
   if (ea != cudaSuccess) return ea;
@@ -494,10 +500,12 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
            (radix_scan_hist_kernel<<<passes, kRadix, 0, stream>>>(s.hist)));
   uint32_t *kin = keys, *kout = keys_alt, *vin = vals, *vout = vals_alt;
   for (int p = 0; p < passes; ++p) {
+    const uint32_t dmask = digit_mask(bits, p * kRadixBits);
+    // a pass of at most 4 digit bits ranks with 4 ballots per key instead of 8
+    auto pass = dmask < 16u ? radix_onesweep_kernel<4> : radix_onesweep_kernel<8>;
     GS_TIMED(depth ? "depth_sort_onesweep" : pairs ? "pair_sort_onesweep" : "tile_sort_onesweep", stream,
-             (radix_onesweep_kernel<<<(unsigned)tiles, kSortThreads, kOnesweepDynSmem, stream>>>(
-                 kin, vin, kout, vout, n, p * kRadixBits, digit_mask(bits, p * kRadixBits),
-                 s.hist + p * kRadix, s.counters + p,
+             (pass<<<(unsigned)tiles, kSortThreads, kOnesweepDynSmem, stream>>>(
+                 kin, vin, kout, vout, n, p * kRadixBits, dmask, s.hist + p * kRadix, s.counters + p,
                  s.lookback + (size_t)p * tiles * kRadix, status)));
     std::swap(kin, kout);
     std::swap(vin, vout);
