@@ -51,6 +51,19 @@ __device__ __forceinline__ void stage_sh(const float* __restrict__ sh, int sh_co
                                          float* s_sh) {
   constexpr int per = 3 * K, row = sh_row_floats<K>();
   const int64_t rows = (n - i0 < THREADS) ? (n - i0) : (int64_t)THREADS;
+  if constexpr (per % 4 == 0) {
+    // rows stored back to back at the degree's own width and 16-byte aligned:
+    // 128-bit loads and stores (a float4 never straddles two rows)
+    const float* base = sh + i0 * per;
+    if (sh_coeffs == K && (reinterpret_cast<uintptr_t>(base) & 15u) == 0) {
+      constexpr int q = per / 4;
+      for (int f = threadIdx.x; f < rows * q; f += THREADS) {
+        const int g = f / q, c4 = f - g * q;
+        reinterpret_cast<float4*>(s_sh + g * row)[c4] = reinterpret_cast<const float4*>(base)[f];
+      }
+      return;
+    }
+  }
   for (int f = threadIdx.x; f < rows * per; f += THREADS) {
     const int g = f / per, c = f - g * per;
     s_sh[g * row + c] = sh[(i0 + g) * (int64_t)sh_coeffs * 3 + c];
@@ -483,7 +496,23 @@ __global__ void __launch_bounds__(kPreBwdThreads) preprocess_backward_kernel(Pre
   {
     constexpr int per = 3 * K;
     const int64_t rows = (P.n - i0 < kPreBwdThreads) ? (P.n - i0) : (int64_t)kPreBwdThreads;
-    if (P.overwrite) {
+    float* base = P.d_sh + i0 * per;
+    const bool vec = per % 4 == 0 && P.sh_coeffs == K && (reinterpret_cast<uintptr_t>(base) & 15u) == 0;
+    if (vec) {
+      // rows back to back at the degree's own width: 128-bit accesses
+      constexpr int q = per / 4 > 0 ? per / 4 : 1;
+      for (int f = threadIdx.x; f < rows * q; f += kPreBwdThreads) {
+        const int g = f / q, c4 = f - g * q;
+        const float4 v = reinterpret_cast<const float4*>(s_dsh + g * row)[c4];
+        float4* dst = reinterpret_cast<float4*>(base) + f;
+        if (P.overwrite) {
+          *dst = v;
+        } else if (v.x != 0.f || v.y != 0.f || v.z != 0.f || v.w != 0.f) {
+          const float4 o = *dst;
+          *dst = make_float4(o.x + v.x, o.y + v.y, o.z + v.z, o.w + v.w);
+        }
+      }
+    } else if (P.overwrite) {
       const int full = 3 * P.sh_coeffs;
       for (int f = threadIdx.x; f < rows * full; f += kPreBwdThreads) {
         const int g = f / full, c = f - g * full;
