@@ -695,6 +695,9 @@ def run_serving(st: Step, args) -> dict:
     from paper_2411_12788_gb300 import serve
     n = args.serve_requests
     skip = n // 11
+    # the earlier phases' cached blocks go back to the device, so that the
+    # servers' buffers are fresh allocations made before their clocks start
+    torch.cuda.empty_cache()
 
     def once(rate, name, streams, views):
         trace = serve.poisson_trace(n, rate=rate, seed=3)

