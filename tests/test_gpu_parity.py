@@ -562,14 +562,17 @@ def test_training_scale_sampled_pixels():
 
 
 # ---------------------------------------------------------------- gradient buffer modes
-@pytest.mark.parametrize("deg", [0, 3])
-def test_backward_overwrite_mode_equals_accumulate_into_zeros(deg):
+@pytest.mark.parametrize("deg,wide", [(0, True), (3, True), (1, False), (3, False)])
+def test_backward_overwrite_mode_equals_accumulate_into_zeros(deg, wide):
     """GS_FLAG_ZERO_ACCUM writes every attribute gradient (the buffers' old
     contents, here NaN, are never read); without it the gradients are added
-    to what the buffers hold."""
+    to what the buffers hold.  With SH rows stored wider than the degree and
+    with rows of exactly the degree's width (degrees 1 and 3 then take the
+    128-bit staging and write-out of the SH rows)."""
     _need_gpu()
     sc = scenes.cluster_scene(30000, 16, seed=17, sh_degree=deg)
-    sc.sh = np.concatenate([sc.sh, np.zeros((sc.n, 2, 3), np.float32)], 1)    # stored rows wider than the degree
+    if wide:
+        sc.sh = np.concatenate([sc.sh, np.zeros((sc.n, 2, 3), np.float32)], 1)    # stored rows wider than the degree
     cams = [scenes.ring_camera(0.5, 96, 80), scenes.ring_camera(2.6, 64, 48)]
     g = raster.GaussianTensors.from_scene(sc)
     fr = raster.forward(g, cams)
