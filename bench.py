@@ -192,8 +192,8 @@ def kernel_times(collect=True) -> dict:
 # valid while the kernel's source file is the one profiled (its SHA-256) and the workload has the same number
 # of tile entries; otherwise the traffic is reported as null.
 PROFILED_TRAFFIC = {
-    "render_bwd": {"bytes": 590.40e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
-                   "sha256": "88b4cff041030be110d840112923dc7992aa3ed259cf1c6406989851518c2a87",
+    "render_bwd": {"bytes": 590.44e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
+                   "sha256": "9dd6bcf9c1548fa8a38ed2697c349416a89dcea6f49fbfbacc92ede5a4600de7",
                    "profile": "profiles/render_bwd_1M_8views.md"},
 }
 

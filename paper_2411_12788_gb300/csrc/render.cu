@@ -485,8 +485,10 @@ struct BwdIn {
 // each warp lists the batch entries whose support box meets its 8x4 block
 // (an entry outside the box was blended at none of the block's pixels), then
 // takes 64 consecutive listed entries at a time (lane l holds the 2l-th and
-// (2l + 1)-th) and walks its 32 pixels.  Each lane composes the affine maps x -> (1 - a) x + a (c.g)
-// of its two entries, one 5-step shuffle scan over the lanes gives both
+// (2l + 1)-th) and walks its 32 pixels; a list tail of at most 32, 16 or 8
+// entries is walked 2, 4 or 8 pixels per step by lane segments (see
+// bwd_walk_chunk).  Each lane composes the affine maps x -> (1 - a) x + a (c.g)
+// of its two entries, one shuffle scan over the lanes gives both
 // prefix quantities for the lane's first entry, and the second follows from
 // the first in registers; the pixel's state is continued from chunk to chunk
 // through shared memory.  Each lane sums its entries' gradients over the
