@@ -164,6 +164,8 @@ SortLayout sort_layout(const gs_plan& p) {
     const size_t c2 = np / kListPairsPerChunk + (size_t)rows + 1;   // second-level chunks, at most
     L.chunks = take(16 * c2);
     L.chunk_cnt = take(4 * c2);
+    L.tile_order = take(4 * (size_t)std::max(p.total_tiles, 1));
+    L.tile_hist = take(4 * 2 * (size_t)kTileBuckets);
   } else {
     L.keys = take(4 * e);
     L.keys_alt = take(4 * e);
@@ -443,6 +445,8 @@ gs_status gs_bin_sort(const gs_plan* plan, void* pre_ws, void* sort_ws, size_t s
     a.chunk_cnt = at<uint32_t>(sort_ws, S.chunk_cnt);
     a.scan_total = at<unsigned long long>(sort_ws, S.scan_blocks + scan_block_bytes(std::max(plan->total_tiles, 1)));
     a.status = status;
+    a.tile_order = at<uint32_t>(sort_ws, S.tile_order);
+    a.tile_hist = at<uint32_t>(sort_ws, S.tile_hist);
     return cuda_status(launch_lists(a, stream));
   }
   if (plan->n_entries > 0) {
@@ -476,7 +480,8 @@ gs_status gs_render_fwd(const gs_plan* plan, const gs_config* cfg, void* pre_ws,
     if (e != cudaSuccess) return GS_ERR_CUDA;
   }
   e = launch_render_fwd(at<ViewDev>(pre_ws, L.views), plan->n_views, plan->n, plan->total_tiles,
-                        at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals), item_state(pre_ws, L), *cfg,
+                        at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals),
+                        S.lists ? at<uint32_t>(sort_ws, S.tile_order) : nullptr, item_state(pre_ws, L), *cfg,
                         *out, stream);
   return cuda_status(e);
 }
@@ -504,7 +509,8 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
   const ItemState st = item_state(pre_ws, L);
   float4* grad2d = at<float4>(pre_ws, L.grad2d);
   e = launch_render_bwd(at<ViewDev>(pre_ws, L.views), plan->n_views, n, plan->total_tiles,
-                        at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals), st, *cfg, dL_dimage, image,
+                        at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals),
+                        S.lists ? at<uint32_t>(sort_ws, S.tile_order) : nullptr, st, *cfg, dL_dimage, image,
                         n_contrib, grad2d, g->weight_sum, g->weight_sum_fixed, stream);
   if (e == cudaSuccess)
     e = launch_preprocess_backward(*scene, at<ViewDev>(pre_ws, L.views), plan->n_views, *cfg, st.tiles, grad2d, *g,

@@ -80,7 +80,7 @@ struct SortLayout {
   bool lists;
   size_t keys, keys_alt, vals, vals_alt, ranges, radix_scratch;
   size_t pkey, pkey_alt, pval, pval_alt, pair_radix, row_T, row_start, c2_start, cnt2_off, counts2, prefix2,
-      tile_count, tile_start, scan_blocks, chunks, chunk_cnt;
+      tile_count, tile_start, scan_blocks, chunks, chunk_cnt, tile_order, tile_hist;
   int rows;
   int64_t counts2_n;
   size_t total;
@@ -198,11 +198,12 @@ cudaError_t launch_duplicate(const ViewDev* views, int n_views, int64_t n_items,
                              uint32_t* status, cudaStream_t stream);
 cudaError_t launch_ranges(const uint32_t* keys, int64_t n_entries, uint2* ranges, int total_tiles,
                           cudaStream_t stream);
+// order: the tiles' launch order written by the tile-list builder (null: tile id order)
 cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
-                              const uint32_t* vals, const ItemState& st, const gs_config& cfg,
+                              const uint32_t* vals, const uint32_t* order, const ItemState& st, const gs_config& cfg,
                               const gs_fwd_outputs& out, cudaStream_t stream);
 cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
-                              const uint32_t* vals, const ItemState& st, const gs_config& cfg,
+                              const uint32_t* vals, const uint32_t* order, const ItemState& st, const gs_config& cfg,
                               const float* dL_dimage, const float* image, const uint32_t* n_contrib,
                               float4* grad2d, float* weight_sum, uint64_t* weight_sum_fixed, cudaStream_t stream);
 // ---- tile lists by counting placement (lists.cu) ----------------------------
@@ -231,7 +232,13 @@ struct ListArgs {
   uint64_t* scan_blocks;
   unsigned long long* scan_total;
   uint32_t* status;
+  // launch order of the render kernels' tiles, longest list first (tiles
+  // bucketed by the bit length of their list), and the buckets' counts and
+  // cursors (kTileBuckets each, zeroed before the tile scan)
+  uint32_t* tile_order;
+  uint32_t* tile_hist;
 };
+constexpr int kTileBuckets = 33;    // bit lengths 0 .. 32 of a list length
 size_t list_pair_radix_bytes(int64_t pairs);
 cudaError_t launch_lists(const ListArgs& a, cudaStream_t stream);
 

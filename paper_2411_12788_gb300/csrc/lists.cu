@@ -296,6 +296,15 @@ __global__ void __launch_bounds__(32 * kL2Warps) l2_count_kernel(ListArgs A) {
   }
 }
 
+// The identity launch order (no entries).
+__global__ void identity_order_kernel(uint32_t* order, int n) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) order[t] = (uint32_t)t;
+}
+
+// Bucket of a tile's list length: its bit length (0 for an empty list).
+__device__ __forceinline__ uint32_t tile_bucket(uint32_t len) { return len ? 32u - (uint32_t)__clz(len) : 0u; }
+
 // Per row: exclusive scan of each column's counts over the row's chunks
 // (into prefix2), and the tile totals.  Block per (row, 32 columns); its
 // warps split the row's chunks, sum their share, and then scan it from the
@@ -327,13 +336,37 @@ __global__ void __launch_bounds__(32 * kTileScanWarps) l2_tile_kernel(ListArgs A
     A.prefix2[i] = run;
     run += (uint32_t)A.counts2[i];
   }
-  if (warp == kTileScanWarps - 1) A.tile_count[V.tile_base + (r - V.row_base) * tx_n + t] = run;
+  if (warp == kTileScanWarps - 1) {
+    A.tile_count[V.tile_base + (r - V.row_base) * tx_n + t] = run;
+    // the tile's length bucket for the render kernels' launch order
+    // (warp-aggregated: one atomic per bucket present in the warp)
+    const uint32_t b = tile_bucket(run);
+    const uint32_t peers = __match_any_sync(__activemask(), b);
+    if (lane == __ffs(peers) - 1) atomicAdd(&A.tile_hist[b], (uint32_t)__popc(peers));
+  }
 }
 
-// [start, end) of every tile; checks the entry total against the preprocess's.
+// [start, end) of every tile and the tiles' launch order; checks the entry
+// total against the preprocess's.
 __global__ void l2_ranges_kernel(ListArgs A) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t < A.total_tiles) A.ranges[t] = make_uint2(A.tile_start[t], A.tile_start[t] + A.tile_count[t]);
+  if (t < A.total_tiles) {
+    const uint32_t c = A.tile_count[t];
+    A.ranges[t] = make_uint2(A.tile_start[t], A.tile_start[t] + c);
+    // launch order, longest lists first: the tile goes after every tile of
+    // a longer bucket, at its bucket's cursor (any order inside a bucket)
+    const uint32_t b = tile_bucket(c);
+    uint32_t off = 0;
+    for (int k = kTileBuckets - 1; k > (int)b; --k) off += A.tile_hist[k];
+    const uint32_t peers = __match_any_sync(__activemask(), b);
+    const int lane = threadIdx.x & 31, leader = __ffs(peers) - 1;
+    uint32_t base = 0;
+    if (lane == leader) base = atomicAdd(&A.tile_hist[kTileBuckets + b], (uint32_t)__popc(peers));
+    base = __shfl_sync(peers, base, leader);
+    const uint32_t pos = off + base + (uint32_t)__popc(peers & ((1u << lane) - 1u));
+    if (pos < (uint32_t)A.total_tiles) A.tile_order[pos] = (uint32_t)t;
+    else atomicOr(A.status, kStatusEntryMismatch);
+  }
   if (t == 0 && *A.scan_total != (unsigned long long)A.n_entries) atomicOr(A.status, kStatusEntryMismatch);
 }
 
@@ -459,9 +492,12 @@ size_t list_pair_radix_bytes(int64_t pairs) { return radix_scratch_bytes(pairs, 
 
 cudaError_t launch_lists(const ListArgs& a, cudaStream_t stream) {
   if (a.n_entries <= 0 || a.n_pairs <= 0) {
-    // no entries: every range is empty
-    if (a.total_tiles > 0) return cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)a.total_tiles, stream);
-    return cudaSuccess;
+    // no entries: every range is empty, and the tiles launch in id order
+    if (a.total_tiles <= 0) return cudaSuccess;
+    cudaError_t e0 = cudaMemsetAsync(a.ranges, 0, sizeof(uint2) * (size_t)a.total_tiles, stream);
+    if (e0 != cudaSuccess) return e0;
+    identity_order_kernel<<<ceil_div(a.total_tiles, 256), 256, 0, stream>>>(a.tile_order, a.total_tiles);
+    return cudaGetLastError();
   }
   static std::atomic<uint64_t> attr_done{0};
   cudaError_t e = once_per_device(attr_done, [] {
@@ -489,6 +525,8 @@ cudaError_t launch_lists(const ListArgs& a, cudaStream_t stream) {
   GS_TIMED("lists_rows", stream, (rows_kernel<<<1, 1024, 0, stream>>>(a)));
   GS_TIMED("lists_rows", stream, (chunk_table_kernel<<<ceil_div(c2_max, 256), 256, 0, stream>>>(a)));
   GS_TIMED("lists_tile_count", stream, (l2_count_kernel<<<l2_blocks, 32 * kL2Warps, smem2, stream>>>(a)));
+  e = cudaMemsetAsync(a.tile_hist, 0, 2 * kTileBuckets * sizeof(uint32_t), stream);
+  if (e != cudaSuccess) return e;
   GS_TIMED("lists_tile_scan", stream,
            (l2_tile_kernel<<<dim3(a.rows, (a.max_tx + 31) / 32), 32 * kTileScanWarps, 0, stream>>>(a)));
   e = cudaGetLastError();

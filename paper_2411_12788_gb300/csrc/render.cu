@@ -54,6 +54,11 @@ struct RenderParams {
   float bg[3];
   uint32_t* status;             // device status word (the checked build's index checks)
   const unsigned long long* n_entries;
+  // launch order of the tiles (block b renders tile order[b]: the longest
+  // lists start first, so that the grid does not end on a few long tiles);
+  // null for the identity
+  const uint32_t* order;
+  int total_tiles;
 };
 
 // The item of list position idx, with the checked build's checks: a position
@@ -402,7 +407,12 @@ __global__ void __launch_bounds__(kFwdThreads) render_fwd_kernel(RenderParams P,
   __shared__ uint32_t s_item[kBatch];
   __shared__ uint32_t s_wsum[kBatch];    // 2^-24 fixed point
 
-  const int tile = blockIdx.x;
+  const uint32_t tile_u = P.order ? P.order[blockIdx.x] : (uint32_t)blockIdx.x;
+  if (tile_u >= (uint32_t)P.total_tiles) {        // an order that names no tile: record, touch nothing
+    if (threadIdx.x == 0) atomicOr(P.status, kStatusBounds);
+    return;
+  }
+  const int tile = (int)tile_u;
   const int tid = threadIdx.x, lane = tid & 31;
   if (tid == 0) s_view = find_view(P.views, P.n_views, tile);
   s_wsum[tid] = 0u;
@@ -745,7 +755,12 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
   __shared__ float4 s_st[kRenderThreads];
   __shared__ uint32_t s_warp_nc[kWarps];
 
-  const int tile = blockIdx.x;
+  const uint32_t tile_u = P.order ? P.order[blockIdx.x] : (uint32_t)blockIdx.x;
+  if (tile_u >= (uint32_t)P.total_tiles) {        // an order that names no tile: record, touch nothing
+    if (threadIdx.x == 0) atomicOr(P.status, kStatusBounds);
+    return;
+  }
+  const int tile = (int)tile_u;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   if (tid == 0) {
     s_view = find_view(P.views, P.n_views, tile);
@@ -879,6 +894,8 @@ RenderParams make_params(const ViewDev* views, int n_views, int64_t n, const uin
   P.depth_frame = st.depth_frame;
   P.status = st.status;
   P.n_entries = st.n_entries;
+  P.order = nullptr;
+  P.total_tiles = 0;
   P.alpha_max = cfg.alpha_max;
   P.e_min = (float)log2((double)cfg.alpha_min);
   P.t_min = cfg.t_min;
@@ -891,9 +908,11 @@ RenderParams make_params(const ViewDev* views, int n_views, int64_t n, const uin
 }  // namespace
 
 cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
-                              const uint32_t* vals, const ItemState& st, const gs_config& cfg,
+                              const uint32_t* vals, const uint32_t* order, const ItemState& st, const gs_config& cfg,
                               const gs_fwd_outputs& out, cudaStream_t stream) {
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
+  P.order = order;
+  P.total_tiles = total_tiles;
   FwdOut O{out.image, out.final_T, out.n_contrib, out.imax, out.wmax, out.depth, out.depth_blend,
            out.weight_sum, out.max_area, out.weight_sum_fixed, out.depth_center, out.n_blended};
   if (total_tiles > 0) {
@@ -911,10 +930,12 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
 }
 
 cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
-                              const uint32_t* vals, const ItemState& st, const gs_config& cfg,
+                              const uint32_t* vals, const uint32_t* order, const ItemState& st, const gs_config& cfg,
                               const float* dL_dimage, const float* image, const uint32_t* n_contrib,
                               float4* grad2d, float* weight_sum, uint64_t* weight_sum_fixed, cudaStream_t stream) {
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
+  P.order = order;
+  P.total_tiles = total_tiles;
   BwdIn B{dL_dimage, image, n_contrib, grad2d, weight_sum, weight_sum_fixed};
   if (total_tiles > 0) {
     if (weight_sum_fixed)
