@@ -509,8 +509,7 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
   const ItemState st = item_state(pre_ws, L);
   float4* grad2d = at<float4>(pre_ws, L.grad2d);
   e = launch_render_bwd(at<ViewDev>(pre_ws, L.views), plan->n_views, n, plan->total_tiles,
-                        at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals),
-                        S.lists ? at<uint32_t>(sort_ws, S.tile_order) : nullptr, st, *cfg, dL_dimage, image,
+                        at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals), st, *cfg, dL_dimage, image,
                         n_contrib, grad2d, g->weight_sum, g->weight_sum_fixed, stream);
   if (e == cudaSuccess)
     e = launch_preprocess_backward(*scene, at<ViewDev>(pre_ws, L.views), plan->n_views, *cfg, st.tiles, grad2d, *g,

@@ -56,7 +56,7 @@ struct RenderParams {
   const unsigned long long* n_entries;
   // launch order of the tiles (block b renders tile order[b]: the longest
   // lists start first, so that the grid does not end on a few long tiles);
-  // null for the identity
+  // null for the identity (the backward)
   const uint32_t* order;
   int total_tiles;
 };
@@ -930,12 +930,11 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
 }
 
 cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
-                              const uint32_t* vals, const uint32_t* order, const ItemState& st, const gs_config& cfg,
+                              const uint32_t* vals, const ItemState& st, const gs_config& cfg,
                               const float* dL_dimage, const float* image, const uint32_t* n_contrib,
                               float4* grad2d, float* weight_sum, uint64_t* weight_sum_fixed, cudaStream_t stream) {
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
-  P.order = order;
-  P.total_tiles = total_tiles;
+  P.total_tiles = total_tiles;                   // tiles in id order (no launch order)
   BwdIn B{dL_dimage, image, n_contrib, grad2d, weight_sum, weight_sum_fixed};
   if (total_tiles > 0) {
     if (weight_sum_fixed)
