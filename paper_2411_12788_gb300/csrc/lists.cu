@@ -27,7 +27,10 @@
 // is stable): exactly the order of a stable sort of the entries by tile id.
 // Traffic: 4 B of output per entry plus about 40 B per pair, against 44 B
 // per entry for emitting every entry and sorting the entries by tile id
-// (about 2.7 entries per pair at the training workloads).  Consistency checks:
+// (about 2.7 entries per pair at the training workloads).  The tile scan and
+// the ranges pass also write the forward's launch order of the tiles,
+// longest list first (tiles bucketed by the bit length of their list).
+// Consistency checks:
 // the pairs written equal the preprocess's count and the entries placed equal
 // the scanned tile counts; a mismatch sets kStatusEntryMismatch.
 #include "project.cuh"
