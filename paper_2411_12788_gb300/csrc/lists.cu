@@ -41,7 +41,7 @@ namespace {
 
 constexpr int kL2Warps = 4;
 constexpr int kL2EmitWarps = 4;
-constexpr int kStageCap = 1024;            // entries a second-level chunk stages in shared memory
+constexpr int kStageCap = 768;             // entries a second-level chunk stages in shared memory
 constexpr int kRowBits = 12;               // kListRowsMax == 1 << kRowBits
 constexpr uint32_t kRowMask = (1u << kRowBits) - 1u;
 static_assert(kListRowsMax <= (1 << kRowBits), "row ids must fit the key's row bits");
