@@ -17,7 +17,7 @@ namespace gs {
 
 namespace {
 
-constexpr int kPreThreads = 128;
+constexpr int kPreThreads = 64;
 constexpr float kLog2eF = 1.4426950408889634f;
 constexpr float kLn2F = 0.6931471805599453f;
 
@@ -278,7 +278,7 @@ struct PreBwdParams {
   bool overwrite;         // write the gradients (every row) instead of adding to them
 };
 
-constexpr int kPreBwdThreads = 64;
+constexpr int kPreBwdThreads = 32;
 
 // One thread per Gaussian; its SH row and the row's gradient live in shared
 // memory (per-thread rows, see sh_row_floats) rather than in registers: at
