@@ -95,7 +95,7 @@ __device__ __forceinline__ int run_owner(uint32_t start, uint32_t len, uint32_t 
 // finds its pair's item (run_owner), evaluates that row's columns with
 // row_tiles (the same arithmetic the preprocess counted with) and writes the
 // pair at the run's start + its index: consecutive lanes, consecutive slots.
-constexpr int kPairWarps = 8;
+constexpr int kPairWarps = 4;
 
 __global__ void __launch_bounds__(32 * kPairWarps) pairs_kernel(ListArgs A) {
   // each lane's item record as three float4 (one 128-bit shared access each):
