@@ -373,11 +373,11 @@ gs_status gs_preprocess(gs_plan* plan, const gs_scene* scene, const gs_config* c
     if (lists_path(*plan))
       e = gather_exclusive_scan(st.band_rows, at<uint32_t>(pre_ws, L.sorted_items), at<uint32_t>(pre_ws, L.pair_offsets),
                                 plan->n_items, at<uint64_t>(pre_ws, L.scan_blocks),
-                                at<unsigned long long>(pre_ws, L.status + 16), stream);
+                                at<unsigned long long>(pre_ws, L.status + 16), stream, status);
     else
       e = gather_exclusive_scan(st.tiles, at<uint32_t>(pre_ws, L.sorted_items), at<uint32_t>(pre_ws, L.offsets),
                                 plan->n_items, at<uint64_t>(pre_ws, L.scan_blocks),
-                                at<unsigned long long>(pre_ws, L.n_entries), stream);
+                                at<unsigned long long>(pre_ws, L.n_entries), stream, status);
   }
   if (e != cudaSuccess) return GS_ERR_CUDA;
   GS_TIMED("preprocess_readback", stream,

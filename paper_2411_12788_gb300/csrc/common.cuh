@@ -161,17 +161,19 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
                              cudaStream_t stream, const char* tag);
 
 // ---- exclusive scan of gathered counts (sort.cu) ---------------------------
-constexpr int kScanThreads = 256;
-constexpr int kScanItems = 8;
+constexpr int kScanThreads = 512;
+constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 size_t scan_block_bytes(int64_t n);
 // Self-test of the sort's bounded look-back wait (scratch: 3 * 256 words).
 cudaError_t lookback_timeout_probe(uint32_t* scratch, uint32_t* status, cudaStream_t stream);
 // out[k] = sum_{j<k} counts[idx[j]] (idx == nullptr: counts[j]); *total = sum of
-// all (device, 64-bit).
+// all (device, 64-bit).  One pass with a decoupled look-back; block_scratch:
+// scan_block_bytes(n), cleared by the call; a look-back wait that runs out
+// records kStatusTimeout in *status (if given).
 cudaError_t gather_exclusive_scan(const uint32_t* counts, const uint32_t* idx, uint32_t* out,
                                   int64_t n, uint64_t* block_scratch, unsigned long long* total,
-                                  cudaStream_t stream);
+                                  cudaStream_t stream, uint32_t* status = nullptr);
 
 // ---- opt-in per-kernel timing (timing.cu) ----------------------------------
 void timing_begin(const char* name, cudaStream_t stream);

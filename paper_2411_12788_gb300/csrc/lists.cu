@@ -534,7 +534,8 @@ cudaError_t launch_lists(const ListArgs& a, cudaStream_t stream) {
            (l2_tile_kernel<<<dim3(a.rows, (a.max_tx + 31) / 32), 32 * kTileScanWarps, 0, stream>>>(a)));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = gather_exclusive_scan(a.tile_count, nullptr, a.tile_start, a.total_tiles, a.scan_blocks, a.scan_total, stream);
+  e = gather_exclusive_scan(a.tile_count, nullptr, a.tile_start, a.total_tiles, a.scan_blocks, a.scan_total, stream,
+                            a.status);
   if (e != cudaSuccess) return e;
   GS_TIMED("lists_ranges", stream,
            (l2_ranges_kernel<<<ceil_div(a.total_tiles, 256), 256, 0, stream>>>(a)));

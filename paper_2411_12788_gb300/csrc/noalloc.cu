@@ -96,7 +96,8 @@ extern "C" gs_status gs_bin_sort_noalloc(const gs_plan* plan, void* pre_ws, uint
   if (plan->n_entries > 0) {
     // the entry offsets of the depth order (the preprocess may have scanned
     // the band sizes instead, for the tile-list builder of gs_bin_sort)
-    e = gather_exclusive_scan(st.tiles, sorted_items, offsets, plan->n_items, scan_blocks, n_entries, stream);
+    e = gather_exclusive_scan(st.tiles, sorted_items, offsets, plan->n_items, scan_blocks, n_entries, stream,
+                              status);
     if (e == cudaSuccess)
       e = launch_duplicate(views, plan->n_views, plan->n_items, plan->n, sorted_items, offsets, st, tile_ids, items,
                          status, stream);

@@ -386,76 +386,140 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* s
   return x - v + add;
 }
 
-// Block sums of the (gathered) counts; with idx the gathered counts are also
-// stored in `gathered` (the output array), so the final pass reads them in
-// order instead of gathering a second time.
-__global__ void __launch_bounds__(kScanThreads) scan_block_sums_kernel(const uint32_t* __restrict__ counts,
-                                                                       const uint32_t* __restrict__ idx,
-                                                                       int64_t n, uint64_t* __restrict__ sums,
-                                                                       uint32_t* __restrict__ gathered) {
-  __shared__ uint32_t s_warp[kScanThreads / 32];
-  int64_t base = (int64_t)blockIdx.x * kScanTile;
-  uint32_t acc = 0;
-  for (int k = 0; k < kScanItems; ++k) {
-    int64_t i = base + k * kScanThreads + threadIdx.x;
-    if (i < n) {
-      const uint32_t c = counts[idx ? idx[i] : i];
-      if (idx) gathered[i] = c;
-      acc += c;
+// Single-pass exclusive scan of the (gathered) counts with a decoupled
+// look-back.  Each block takes the next tile of kScanTile counts (dynamic tile
+// ids, so every predecessor of a tile is running or done), scans it, publishes
+// its total, finds the total of all tiles before it from its predecessors'
+// published words and publishes its own inclusive prefix.  A word holds the
+// flag in its top two bits and the value below them, so a reader sees both
+// together.  The resident tiles of the first wave finish their loads at about
+// the same time, when only tile 0 has a prefix, so the look-back warp reads
+// kScanWindow predecessors per step (kScanWindow / 32 per lane, nearest
+// first): the walk back to tile 0 takes a few L2 round trips, not one per 32
+// tiles.  The wait for an unpublished predecessor is bounded like the sort's:
+// after kSpinLimit polls it records kStatusTimeout (when a status word is
+// given) and carries on with what it has.
+constexpr uint64_t kScanAggregate = 1ull << 62, kScanPrefix = 2ull << 62, kScanValueMask = (1ull << 62) - 1;
+constexpr int kScanPerLane = 4, kScanWindow = 32 * kScanPerLane;
+static_assert(kScanItems % 4 == 0, "a thread's counts are read as uint4");
+
+__device__ __forceinline__ uint64_t ld_volatile_u64(const uint64_t* p) { return *(const volatile uint64_t*)p; }
+__device__ __forceinline__ void st_volatile_u64(uint64_t* p, uint64_t v) { *(volatile uint64_t*)p = v; }
+
+// The sum of the published values of tiles [0, tile): read back from tile - 1
+// to the nearest inclusive prefix, kScanWindow words per step (lane l holds
+// the words at distances 4l .. 4l + 3).  Warp-uniform result.
+__device__ uint64_t scan_lookback(const uint64_t* words, int tile, uint32_t* status) {
+  const int lane = threadIdx.x & 31;
+  uint64_t excl = 0;
+  int64_t j = tile - 1;
+  long spins = 0;
+  while (true) {
+    uint64_t w[kScanPerLane];
+#pragma unroll
+    for (int u = 0; u < kScanPerLane; ++u) {
+      const int64_t q = j - (lane * kScanPerLane + u);
+      w[u] = q >= 0 ? ld_volatile_u64(&words[q]) : kScanPrefix;
     }
+    // this lane's nearest prefix (kScanPerLane: none), any word before it unpublished, their sum
+    int up = kScanPerLane;
+    bool unready = false;
+    uint64_t v = 0;
+#pragma unroll
+    for (int u = 0; u < kScanPerLane; ++u) {
+      if (up == kScanPerLane) {
+        const uint64_t flag = w[u] & ~kScanValueMask;
+        unready |= flag == 0;
+        v += w[u] & kScanValueMask;
+        if (flag == kScanPrefix) up = u;
+      }
+    }
+    const uint32_t prefix = __ballot_sync(0xffffffffu, up < kScanPerLane);
+    const int first = prefix ? __ffs(prefix) - 1 : 31;      // lanes 0..first hold the words that count
+    const uint32_t upto = first == 31 ? 0xffffffffu : ((2u << first) - 1u);
+    if (__ballot_sync(0xffffffffu, unready) & upto) {
+      if (++spins > kSpinLimit) {
+        if (status && lane == 0) atomicOr(status, kStatusTimeout);
+        return excl;
+      }
+      continue;                                              // the same window again
+    }
+    if (lane > first) v = 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    excl += v;
+    if (prefix) return excl;
+    j -= kScanWindow;
   }
-  uint32_t tot;
-  block_exclusive_scan(acc, s_warp, &tot);
-  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
 }
 
-// Single block: exclusive scan of the block sums in place, total to *total.
-__global__ void __launch_bounds__(1024) scan_top_kernel(uint64_t* sums, int64_t nb, unsigned long long* total) {
-  __shared__ uint64_t s[1024];
-  __shared__ uint64_t carry;
-  if (threadIdx.x == 0) carry = 0;
+__global__ void __launch_bounds__(kScanThreads, 2048 / kScanThreads) scan_onepass_kernel(const uint32_t* __restrict__ counts,
+                                                                    const uint32_t* __restrict__ idx, int64_t n,
+                                                                    uint64_t* __restrict__ words, int nb,
+                                                                    uint32_t* __restrict__ out,
+                                                                    unsigned long long* __restrict__ total,
+                                                                    uint32_t* __restrict__ status) {
+  __shared__ uint32_t s_warp[kScanThreads / 32];
+  __shared__ uint32_t s_tile;
+  __shared__ uint64_t s_excl;
+  const int tid = threadIdx.x;
+  if (tid == 0) s_tile = atomicAdd(reinterpret_cast<uint32_t*>(words + nb), 1u);
   __syncthreads();
-  for (int64_t base = 0; base < nb; base += 1024) {
-    int64_t i = base + threadIdx.x;
-    uint64_t v = i < nb ? sums[i] : 0;
-    s[threadIdx.x] = v;
-    __syncthreads();
-    for (int off = 1; off < 1024; off <<= 1) {
-      uint64_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0;
-      __syncthreads();
-      s[threadIdx.x] += t;
-      __syncthreads();
-    }
-    if (i < nb) sums[i] = carry + s[threadIdx.x] - v;
-    __syncthreads();
-    if (threadIdx.x == 1023) carry += s[1023];
-    __syncthreads();
-  }
-  if (threadIdx.x == 0) *total = carry;
-}
-
-__global__ void __launch_bounds__(kScanThreads) scan_final_kernel(const uint32_t* __restrict__ counts,
-                                                                  const uint32_t* __restrict__ idx, int64_t n,
-                                                                  const uint64_t* __restrict__ sums,
-                                                                  uint32_t* __restrict__ out) {
-  // thread t owns the contiguous items [t*kScanItems, (t+1)*kScanItems) of the block
-  __shared__ uint32_t s_warp[kScanThreads / 32];
-  int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  const int tile = (int)s_tile;
+  // thread t owns the contiguous counts [t kScanItems, (t + 1) kScanItems) of the tile
+  const int64_t base = (int64_t)tile * kScanTile + (int64_t)tid * kScanItems;
   uint32_t c[kScanItems];
+  const uint32_t* src = idx ? idx : counts;
+  if (base + kScanItems <= n && (reinterpret_cast<uintptr_t>(src) & 15) == 0) {
+#pragma unroll
+    for (int k = 0; k < kScanItems; k += 4) {
+      const uint4 q = *reinterpret_cast<const uint4*>(src + base + k);
+      c[k] = q.x, c[k + 1] = q.y, c[k + 2] = q.z, c[k + 3] = q.w;
+    }
+    if (idx) {
+#pragma unroll
+      for (int k = 0; k < kScanItems; ++k) c[k] = counts[c[k]];
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const int64_t i = base + k;
+      c[k] = i < n ? counts[idx ? idx[i] : i] : 0u;
+    }
+  }
   uint32_t acc = 0;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    int64_t i = base + k;
-    c[k] = i < n ? (idx ? out[i] : counts[i]) : 0u;     // with idx: the block-sum pass's gathered copy
-    acc += c[k];
-  }
+  for (int k = 0; k < kScanItems; ++k) acc += c[k];
   uint32_t tot;
-  uint32_t run = block_exclusive_scan(acc, s_warp, &tot) + (uint32_t)sums[blockIdx.x];
+  const uint32_t pre = block_exclusive_scan(acc, s_warp, &tot);
+  if (tid == 0) st_volatile_u64(&words[tile], (tile == 0 ? kScanPrefix : kScanAggregate) | (uint64_t)tot);
+  if (tid < 32) {
+    const uint64_t excl = tile > 0 ? scan_lookback(words, tile, status) : 0ull;
+    if (tid == 0) {
+      if (tile > 0) st_volatile_u64(&words[tile], kScanPrefix | ((excl + tot) & kScanValueMask));
+      s_excl = excl;
+      if (tile == nb - 1) *total = (unsigned long long)(excl + tot);
+    }
+  }
+  __syncthreads();
+  uint32_t run = (uint32_t)s_excl + pre;
+  if (base + kScanItems <= n && (reinterpret_cast<uintptr_t>(out) & 15) == 0) {
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {
-    int64_t i = base + k;
-    if (i < n) out[i] = run;
-    run += c[k];
+    for (int k = 0; k < kScanItems; k += 4) {
+      uint4 q;
+      q.x = run, run += c[k];
+      q.y = run, run += c[k + 1];
+      q.z = run, run += c[k + 2];
+      q.w = run, run += c[k + 3];
+      *reinterpret_cast<uint4*>(out + base + k) = q;
+    }
+  } else {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {
+      const int64_t i = base + k;
+      if (i < n) out[i] = run;
+      run += c[k];
+    }
   }
 }
 
@@ -527,17 +591,21 @@ cudaError_t lookback_timeout_probe(uint32_t* scratch, uint32_t* status, cudaStre
   return cudaGetLastError();
 }
 
-size_t scan_block_bytes(int64_t n) { return align_up((size_t)ceil_div(std::max<int64_t>(n, 1), kScanTile) * 8); }
+// One look-back word per tile and the tile counter.
+size_t scan_block_bytes(int64_t n) {
+  return align_up(((size_t)ceil_div(std::max<int64_t>(n, 1), kScanTile) + 1) * 8);
+}
 
 cudaError_t gather_exclusive_scan(const uint32_t* counts, const uint32_t* idx, uint32_t* out, int64_t n,
-                                  uint64_t* block_scratch, unsigned long long* total, cudaStream_t stream) {
+                                  uint64_t* block_scratch, unsigned long long* total, cudaStream_t stream,
+                                  uint32_t* status) {
   if (n <= 0) return cudaMemsetAsync(total, 0, 8, stream);
-  int nb = ceil_div(n, kScanTile);
-  GS_TIMED("scan_block_sums", stream,
-           (scan_block_sums_kernel<<<nb, kScanThreads, 0, stream>>>(counts, idx, n, block_scratch, out)));
-  GS_TIMED("scan_top", stream, (scan_top_kernel<<<1, 1024, 0, stream>>>(block_scratch, nb, total)));
-  GS_TIMED("scan_final", stream,
-           (scan_final_kernel<<<nb, kScanThreads, 0, stream>>>(counts, idx, n, block_scratch, out)));
+  const int nb = ceil_div(n, kScanTile);
+  cudaError_t e = cudaMemsetAsync(block_scratch, 0, ((size_t)nb + 1) * 8, stream);
+  if (e != cudaSuccess) return e;
+  GS_TIMED("scan", stream,
+           (scan_onepass_kernel<<<nb, kScanThreads, 0, stream>>>(counts, idx, n, block_scratch, nb, out, total,
+                                                                 status)));
   return cudaGetLastError();
 }
 
