@@ -427,12 +427,14 @@ gs_status gs_loss_l1_ssim(const gs_plan* plan, const float* image, const float* 
 
 /* ---- failure detection self-check ---------------------------------------- */
 
-/* No counterpart in the paper: checks that the sort's bounded device wait
- * gives up instead of hanging.  Runs the onesweep look-back for a tile whose
- * predecessor never publishes its counts; every wait runs out after its bound
- * (about a second), records the timeout in a status word, and the call
- * returns GS_ERR_TIMEOUT with the context still usable (GS_OK would mean the
- * wait did not detect the missing publisher).  scratch: device,
+/* No counterpart in the paper: checks that the bounded device waits of the
+ * sort and the scan give up instead of hanging.  Runs the onesweep look-back
+ * and the exclusive scan's look-back for a tile whose predecessor never
+ * publishes;
+ * every wait runs out after its bound (about a second each), records the
+ * timeout in a status word of its own, and the call returns GS_ERR_TIMEOUT
+ * when both did, with the context still usable (GS_OK would mean a wait did
+ * not detect the missing publisher).  scratch: device,
  * GS_SELFTEST_SCRATCH_BYTES bytes, 16-byte aligned.  Synchronous. */
 #define GS_SELFTEST_SCRATCH_BYTES 4096u
 gs_status gs_selftest_wait_timeout(void* scratch, size_t scratch_bytes, void* stream);

@@ -553,15 +553,20 @@ gs_status gs_selftest_wait_timeout(void* scratch, size_t scratch_bytes, void* st
   if (!scratch || scratch_bytes < GS_SELFTEST_SCRATCH_BYTES || (reinterpret_cast<uintptr_t>(scratch) & 15))
     return GS_ERR_INVALID_ARG;
   cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  // [0, 3 kRadix) words: the sort's probe; then one status word per probe;
+  // from byte 3200: the scan's probe
+  static_assert(3 * kRadix * 4 + 8 <= 3200 && 3200 + 3 * 8 <= GS_SELFTEST_SCRATCH_BYTES, "self-test scratch layout");
   uint32_t* words = static_cast<uint32_t*>(scratch);
   uint32_t* status = words + 3 * kRadix;
-  uint32_t word = 0;
-  cudaError_t e = cudaMemsetAsync(status, 0, 4, stream);
+  uint64_t* scan_words = reinterpret_cast<uint64_t*>(static_cast<char*>(scratch) + 3200);
+  uint32_t word[2] = {0u, 0u};
+  cudaError_t e = cudaMemsetAsync(status, 0, 8, stream);
   if (e == cudaSuccess) e = lookback_timeout_probe(words, status, stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&word, status, 4, cudaMemcpyDeviceToHost, stream);
+  if (e == cudaSuccess) e = scan_timeout_probe(scan_words, status + 1, stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(word, status, 8, cudaMemcpyDeviceToHost, stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(stream);
   if (e != cudaSuccess) return GS_ERR_CUDA;
-  return (word & kStatusTimeout) ? GS_ERR_TIMEOUT : GS_OK;
+  return ((word[0] & kStatusTimeout) && (word[1] & kStatusTimeout)) ? GS_ERR_TIMEOUT : GS_OK;
 }
 
 gs_status gs_inspect_preprocess(const gs_plan* plan, const void* pre_ws, gs_preprocess_view* out) {

@@ -167,6 +167,8 @@ constexpr int kScanTile = kScanThreads * kScanItems;
 size_t scan_block_bytes(int64_t n);
 // Self-test of the sort's bounded look-back wait (scratch: 3 * 256 words).
 cudaError_t lookback_timeout_probe(uint32_t* scratch, uint32_t* status, cudaStream_t stream);
+// The same for the exclusive scan's look-back (scratch: 3 words of 8 bytes).
+cudaError_t scan_timeout_probe(uint64_t* scratch, uint32_t* status, cudaStream_t stream);
 // out[k] = sum_{j<k} counts[idx[j]] (idx == nullptr: counts[j]); *total = sum of
 // all (device, 64-bit).  One pass with a decoupled look-back; block_scratch:
 // scan_block_bytes(n), cleared by the call; a look-back wait that runs out

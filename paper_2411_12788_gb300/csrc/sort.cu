@@ -453,6 +453,14 @@ __device__ uint64_t scan_lookback(const uint64_t* words, int tile, uint32_t* sta
   }
 }
 
+// Self-test of the scan's bounded wait: one warp looks back from tile 1 over
+// a tile 0 that never publishes; *out receives what the wait returned.
+__global__ void scan_timeout_probe_kernel(const uint64_t* __restrict__ words, uint32_t* __restrict__ status,
+                                          unsigned long long* __restrict__ out) {
+  const uint64_t v = scan_lookback(words, 1, status);
+  if (threadIdx.x == 0) *out = (unsigned long long)v;
+}
+
 __global__ void __launch_bounds__(kScanThreads, 2048 / kScanThreads) scan_onepass_kernel(const uint32_t* __restrict__ counts,
                                                                     const uint32_t* __restrict__ idx, int64_t n,
                                                                     uint64_t* __restrict__ words, int nb,
@@ -588,6 +596,14 @@ cudaError_t lookback_timeout_probe(uint32_t* scratch, uint32_t* status, cudaStre
   cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * kRadix * sizeof(uint32_t), stream);
   if (e != cudaSuccess) return e;
   lookback_timeout_probe_kernel<<<1, kRadix, 0, stream>>>(scratch, status, scratch + 2 * kRadix);
+  return cudaGetLastError();
+}
+
+cudaError_t scan_timeout_probe(uint64_t* scratch, uint32_t* status, cudaStream_t stream) {
+  // scratch: [2] look-back words (tile 0 never published) + [1] output
+  cudaError_t e = cudaMemsetAsync(scratch, 0, 3 * sizeof(uint64_t), stream);
+  if (e != cudaSuccess) return e;
+  scan_timeout_probe_kernel<<<1, 32, 0, stream>>>(scratch, status, reinterpret_cast<unsigned long long*>(scratch + 2));
   return cudaGetLastError();
 }
 

@@ -634,8 +634,9 @@ def test_backward_over_many_views_is_the_sum_of_single_view_passes():
 
 # ---------------------------------------------------------------- failure detection
 def test_bounded_wait_reports_timeout_and_context_survives():
-    """A look-back wait whose predecessor never publishes gives up after its
-    bound and reports GS_ERR_TIMEOUT; the context keeps working."""
+    """The sort's and the scan's look-back waits, each over a predecessor that
+    never publishes, give up after their bounds and report GS_ERR_TIMEOUT;
+    the context keeps working."""
     _need_gpu()
     import time
     t0 = time.perf_counter()
