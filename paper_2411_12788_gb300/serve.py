@@ -53,6 +53,10 @@ class Request:
     arrival: float              # seconds after the trace start
     cam: object
     done: float | None = None   # seconds after the trace start (device time)
+    # seconds after the trace start (host clock) at which the slot's worker
+    # began launching the request's batch: latency splits into the wait
+    # before it (queue and admission) and the service after it
+    started: float | None = None
     batch: int = -1
     image: torch.Tensor | None = None
     # set by the caller at any time before the request is admitted: the
@@ -216,6 +220,9 @@ class RenderServer:
                 return
             reqs, bid, est = job
             try:
+                started = time.perf_counter() - st["t0"]
+                for r in reqs:
+                    r.started = started
                 b = self._launch(reqs, slot, bid, est)
                 b.event.synchronize()
                 done = st["t0_ev"].elapsed_time(b.event) / 1e3
@@ -248,6 +255,7 @@ class RenderServer:
         st["t0_ev"] = torch.cuda.Event(enable_timing=True)
         st["t0_ev"].record(torch.cuda.current_stream())
         t0 = time.perf_counter()
+        st["t0"] = t0
         bid = 0
         try:
             while True:
@@ -313,11 +321,20 @@ def poisson_trace(n: int, rate: float, seed: int = 3, sizes=None) -> list:
 
 def latency_stats(reqs: list, skip: int = 0) -> dict:
     """Latency percentiles and throughput of the served requests after the
-    first `skip` (cancelled requests, which have no completion, are left out)."""
+    first `skip` (cancelled requests, which have no completion, are left out),
+    with the split of the slowest request's latency into its wait before its
+    batch began launching and its service after that."""
     reqs = [r for r in reqs[skip:] if r.done is not None]
     lat = np.array([r.done - r.arrival for r in reqs]) * 1e3
     span = max(r.done for r in reqs) - min(r.arrival for r in reqs)
     pix = sum(r.pixels for r in reqs)
-    return {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-            "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "requests": len(lat),
-            "mpix_per_s": pix / span / 1e6}
+    out = {"p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "mean_ms": float(lat.mean()), "max_ms": float(lat.max()), "requests": len(lat),
+           "mpix_per_s": pix / span / 1e6}
+    if all(r.started is not None for r in reqs):
+        wait = np.array([r.started - r.arrival for r in reqs]) * 1e3
+        service = lat - wait
+        worst = int(lat.argmax())
+        out.update({"wait_p99_ms": float(np.percentile(wait, 99)), "service_p99_ms": float(np.percentile(service, 99)),
+                    "slowest_wait_ms": float(wait[worst]), "slowest_service_ms": float(service[worst])})
+    return out

@@ -22,7 +22,11 @@ def _need_gpu():
 
 @pytest.mark.parametrize("n,k,kind", [(1000, 250, "uniform"), (100_003, 25_001, "ties"), (64, 0, "uniform"),
                                       (64, 64, "uniform"), (5000, 1, "ties"), (5000, 4999, "zeros"),
-                                      (1 << 20, 1 << 18, "ties")])
+                                      (1 << 20, 1 << 18, "ties"),
+                                      # the flag scans' tiles hold 8,192 counts: one full tile, one
+                                      # plus a single count, and 301 tiles with a 3-count tail, whose
+                                      # look-back walks more than two windows of 128 predecessors
+                                      (8192, 4096, "ties"), (8193, 1, "uniform"), (300 * 8192 + 3, 614_400, "ties")])
 def test_prune_select_matches_oracle(n, k, kind):
     _need_gpu()
     rng = np.random.default_rng(n + k)

@@ -25,6 +25,21 @@ def test_latency_stats():
     assert st["max_ms"] > 49.9 and st["requests"] == 200
 
 
+def test_latency_stats_split_wait_and_service():
+    """With launch start times recorded, the slowest request's latency splits
+    into the wait before its batch began and the service after it."""
+    tr = serve.poisson_trace(100, rate=100.0, seed=2)
+    for k, r in enumerate(tr):
+        r.started = r.arrival + (0.030 if k == 50 else 0.0002)
+        r.done = r.started + 0.001
+    st = serve.latency_stats(tr)
+    assert abs(st["max_ms"] - 31.0) < 1e-6
+    assert abs(st["slowest_wait_ms"] - 30.0) < 1e-6 and abs(st["slowest_service_ms"] - 1.0) < 1e-6
+    assert abs(st["service_p99_ms"] - 1.0) < 1e-6
+    # without start times there is no split
+    assert "wait_p99_ms" not in serve.latency_stats([serve.Request(0, 0.0, tr[0].cam, done=0.001)])
+
+
 def test_scene_save_load_round_trip(tmp_path):
     """A scene written with Scene.save reads back bit-identical."""
     sc = scenes.cluster_scene(500, 8, seed=2, sh_degree=3)
