@@ -153,12 +153,15 @@ constexpr int kSortTile = kSortThreads * kSortItemsPerThread;   // keys per CTA 
 
 size_t radix_scratch_bytes(int64_t n, int bits);
 // Stable LSD sort of (key, value) pairs over bits [0, bits) (higher key bits
-// are carried along, not sorted); the result ends up in (keys, vals) (the alt
-// buffers are scratch).  `status` receives
-// kStatusTimeout if a look-back spin ran out.
+// are carried along, not sorted): 8-bit passes and a narrow last one, or one
+// 512-digit pass when bits is 9.  The result ends up in (keys, vals) (the alt
+// buffers are scratch), except that with result_in_alt given an odd number
+// of passes leaves it in the alt buffers and sets *result_in_alt instead of
+// copying it back.  `status` receives kStatusTimeout if a look-back spin ran
+// out.
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                              int64_t n, int bits, void* scratch, uint32_t* status,
-                             cudaStream_t stream, const char* tag);
+                             cudaStream_t stream, const char* tag, bool* result_in_alt = nullptr);
 
 // ---- exclusive scan of gathered counts (sort.cu) ---------------------------
 constexpr int kScanThreads = 512;

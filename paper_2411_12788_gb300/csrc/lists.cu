@@ -520,28 +520,38 @@ cudaError_t launch_lists(const ListArgs& a, cudaStream_t stream) {
   GS_TIMED("lists_pairs", stream,
            (pairs_kernel<<<ceil_div(a.n_items, 32 * kPairWarps), 32 * kPairWarps, 0, stream>>>(a)));
   e = cudaGetLastError();
+  // the sort covers the bits the row ids use: one 8- or 9-bit pass up to 512
+  // rows; with one pass the sorted pairs stay in the alternate buffers
+  int row_bits = 1;
+  while ((1 << row_bits) < a.rows) ++row_bits;
+  bool in_alt = false;
   if (e == cudaSuccess)
-    e = radix_sort_pairs(a.pkey, a.pkey_alt, a.pval, a.pval_alt, a.n_pairs, kRowBits, a.pair_radix, a.status, stream,
-                         "pairs");
+    e = radix_sort_pairs(a.pkey, a.pkey_alt, a.pval, a.pval_alt, a.n_pairs, row_bits, a.pair_radix, a.status, stream,
+                         "pairs", &in_alt);
   if (e != cudaSuccess) return e;
-  GS_TIMED("lists_rows", stream, (row_ranges_kernel<<<ceil_div((int64_t)a.rows + 1, 256), 256, 0, stream>>>(a)));
-  GS_TIMED("lists_rows", stream, (rows_kernel<<<1, 1024, 0, stream>>>(a)));
-  GS_TIMED("lists_rows", stream, (chunk_table_kernel<<<ceil_div(c2_max, 256), 256, 0, stream>>>(a)));
-  GS_TIMED("lists_tile_count", stream, (l2_count_kernel<<<l2_blocks, 32 * kL2Warps, smem2, stream>>>(a)));
-  e = cudaMemsetAsync(a.tile_hist, 0, 2 * kTileBuckets * sizeof(uint32_t), stream);
+  ListArgs L = a;
+  if (in_alt) {
+    std::swap(L.pkey, L.pkey_alt);
+    std::swap(L.pval, L.pval_alt);
+  }
+  GS_TIMED("lists_rows", stream, (row_ranges_kernel<<<ceil_div((int64_t)a.rows + 1, 256), 256, 0, stream>>>(L)));
+  GS_TIMED("lists_rows", stream, (rows_kernel<<<1, 1024, 0, stream>>>(L)));
+  GS_TIMED("lists_rows", stream, (chunk_table_kernel<<<ceil_div(c2_max, 256), 256, 0, stream>>>(L)));
+  GS_TIMED("lists_tile_count", stream, (l2_count_kernel<<<l2_blocks, 32 * kL2Warps, smem2, stream>>>(L)));
+  e = cudaMemsetAsync(L.tile_hist, 0, 2 * kTileBuckets * sizeof(uint32_t), stream);
   if (e != cudaSuccess) return e;
   GS_TIMED("lists_tile_scan", stream,
-           (l2_tile_kernel<<<dim3(a.rows, (a.max_tx + 31) / 32), 32 * kTileScanWarps, 0, stream>>>(a)));
+           (l2_tile_kernel<<<dim3(a.rows, (a.max_tx + 31) / 32), 32 * kTileScanWarps, 0, stream>>>(L)));
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  e = gather_exclusive_scan(a.tile_count, nullptr, a.tile_start, a.total_tiles, a.scan_blocks, a.scan_total, stream,
-                            a.status);
+  e = gather_exclusive_scan(L.tile_count, nullptr, L.tile_start, L.total_tiles, L.scan_blocks, L.scan_total, stream,
+                            L.status);
   if (e != cudaSuccess) return e;
   GS_TIMED("lists_ranges", stream,
-           (l2_ranges_kernel<<<ceil_div(a.total_tiles, 256), 256, 0, stream>>>(a)));
+           (l2_ranges_kernel<<<ceil_div(a.total_tiles, 256), 256, 0, stream>>>(L)));
   GS_TIMED("lists_entries", stream,
            (l2_emit_kernel<<<(int)((c2_max + kL2EmitWarps - 1) / kL2EmitWarps), 32 * kL2EmitWarps, smem3, stream>>>(
-               a)));
+               L)));
   return cudaGetLastError();
 }
 

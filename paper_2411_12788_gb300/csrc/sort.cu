@@ -56,11 +56,17 @@ __device__ __forceinline__ uint32_t lanemask_lt() {
   return m;
 }
 
-// Digit mask of the pass starting at bit `shift` of a sort over bits [0, bits):
-// the key bits above `bits` ride along unsorted.
-__host__ __device__ inline uint32_t digit_mask(int bits, int shift) {
-  return bits - shift >= kRadixBits ? (uint32_t)(kRadix - 1) : (1u << (bits - shift)) - 1u;
+// Digit mask of the pass starting at bit `shift` of a sort over bits [0, bits)
+// with digits of rbits bits: the key bits above `bits` ride along unsorted.
+__host__ __device__ inline uint32_t digit_mask(int bits, int shift, int rbits = kRadixBits) {
+  return bits - shift >= rbits ? (1u << rbits) - 1u : (1u << (bits - shift)) - 1u;
 }
+
+// A sort over at most 9 bits takes one pass of 512 digits (the wide
+// instance of the pass kernel) instead of an 8-bit pass and a narrow one.
+constexpr int kWideBits = 9;
+constexpr int kWideRadix = 1 << kWideBits;
+__host__ __device__ inline bool wide_sort(int bits) { return bits == kWideBits; }
 
 // Counts the digits of every pass in one read of the keys.  Each thread
 // takes 8 consecutive keys and adds runs of equal digits with one shared
@@ -68,10 +74,12 @@ __host__ __device__ inline uint32_t digit_mask(int bits, int shift) {
 // digit) from serialising on a single counter.
 constexpr int kHistKeys = 8;
 
+template <int kRBits>
 __global__ void __launch_bounds__(256) radix_histogram_kernel(const uint32_t* __restrict__ keys, int64_t n,
                                                               int passes, int bits, uint32_t* __restrict__ hist) {
-  __shared__ uint32_t sh[kMaxPasses * kRadix];
-  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x) sh[i] = 0;
+  constexpr int kR = 1 << kRBits;
+  __shared__ uint32_t sh[kMaxPasses * kRadix];   // passes x kR counters (at most 1,024)
+  for (int i = threadIdx.x; i < passes * kR; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   const int64_t stride = (int64_t)gridDim.x * blockDim.x * kHistKeys;
   for (int64_t base = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) * kHistKeys; base < n; base += stride) {
@@ -86,8 +94,8 @@ __global__ void __launch_bounds__(256) radix_histogram_kernel(const uint32_t* __
       for (int j = 0; j < kHistKeys; ++j) k[j] = j < cnt ? keys[base + j] : 0u;
     }
     for (int p = 0; p < passes; ++p) {
-      const int sh_p = p * kRadixBits;
-      const uint32_t msk = digit_mask(bits, sh_p);
+      const int sh_p = p * kRBits;
+      const uint32_t msk = digit_mask(bits, sh_p, kRBits);
       uint32_t cur = (k[0] >> sh_p) & msk, run = 1;
 #pragma unroll
       for (int j = 1; j < kHistKeys; ++j) {
@@ -96,27 +104,28 @@ __global__ void __launch_bounds__(256) radix_histogram_kernel(const uint32_t* __
         if (d == cur) {
           ++run;
         } else {
-          atomicAdd(&sh[p * kRadix + cur], run);
+          atomicAdd(&sh[p * kR + cur], run);
           cur = d;
           run = 1;
         }
       }
-      atomicAdd(&sh[p * kRadix + cur], run);
+      atomicAdd(&sh[p * kR + cur], run);
     }
   }
   __syncthreads();
-  for (int i = threadIdx.x; i < passes * kRadix; i += blockDim.x)
+  for (int i = threadIdx.x; i < passes * kR; i += blockDim.x)
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-// Exclusive scan of each pass's 256 digit counts (one block per pass).
-__global__ void __launch_bounds__(kRadix) radix_scan_hist_kernel(uint32_t* hist) {
-  __shared__ uint32_t s[kRadix];
-  uint32_t* h = hist + blockIdx.x * kRadix;
+// Exclusive scan of each pass's kR digit counts (one block of kR threads per pass).
+template <int kR>
+__global__ void __launch_bounds__(kR) radix_scan_hist_kernel(uint32_t* hist) {
+  __shared__ uint32_t s[kR];
+  uint32_t* h = hist + blockIdx.x * kR;
   uint32_t v = h[threadIdx.x];
   s[threadIdx.x] = v;
   __syncthreads();
-  for (int off = 1; off < kRadix; off <<= 1) {
+  for (int off = 1; off < kR; off <<= 1) {
     uint32_t t = threadIdx.x >= off ? s[threadIdx.x - off] : 0u;
     __syncthreads();
     s[threadIdx.x] += t;
@@ -132,6 +141,7 @@ __global__ void __launch_bounds__(kRadix) radix_scan_hist_kernel(uint32_t* hist)
 // yet is repeated; after kSpinLimit such rounds the wait gives up, records
 // kStatusTimeout and returns what it has (the sort result is then wrong and
 // the host reports GS_ERR_TIMEOUT), so a missing publisher cannot hang the GPU.
+template <int kR = kRadix>
 __device__ __forceinline__ uint32_t lookback_exclusive(const uint32_t* lookback, int64_t tile, int d,
                                                        uint32_t* status) {
   uint32_t exclusive = 0;
@@ -142,7 +152,7 @@ __device__ __forceinline__ uint32_t lookback_exclusive(const uint32_t* lookback,
     uint32_t st[kWin];
 #pragma unroll
     for (int w = 0; w < kWin; ++w)
-      st[w] = (j - w >= 0) ? *(const volatile uint32_t*)(lookback + (j - w) * kRadix + d) : (uint32_t)kFlagPrefix;
+      st[w] = (j - w >= 0) ? *(const volatile uint32_t*)(lookback + (j - w) * kR + d) : (uint32_t)kFlagPrefix;
     uint32_t add = 0;
     int used = 0;
     bool found = false, stalled = false;
@@ -184,20 +194,32 @@ constexpr size_t kOnesweepDynSmem = 3 * (size_t)kSortTile * sizeof(uint32_t);
 constexpr long kCopyWaitLimit = 1L << 22;
 
 // kDigitBits: the widest digit the instance ranks (8, or 4 for the narrow
-// last pass of a sort whose bit count is not a multiple of 8).
-template <int kDigitBits>
+// last pass of a sort whose bit count is not a multiple of 8, or 9 for the
+// single pass of a 9-bit sort); kR: the digits of the instance (256, or 512
+// for the 9-bit pass).  With 512 digits every thread owns one digit, the
+// per-warp digit counts (at most 480) are kept two to a word (16 bits each)
+// so that the shared memory stays that of the 256-digit instance, and the
+// output bases reuse the CTA offsets' array.
+template <int kDigitBits, int kR>
 __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesweep_kernel(
     const uint32_t* __restrict__ keys_in, const uint32_t* __restrict__ vals_in,
     uint32_t* __restrict__ keys_out, uint32_t* __restrict__ vals_out, int64_t n, int shift, uint32_t dmask,
     const uint32_t* __restrict__ digit_base, uint32_t* __restrict__ counter,
     uint32_t* __restrict__ lookback, uint32_t* __restrict__ status) {
+  static_assert(kR == kRadix || (kR == kWideRadix && kR == kSortThreads), "256 digits, or one digit per thread");
+  static_assert((1 << kDigitBits) <= kR, "digits of the instance");
+  constexpr bool kPacked = kR > kRadix;
+  static_assert(!kPacked || kWarpKeys < 65536, "16-bit per-warp counts");
+  constexpr int kHistWords = kPacked ? kR / 2 : kR;
   extern __shared__ __align__(16) uint32_t s_dyn[];
   uint32_t* s_keys = s_dyn;                       // keys: loaded, then in output order
   uint32_t* s_vin = s_dyn + kSortTile;            // values as loaded
   uint32_t* s_vals = s_dyn + 2 * kSortTile;       // values in output order
-  __shared__ uint32_t s_warp_hist[kWarps][kRadix];
-  __shared__ uint32_t s_cta_start[kRadix];
-  __shared__ uint32_t s_out_base[kRadix];         // output index of the CTA's first key of each digit, minus its start
+  __shared__ uint32_t s_warp_hist[kWarps][kHistWords];
+  __shared__ uint32_t s_cta_start[kR];
+  __shared__ uint32_t s_out_arr[kPacked ? 1 : kR];
+  // output index of the CTA's first key of each digit, minus its start
+  uint32_t* s_out_base = kPacked ? s_cta_start : s_out_arr;
   __shared__ uint32_t s_tile;
   __shared__ __align__(8) uint64_t s_bar;
 
@@ -208,7 +230,7 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
     s_tile = atomicAdd(counter, 1u);
     mbar_init(&s_bar, 1);
   }
-  for (int i = tid; i < kWarps * kRadix; i += kSortThreads) {
+  for (int i = tid; i < kWarps * kHistWords; i += kSortThreads) {
     (&s_warp_hist[0][0])[i] = 0;
   }
   __syncthreads();
@@ -270,7 +292,14 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
     const uint32_t peers = ~diff;
     const uint32_t leader = valid ? (uint32_t)(__ffs(peers) - 1) : (uint32_t)lane;
     uint32_t m = leader | ((uint32_t)__popc(peers & lt) << 5);
-    if (valid && (uint32_t)lane == leader) m |= atomicAdd(&whist[d], (uint32_t)__popc(peers)) << 10;
+    if (valid && (uint32_t)lane == leader) {
+      if constexpr (kPacked) {
+        const uint32_t sh16 = (d & 1u) * 16u;
+        m |= ((atomicAdd(&whist[d >> 1], (uint32_t)__popc(peers) << sh16) >> sh16) & 0xFFFFu) << 10;
+      } else {
+        m |= atomicAdd(&whist[d], (uint32_t)__popc(peers)) << 10;
+      }
+    }
     // orders this row's counter update before the next row's (the next
     // leader may be another lane)
     __syncwarp();
@@ -283,19 +312,30 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
   }
   __syncthreads();
 
-  // 2. per digit (threads < kRadix, one digit each): offsets of each warp
+  // 2. per digit (threads < kR, one digit each): offsets of each warp
   //    inside the CTA and the CTA's count, published for the successors
-  const bool digit_thread = tid < kRadix;
+  const bool digit_thread = tid < kR;
   uint32_t cta_count = 0;
   if (digit_thread) {
     const int d = tid;
     for (int w = 0; w < kWarps; ++w) {
-      uint32_t c = s_warp_hist[w][d];
-      s_warp_hist[w][d] = cta_count;
-      cta_count += c;
+      if constexpr (kPacked) {
+        // digits 2j and 2j + 1 share word j and are neighbouring lanes: both
+        // read it, then the even lane writes both offsets
+        const uint32_t word = s_warp_hist[w][d >> 1];
+        const uint32_t c = (d & 1) ? (word >> 16) : (word & 0xFFFFu);
+        const uint32_t odd = __shfl_xor_sync(0xffffffffu, cta_count, 1);
+        __syncwarp();
+        if (!(d & 1)) s_warp_hist[w][d >> 1] = cta_count | (odd << 16);
+        cta_count += c;
+      } else {
+        uint32_t c = s_warp_hist[w][d];
+        s_warp_hist[w][d] = cta_count;
+        cta_count += c;
+      }
     }
     // publish this tile's count (or its inclusive prefix for tile 0)
-    uint32_t* mine = lookback + tile * kRadix + d;
+    uint32_t* mine = lookback + tile * kR + d;
     if (tile == 0) {
       __threadfence();
       *(volatile uint32_t*)mine = kFlagPrefix | cta_count;
@@ -314,7 +354,7 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
       uint32_t t = __shfl_up_sync(0xffffffffu, v, off);
       if (lane >= off) v += t;
     }
-    __shared__ uint32_t s_warp_tot[kRadix / 32];
+    __shared__ uint32_t s_warp_tot[kR / 32];
     if (digit_thread && lane == 31) s_warp_tot[warp] = v;
     __syncthreads();
     if (digit_thread) {
@@ -334,7 +374,8 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
     const int i = warp_start + k * 32 + lane;
     if (i < count) {
       const uint32_t d = (key[k] >> shift) & dmask;
-      const uint32_t pos = s_cta_start[d] + s_warp_hist[warp][d] + rank[k];
+      const uint32_t woff = kPacked ? (s_warp_hist[warp][d >> 1] >> ((d & 1u) * 16u)) & 0xFFFFu : s_warp_hist[warp][d];
+      const uint32_t pos = s_cta_start[d] + woff + rank[k];
       if (GS_IN_RANGE(pos, count, status)) {
         s_keys[pos] = key[k];
         s_vals[pos] = s_vin[i];
@@ -343,14 +384,13 @@ __global__ void __launch_bounds__(kSortThreads, 1024 / kSortThreads) radix_onesw
   }
 
   // 5. decoupled look-back for this digit, then this tile's inclusive prefix
-  if (digit_thread) {
-    uint32_t exclusive = 0;
-    if (tile > 0) {
-      exclusive = lookback_exclusive(lookback, tile, tid, status);
-      *(volatile uint32_t*)(lookback + tile * kRadix + tid) = kFlagPrefix | (exclusive + cta_count);
-    }
-    s_out_base[tid] = digit_base[tid] + exclusive - start;
+  uint32_t exclusive = 0;
+  if (digit_thread && tile > 0) {
+    exclusive = lookback_exclusive<kR>(lookback, tile, tid, status);
+    *(volatile uint32_t*)(lookback + tile * kR + tid) = kFlagPrefix | (exclusive + cta_count);
   }
+  if constexpr (kPacked) __syncthreads();         // the staging above has read every s_cta_start
+  if (digit_thread) s_out_base[tid] = digit_base[tid] + exclusive - start;
   __syncthreads();
 
   // 6. write out: runs of equal digits are contiguous in the output
@@ -534,28 +574,36 @@ __global__ void __launch_bounds__(kScanThreads, 2048 / kScanThreads) scan_onepas
 }  // namespace
 
 size_t radix_scratch_bytes(int64_t n, int bits) {
-  int passes = (bits + kRadixBits - 1) / kRadixBits;
-  return align_up((kMaxPasses * kRadix + kMaxPasses) * 4) +
-         align_up((size_t)passes * (size_t)sort_tiles(n) * kRadix * 4);
+  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  // look-back words: passes x 256 per tile, or 512 for the one wide pass
+  const size_t per_tile = wide_sort(bits) ? (size_t)kWideRadix : (size_t)passes * kRadix;
+  return align_up((kMaxPasses * kRadix + kMaxPasses) * 4) + align_up(per_tile * (size_t)sort_tiles(n) * 4);
 }
 
 cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals, uint32_t* vals_alt,
                              int64_t n, int bits, void* scratch, uint32_t* status, cudaStream_t stream,
-                             const char* tag) {
+                             const char* tag, bool* result_in_alt) {
+  if (result_in_alt) *result_in_alt = false;
   if (n <= 0 || bits <= 0) return cudaSuccess;
   if ((reinterpret_cast<uintptr_t>(keys) | reinterpret_cast<uintptr_t>(keys_alt) | reinterpret_cast<uintptr_t>(vals) |
        reinterpret_cast<uintptr_t>(vals_alt)) & 15)
     return cudaErrorMisalignedAddress;     // the bulk copies need 16-byte aligned rows
   static std::atomic<uint64_t> attr_done{0};
   cudaError_t ea = once_per_device(attr_done, [] {
-    cudaError_t e = cudaFuncSetAttribute(radix_onesweep_kernel<8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)kOnesweepDynSmem);
-    if (e != cudaSuccess) return e;
-    return cudaFuncSetAttribute(radix_onesweep_kernel<4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)kOnesweepDynSmem);
+    cudaError_t e = cudaFuncSetAttribute(radix_onesweep_kernel<8, kRadix>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOnesweepDynSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(radix_onesweep_kernel<4, kRadix>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kOnesweepDynSmem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(radix_onesweep_kernel<kWideBits, kWideRadix>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOnesweepDynSmem);
+    return e;
   });
   if (ea != cudaSuccess) return ea;
-  const int passes = (bits + kRadixBits - 1) / kRadixBits;
+  const bool wide = wide_sort(bits);
+  const int rbits = wide ? kWideBits : kRadixBits, radix = 1 << rbits;
+  const int passes = (bits + rbits - 1) / rbits;
   RadixScratch s = carve(scratch, n);
   const int64_t tiles = sort_tiles(n);
   cudaError_t e = cudaMemsetAsync(scratch, 0, radix_scratch_bytes(n, bits), stream);
@@ -566,25 +614,35 @@ cudaError_t radix_sort_pairs(uint32_t* keys, uint32_t* keys_alt, uint32_t* vals,
   int hist_blocks = (int)std::min<int64_t>((int64_t)(passes <= 2 ? 8 : 4) * device_sm_count(),
                                           (n + 256 * kHistKeys - 1) / (256 * kHistKeys));
   const bool depth = tag && tag[0] == 'd', pairs = tag && tag[0] == 'p';
-  GS_TIMED(depth ? "depth_sort_histogram" : pairs ? "pair_sort_histogram" : "tile_sort_histogram", stream,
-           (radix_histogram_kernel<<<hist_blocks, 256, 0, stream>>>(keys, n, passes, bits, s.hist)));
-  GS_TIMED(depth ? "depth_sort_scan_hist" : pairs ? "pair_sort_scan_hist" : "tile_sort_scan_hist", stream,
-           (radix_scan_hist_kernel<<<passes, kRadix, 0, stream>>>(s.hist)));
+  const char* hist_name = depth ? "depth_sort_histogram" : pairs ? "pair_sort_histogram" : "tile_sort_histogram";
+  const char* scan_name = depth ? "depth_sort_scan_hist" : pairs ? "pair_sort_scan_hist" : "tile_sort_scan_hist";
+  if (wide) {
+    GS_TIMED(hist_name, stream,
+             (radix_histogram_kernel<kWideBits><<<hist_blocks, 256, 0, stream>>>(keys, n, passes, bits, s.hist)));
+    GS_TIMED(scan_name, stream, (radix_scan_hist_kernel<kWideRadix><<<passes, kWideRadix, 0, stream>>>(s.hist)));
+  } else {
+    GS_TIMED(hist_name, stream,
+             (radix_histogram_kernel<kRadixBits><<<hist_blocks, 256, 0, stream>>>(keys, n, passes, bits, s.hist)));
+    GS_TIMED(scan_name, stream, (radix_scan_hist_kernel<kRadix><<<passes, kRadix, 0, stream>>>(s.hist)));
+  }
   uint32_t *kin = keys, *kout = keys_alt, *vin = vals, *vout = vals_alt;
   for (int p = 0; p < passes; ++p) {
-    const uint32_t dmask = digit_mask(bits, p * kRadixBits);
+    const uint32_t dmask = digit_mask(bits, p * rbits, rbits);
     // a pass of at most 4 digit bits ranks with 4 ballots per key instead of 8
-    auto pass = dmask < 16u ? radix_onesweep_kernel<4> : radix_onesweep_kernel<8>;
+    auto pass = wide ? radix_onesweep_kernel<kWideBits, kWideRadix>
+                     : dmask < 16u ? radix_onesweep_kernel<4, kRadix> : radix_onesweep_kernel<8, kRadix>;
     GS_TIMED(depth ? "depth_sort_onesweep" : pairs ? "pair_sort_onesweep" : "tile_sort_onesweep", stream,
              (pass<<<(unsigned)tiles, kSortThreads, kOnesweepDynSmem, stream>>>(
-                 kin, vin, kout, vout, n, p * kRadixBits, dmask, s.hist + p * kRadix, s.counters + p,
-                 s.lookback + (size_t)p * tiles * kRadix, status)));
+                 kin, vin, kout, vout, n, p * rbits, dmask, s.hist + p * radix, s.counters + p,
+                 s.lookback + (size_t)p * tiles * radix, status)));
     std::swap(kin, kout);
     std::swap(vin, vout);
   }
   cudaError_t el = cudaGetLastError();
   if (el != cudaSuccess) return el;
-  if (kin != keys) {   // odd number of passes: the result sits in the alt buffers
+  if (kin != keys && result_in_alt) {   // odd number of passes: the caller takes the alt buffers
+    *result_in_alt = true;
+  } else if (kin != keys) {   // odd number of passes: the result sits in the alt buffers
     el = cudaMemcpyAsync(keys, kin, n * 4, cudaMemcpyDeviceToDevice, stream);
     if (el == cudaSuccess) el = cudaMemcpyAsync(vals, vin, n * 4, cudaMemcpyDeviceToDevice, stream);
   }

@@ -60,11 +60,24 @@ SCENES = {
     "box1024_deg0": lambda: (scenes.box_scene(1024, seed=0, sh_degree=0), [scenes.origin_camera()]),
     "box512_deg3_multiview": lambda: (scenes.box_scene(512, seed=4, sh_degree=3), _multiview_cams()),
 }
+def _tall_cams(k):
+    # k views 40 x 1040 (65 tile rows each) from eyes spread around the box
+    cams = []
+    for i in range(k):
+        R, t = scenes.look_at((0.08 * (i - k / 2), 0.05 * i, -0.1 * (i % 3)), (0.0, 0.0, 4.0))
+        cams.append(scenes.fov_camera(R, t, 40, 1040, 20.0))
+    return cams
+
+
 # binning cases: also a view 1,026 tiles across, whose lists gs_bin_sort builds
-# by sorting the entries by tile id (the other scenes take the pair sort)
+# by sorting the entries by tile id (the other scenes take the pair sort); and
+# tall views whose 325 or 585 tile rows make the pair sort one 9-bit pass or
+# an 8-bit and a 2-bit pass (the small scenes' few rows take one narrow pass)
 SORT_SCENES = dict(SCENES, box600_wide_strip=lambda: (scenes.box_scene(600, seed=9, sh_degree=1),
                                                       [scenes.origin_camera(16410, 24, 2400.0),
-                                                       scenes.origin_camera(64, 48, 64.0)]))
+                                                       scenes.origin_camera(64, 48, 64.0)]),
+                   box400_tall_325_rows=lambda: (scenes.box_scene(400, seed=5, sh_degree=1), _tall_cams(5)),
+                   box400_tall_585_rows=lambda: (scenes.box_scene(400, seed=6, sh_degree=1), _tall_cams(9)))
 
 
 # ---------------------------------------------------------------- stage P
