@@ -283,8 +283,8 @@ def roofline(kt: dict, st: "Step", steps: int, peaks: dict, clocks: dict, name: 
            "duplicate": 8 * I + 52 * V + 8 * E,
            # attributes of every Gaussian; count and key of every item, 136 B of state per visible item
            "preprocess": 236 * N + 8 * I + 136 * V,
-           # attributes and their gradients; the 2-D gradients of visible items
-           "preprocess_backward": 2 * 236 * N + 48 * V}
+           # attributes and their gradients; the 2-D gradients (36 B) of visible items
+           "preprocess_backward": 2 * 236 * N + 36 * V}
     bytes_ = per.get(name, 0)
     ach = bytes_ / (ms * 1e-3) / 1e9
     peak = peaks.get("hbm_gbs", 6800.0)

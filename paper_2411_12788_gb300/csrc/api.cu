@@ -103,7 +103,7 @@ PreLayout pre_layout(const gs_plan& p) {
   L.pair_offsets = take(4 * m);
   L.scan_blocks = take(scan_block_bytes((int64_t)m));
   L.radix_scratch = take(radix_scratch_bytes((int64_t)m, 32));
-  L.grad2d = take(48 * m);
+  L.grad2d = take(36 * m);       // 2 x float4 per item, then 1 float per item
   L.total = o;
   return L;
 }
@@ -498,7 +498,7 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
   const PreLayout L = pre_layout(*plan);
   const SortLayout S = sort_layout(*plan);
   const int64_t n = plan->n;
-  cudaError_t e = cudaMemsetAsync(at<char>(pre_ws, L.grad2d), 0, 48 * (size_t)plan->n_items, stream);
+  cudaError_t e = cudaMemsetAsync(at<char>(pre_ws, L.grad2d), 0, 36 * (size_t)plan->n_items, stream);
   // with GS_FLAG_ZERO_ACCUM the preprocess backward writes every attribute
   // gradient row (no read-modify-write); I_i is accumulated by atomics
   if (e == cudaSuccess && (cfg->flags & GS_FLAG_ZERO_ACCUM) && g->weight_sum)
@@ -508,12 +508,13 @@ gs_status gs_render_bwd(const gs_plan* plan, const gs_scene* scene, const gs_con
   if (e != cudaSuccess) return GS_ERR_CUDA;
   const ItemState st = item_state(pre_ws, L);
   float4* grad2d = at<float4>(pre_ws, L.grad2d);
+  float* grad2d_b = reinterpret_cast<float*>(grad2d + 2 * plan->n_items);
   e = launch_render_bwd(at<ViewDev>(pre_ws, L.views), plan->n_views, n, plan->total_tiles,
                         at<uint2>(sort_ws, S.ranges), at<uint32_t>(sort_ws, S.vals), st, *cfg, dL_dimage, image,
-                        n_contrib, grad2d, g->weight_sum, g->weight_sum_fixed, stream);
+                        n_contrib, grad2d, grad2d_b, g->weight_sum, g->weight_sum_fixed, stream);
   if (e == cudaSuccess)
-    e = launch_preprocess_backward(*scene, at<ViewDev>(pre_ws, L.views), plan->n_views, *cfg, st.tiles, grad2d, *g,
-                                   stream);
+    e = launch_preprocess_backward(*scene, at<ViewDev>(pre_ws, L.views), plan->n_views, *cfg, st.tiles, grad2d,
+                                   grad2d_b, *g, stream);
   return cuda_status(e);
 }
 

@@ -69,7 +69,7 @@ struct PreLayout {
   size_t sorted_items, offsets, pair_offsets;        // after the depth sort: scanned tiles / band sizes
   size_t scan_blocks;
   size_t radix_scratch;                              // histograms + look-back
-  size_t grad2d;                                     // 3 x float4 per item
+  size_t grad2d;                                     // 2 x float4 per item, then 1 float per item
   size_t total;
 };
 
@@ -198,8 +198,8 @@ struct TimedLaunch {
 cudaError_t launch_preprocess(const gs_scene& sc, const ViewDev* views, int n_views, const uint8_t* mask,
                               const gs_config& cfg, const ItemState& st, cudaStream_t stream);
 cudaError_t launch_preprocess_backward(const gs_scene& sc, const ViewDev* views, int n_views, const gs_config& cfg,
-                                       const uint32_t* tiles, const float4* grad2d, const gs_grads& gr,
-                                       cudaStream_t stream);
+                                       const uint32_t* tiles, const float4* grad2d, const float* grad2d_b,
+                                       const gs_grads& gr, cudaStream_t stream);
 cudaError_t launch_duplicate(const ViewDev* views, int n_views, int64_t n_items, int64_t n, const uint32_t* sorted_items,
                              const uint32_t* offsets, const ItemState& st, uint32_t* keys, uint32_t* vals,
                              uint32_t* status, cudaStream_t stream);
@@ -216,7 +216,8 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
 cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
                               const uint32_t* vals, const ItemState& st, const gs_config& cfg,
                               const float* dL_dimage, const float* image, const uint32_t* n_contrib,
-                              float4* grad2d, float* weight_sum, uint64_t* weight_sum_fixed, cudaStream_t stream);
+                              float4* grad2d, float* grad2d_b, float* weight_sum, uint64_t* weight_sum_fixed,
+                              cudaStream_t stream);
 // ---- tile lists by counting placement (lists.cu) ----------------------------
 constexpr int kListRowsMax = 4096;        // global tile rows (all views) the lists path handles
 constexpr int kListTxMax = 1023;          // tiles per row

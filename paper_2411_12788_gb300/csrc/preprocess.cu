@@ -268,7 +268,8 @@ struct PreBwdParams {
   int n_views;
   float lowpass;
   const uint32_t* tiles;
-  const float4* grad2d;   // 3 x float4 per item: (mx, my, a2, b2), (c2, log2 o, r, g), (b, -, -, -)
+  const float4* grad2d;   // 2 x float4 per item: (mx, my, a2, b2), (c2, log2 o, r, g)
+  const float* grad2d_b;  // 1 float per item: b
   float* d_means;
   float* d_scales;
   float* d_rots;
@@ -340,28 +341,30 @@ __global__ void __launch_bounds__(kPreBwdThreads) preprocess_backward_kernel(Pre
   uint64_t wvis = ((uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)(vis >> 32)) << 32) |
                   (uint64_t)__reduce_or_sync(0xffffffffu, (uint32_t)vis);
   const bool any = vis != 0;
-  float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0, n2 = n0;
+  float4 n0 = make_float4(0.f, 0.f, 0.f, 0.f), n1 = n0;
+  float n2 = 0.f;
   if (wvis) {
     const int v0 = __ffsll((long long)wvis) - 1;
     if ((vis >> v0) & 1u) {
       const int64_t item = (int64_t)v0 * P.n + i;
-      n0 = P.grad2d[3 * item];
-      n1 = P.grad2d[3 * item + 1];
-      n2 = P.grad2d[3 * item + 2];
+      n0 = P.grad2d[2 * item];
+      n1 = P.grad2d[2 * item + 1];
+      n2 = P.grad2d_b[item];
     }
   }
   while (wvis) {
     const int v = __ffsll((long long)wvis) - 1;
     wvis &= wvis - 1;
     const bool mine = (vis >> v) & 1u;
-    const float4 g0 = n0, g1 = n1, g2 = n2;
+    const float4 g0 = n0, g1 = n1;
+    const float g2 = n2;
     if (wvis) {
       const int vn = __ffsll((long long)wvis) - 1;
       if ((vis >> vn) & 1u) {
         const int64_t item = (int64_t)vn * P.n + i;
-        n0 = P.grad2d[3 * item];
-        n1 = P.grad2d[3 * item + 1];
-        n2 = P.grad2d[3 * item + 2];
+        n0 = P.grad2d[2 * item];
+        n1 = P.grad2d[2 * item + 1];
+        n2 = P.grad2d_b[item];
       }
     }
     if (!mine) continue;
@@ -372,7 +375,7 @@ __global__ void __launch_bounds__(kPreBwdThreads) preprocess_backward_kernel(Pre
     const float dA = -0.5f * kLog2eF * g0.z, dB = -kLog2eF * g0.w, dC = -0.5f * kLog2eF * g1.x;
     dop += g1.y / (opac_i * kLn2F);
     m2abs += sqrtf(dmx * dmx + dmy * dmy);
-    const float drgb[3] = {g1.z, g1.w, g2.x};
+    const float drgb[3] = {g1.z, g1.w, g2};
 
     // recompute the forward quantities of this view
     const float px = V.R[0] * p.x + V.R[1] * p.y + V.R[2] * p.z + V.t[0];
@@ -633,8 +636,8 @@ cudaError_t launch_preprocess(const gs_scene& sc, const ViewDev* views, int n_vi
 }
 
 cudaError_t launch_preprocess_backward(const gs_scene& sc, const ViewDev* views, int n_views, const gs_config& cfg,
-                                       const uint32_t* tiles, const float4* grad2d, const gs_grads& gr,
-                                       cudaStream_t stream) {
+                                       const uint32_t* tiles, const float4* grad2d, const float* grad2d_b,
+                                       const gs_grads& gr, cudaStream_t stream) {
   PreBwdParams P;
   P.means = sc.means;
   P.scales = sc.scales;
@@ -648,6 +651,7 @@ cudaError_t launch_preprocess_backward(const gs_scene& sc, const ViewDev* views,
   P.lowpass = cfg.lowpass;
   P.tiles = tiles;
   P.grad2d = grad2d;
+  P.grad2d_b = grad2d_b;
   P.d_means = gr.d_means;
   P.d_scales = gr.d_scales;
   P.d_rots = gr.d_rotations;

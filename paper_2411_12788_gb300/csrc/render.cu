@@ -480,7 +480,8 @@ struct BwdIn {
   const float* dL_dimage;
   const float* image;           // forward output c(x) + T_final bg
   const uint32_t* n_contrib;
-  float4* grad2d;               // 3 x float4 per item
+  float4* grad2d;               // 2 x float4 per item: (mx, my, a2, b2), (c2, log2 o, r, g)
+  float* grad2d_b;              // 1 float per item: b
   float* weight_sum;            // optional: += I_i per item
   uint64_t* weight_sum_fixed;   // optional: += I_i per item in units of 2^-24
 };
@@ -859,12 +860,12 @@ __global__ void __launch_bounds__(kRenderThreads, 3) render_bwd_kernel(RenderPar
         v[k] = s_g[k][tid];
         s_g[k][tid] = 0.f;
       }
-      float4* dst = B.grad2d + 3 * item;
+      float4* dst = B.grad2d + 2 * item;
       if (v[0] != 0.f || v[1] != 0.f || v[2] != 0.f || v[3] != 0.f)
         atomicAdd(dst, make_float4(v[0], v[1], v[2], v[3]));
       if (v[4] != 0.f || v[5] != 0.f || v[6] != 0.f || v[7] != 0.f)
         atomicAdd(dst + 1, make_float4(v[4], v[5], v[6], v[7]));
-      if (v[8] != 0.f) atomicAdd(&dst[2].x, v[8]);
+      if (v[8] != 0.f) atomicAdd(&B.grad2d_b[item], v[8]);
       if (kFix) {
         const uint32_t wf = s_wfix[tid];
         s_wfix[tid] = 0u;
@@ -932,10 +933,11 @@ cudaError_t launch_render_fwd(const ViewDev* views, int n_views, int64_t n, int 
 cudaError_t launch_render_bwd(const ViewDev* views, int n_views, int64_t n, int total_tiles, const uint2* ranges,
                               const uint32_t* vals, const ItemState& st, const gs_config& cfg,
                               const float* dL_dimage, const float* image, const uint32_t* n_contrib,
-                              float4* grad2d, float* weight_sum, uint64_t* weight_sum_fixed, cudaStream_t stream) {
+                              float4* grad2d, float* grad2d_b, float* weight_sum, uint64_t* weight_sum_fixed,
+                              cudaStream_t stream) {
   RenderParams P = make_params(views, n_views, n, ranges, vals, st, cfg);
   P.total_tiles = total_tiles;                   // tiles in id order (no launch order)
-  BwdIn B{dL_dimage, image, n_contrib, grad2d, weight_sum, weight_sum_fixed};
+  BwdIn B{dL_dimage, image, n_contrib, grad2d, grad2d_b, weight_sum, weight_sum_fixed};
   if (total_tiles > 0) {
     if (weight_sum_fixed)
       GS_TIMED("render_bwd", stream, (render_bwd_kernel<true><<<total_tiles, kRenderThreads, 0, stream>>>(P, B)));
