@@ -192,8 +192,8 @@ def kernel_times(collect=True) -> dict:
 # valid while the kernel's source file is the one profiled (its SHA-256) and the workload has the same number
 # of tile entries; otherwise the traffic is reported as null.
 PROFILED_TRAFFIC = {
-    "render_bwd": {"bytes": 587.44e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
-                   "sha256": "65a6a033ef6823d469dcaab0c08aa0f4efbeba5974acb3df8fb7d3e0aa79549e",
+    "render_bwd": {"bytes": 591.99e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
+                   "sha256": "55ebdb4e99cf8d510aa9712431c5ab57669372a631741d3dae6731138b9f03cb",
                    "profile": "profiles/render_bwd_1M_8views.md"},
 }
 
