@@ -3,7 +3,9 @@
 // (view, Gaussian) items and the stable sort of tile entries by tile id give
 // every tile its list in the depth order of Sec. 3.1.
 //
-// Radix sort, per 8-bit digit pass:
+// Radix sort, 8-bit digit passes (the last one narrower when the bit count is
+// not a multiple of 8), or a single 9-bit pass of 512 digits for a 9-bit sort
+// (the tile-row sort of the list builder, whose rows usually fit 9 bits):
 //   * one histogram kernel counts every pass's digits in a single read;
 //   * each CTA of the pass kernel takes the next tile of 7680 keys (dynamic
 //     tile id, so every predecessor tile is already running), ranks its keys

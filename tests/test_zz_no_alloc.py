@@ -32,6 +32,9 @@ def _cases():
         (scenes.box_scene(1024, seed=0), [scenes.origin_camera()]),
         multiview(),
         (scenes.cluster_scene(60_000, 64, seed=3, sh_degree=1), [scenes.ring_camera(0.5, 640, 480)]),
+        # 320 tiles: the tile-id sort is one pass of 512 digits, copied back
+        # out of the alternate buffers (the other cases sort 4 or 11 bits)
+        (scenes.cluster_scene(30_000, 32, seed=5, sh_degree=1), [scenes.ring_camera(0.2, 320, 256)]),
     ]
 
 
