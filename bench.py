@@ -192,8 +192,8 @@ def kernel_times(collect=True) -> dict:
 # valid while the kernel's source file is the one profiled (its SHA-256) and the workload has the same number
 # of tile entries; otherwise the traffic is reported as null.
 PROFILED_TRAFFIC = {
-    "render_bwd": {"bytes": 592.05e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
-                   "sha256": "d45ab12a8950cf58dc1ecb40ee69f23972e48677fe8f8df6cda548893bf6216e",
+    "render_bwd": {"bytes": 594.82e6, "entries": 79448137, "source": "paper_2411_12788_gb300/csrc/render.cu",
+                   "sha256": "022f3893b1ac2df820a6f7bb1719c7874117dec52fe852828fbb15647ed631f6",
                    "profile": "profiles/render_bwd_1M_8views.md"},
 }
 
